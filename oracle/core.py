@@ -1,0 +1,202 @@
+"""ctypes front end of the FP64 oracle in ``knn_oracle.c``.
+
+Test infrastructure only (see the package docstring). Arrays are converted
+to C-contiguous float64 / int64 / float32 as each routine requires; results
+come back as numpy arrays.
+"""
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+IP, L2, COS = 0, 1, 2
+METRICS = {"ip": IP, "l2": L2, "cos": COS}
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "knn_oracle.c")
+_OUT_DIR = os.path.join(_HERE, "_build")
+_LIB = os.path.join(_OUT_DIR, "liborc.so")
+_lock = threading.Lock()
+_lib = None
+
+
+def lib_path():
+    return _LIB
+
+
+def build(force=False):
+    """Compile knn_oracle.c with gcc (OpenMP, FP contraction off)."""
+    os.makedirs(_OUT_DIR, exist_ok=True)
+    if (not force and os.path.exists(_LIB)
+            and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC)):
+        return _LIB
+    tmp = _LIB + ".tmp.%d" % os.getpid()
+    cmd = ["gcc", "-O2", "-fopenmp", "-ffp-contract=off", "-fno-fast-math",
+           "-shared", "-fPIC", "-o", tmp, _SRC, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            lib = ctypes.CDLL(_LIB)
+            P = ctypes.c_void_p
+            i64, i32 = ctypes.c_int64, ctypes.c_int
+            lib.orc_exact_topk.argtypes = [P, i64, P, i64, i32, i32, i32, P, P]
+            lib.orc_partial_reduce.argtypes = [P, i64, P, i64, i32, i32, i64, P, P]
+            lib.orc_topk_pairs.argtypes = [P, P, i64, i64, i32, P, P]
+            lib.orc_rerank.argtypes = [P, i64, P, i64, i32, i32, P, i32, i32, P, P]
+            lib.orc_grad.argtypes = [P, i64, P, i64, i32, i32, P, i32, P, P, P]
+            lib.orc_score.argtypes = [P, P, i32, i32]
+            lib.orc_score.restype = ctypes.c_double
+            lib.orc_bf16_round_array.argtypes = [P, i64, P]
+            lib.orc_e4m3_rows.argtypes = [P, i64, i32, P, P]
+            lib.orc_normalize_rows.argtypes = [P, i64, i32, P]
+            lib.orc_e4m3_round.argtypes = [ctypes.c_double]
+            lib.orc_e4m3_round.restype = ctypes.c_double
+            _lib = lib
+    return _lib
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _f32(a):
+    return np.ascontiguousarray(a, dtype=np.float32)
+
+
+def _i64(a):
+    return np.ascontiguousarray(a, dtype=np.int64)
+
+
+def _p(a):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _metric(m):
+    return METRICS[m] if isinstance(m, str) else int(m)
+
+
+def score(q, x, metric):
+    """Larger-is-better score of one row pair (IP, -||q-x||^2, or cosine)."""
+    q, x = _f64(q), _f64(x)
+    return _load().orc_score(_p(q), _p(x), q.shape[0], _metric(metric))
+
+
+def exact_topk(Q, X, K, metric):
+    """Exact K-NN (Eq. 1-2): (values, indices), each M x K, best first.
+
+    Values are reported forms: IP -> <q,x>, L2 -> ||q-x||^2, COS -> cosine.
+    """
+    Q, X = _f64(Q), _f64(X)
+    M, D = Q.shape
+    N = X.shape[0]
+    val = np.empty((M, K), np.float64)
+    idx = np.empty((M, K), np.int64)
+    _load().orc_exact_topk(_p(Q), M, _p(X), N, D, _metric(metric), K, _p(val), _p(idx))
+    return val, idx
+
+
+def partial_reduce(Q, X, L, metric):
+    """PartialReduce (Alg. 1) with bin l = j mod L: (V, A), each M x L.
+
+    V holds larger-is-better scores (L2: -||q-x||^2); empty bins have
+    V = -inf, A = -1.
+    """
+    Q, X = _f64(Q), _f64(X)
+    M, D = Q.shape
+    N = X.shape[0]
+    V = np.empty((M, L), np.float64)
+    A = np.empty((M, L), np.int64)
+    _load().orc_partial_reduce(_p(Q), M, _p(X), N, D, _metric(metric), L, _p(V), _p(A))
+    return V, A
+
+
+def topk_pairs(V, A, K):
+    """ExactRescoring (Sec. 5): the best K (value, index) pairs per row."""
+    V, A = _f64(V), _i64(A)
+    M, L = V.shape
+    val = np.empty((M, K), np.float64)
+    idx = np.empty((M, K), np.int64)
+    _load().orc_topk_pairs(_p(V), _p(A), M, L, K, _p(val), _p(idx))
+    return val, idx
+
+
+def _report(v, metric):
+    return -v if _metric(metric) == L2 else v
+
+
+def binwise_topk(Q, X, K, L, metric):
+    """The approximate method end to end: PartialReduce then ExactRescoring.
+
+    Returns reported values and indices, M x K, best first.
+    """
+    V, A = partial_reduce(Q, X, L, metric)
+    val, idx = topk_pairs(V, A, K)
+    return _report(val, metric), idx
+
+
+def rerank(Q, X, cand, K, metric):
+    """Score the candidate rows ``cand`` (M x Kp, -1 = none) and keep K."""
+    Q, X, cand = _f64(Q), _f64(X), _i64(cand)
+    M, D = Q.shape
+    N = X.shape[0]
+    Kp = cand.shape[1]
+    val = np.empty((M, K), np.float64)
+    idx = np.empty((M, K), np.int64)
+    _load().orc_rerank(_p(Q), M, _p(X), N, D, _metric(metric), _p(cand), Kp, K,
+                       _p(val), _p(idx))
+    return val, idx
+
+
+def grad(Q, X, idx, g, metric, want_dq=True, want_dx=True):
+    """Gradient of sum g[i,k] * value(q_i, x_idx[i,k]) w.r.t. Q and X."""
+    Q, X, idx, g = _f64(Q), _f64(X), _i64(idx), _f64(g)
+    M, D = Q.shape
+    N = X.shape[0]
+    K = idx.shape[1]
+    dQ = np.zeros((M, D), np.float64) if want_dq else None
+    dX = np.zeros((N, D), np.float64) if want_dx else None
+    _load().orc_grad(_p(Q), M, _p(X), N, D, _metric(metric), _p(idx), K, _p(g),
+                     _p(dQ) if dQ is not None else None,
+                     _p(dX) if dX is not None else None)
+    return dQ, dX
+
+
+def bf16_round(x):
+    """Round binary32 values to bfloat16 (nearest, ties to even), as float64."""
+    x = _f32(x)
+    out = np.empty(x.shape, np.float64)
+    _load().orc_bf16_round_array(_p(x), x.size, _p(out))
+    return out
+
+
+def e4m3_rows(x):
+    """Per-row E4M3 quantisation: (dequantised values float64, scales float32)."""
+    x = _f32(x)
+    rows, D = x.shape
+    out = np.empty((rows, D), np.float64)
+    sc = np.empty((rows,), np.float32)
+    _load().orc_e4m3_rows(_p(x), rows, D, _p(out), _p(sc))
+    return out, sc
+
+
+def e4m3_round(v):
+    """E4M3 rounding of one value (nearest even, saturating at 448)."""
+    return _load().orc_e4m3_round(float(v))
+
+
+def normalize_rows(x):
+    """Cosine preparation: rows scaled to unit l2 norm, returned as float32."""
+    x = _f32(x)
+    rows, D = x.shape
+    y = np.empty((rows, D), np.float32)
+    _load().orc_normalize_rows(_p(x), rows, D, _p(y))
+    return y

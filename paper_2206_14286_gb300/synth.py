@@ -1,0 +1,94 @@
+"""Seeded synthetic inputs shaped like the paper's workloads.
+
+This module holds no arithmetic of the search method: it only draws random
+numbers. Both the CUDA path's tests and the CPU oracle's tests take their
+inputs from here, so both sides see the same float32 bytes.
+
+Recipe (NumPy PCG64 generators, float32 output):
+  * ``iid_normal``: rows i.i.d. N(0, std^2).
+  * ``mixture``: ``n_centres`` centres drawn N(0, centre_std^2 I) from the data
+    seed; each point picks a centre uniformly and adds N(0, within_std^2 I).
+    The database uses the data seed (0 by default) and queries use another
+    seed (1 by default) with the *same* centres, so queries come from the
+    same mixture as the database.
+  * ``unit_rows``: rows scaled to unit l2 norm in float64 and stored as
+    float32 (the cosine workload's "rows normalised after sampling").
+Generation is chunked so that peak host memory stays near the output size.
+"""
+import numpy as np
+
+DATA_SEED, QUERY_SEED, TARGET_SEED, ARRIVAL_SEED = 0, 1, 2, 3
+_CHUNK = 1 << 18
+
+
+def iid_normal(n, d, seed, std=1.0):
+    rng = np.random.Generator(np.random.PCG64(seed))
+    out = np.empty((n, d), np.float32)
+    for s in range(0, n, _CHUNK):
+        e = min(n, s + _CHUNK)
+        out[s:e] = rng.standard_normal((e - s, d), dtype=np.float32)
+        if std != 1.0:
+            out[s:e] *= np.float32(std)
+    return out
+
+
+def mixture_centres(n_centres, d, seed=DATA_SEED, centre_std=1.0):
+    rng = np.random.Generator(np.random.PCG64([seed, 0xC0FFEE]))
+    return (rng.standard_normal((n_centres, d)) * centre_std).astype(np.float32)
+
+
+def mixture(n, d, n_centres, seed, centre_std=1.0, within_std=0.3, centre_seed=DATA_SEED):
+    centres = mixture_centres(n_centres, d, centre_seed, centre_std)
+    rng = np.random.Generator(np.random.PCG64(seed))
+    out = np.empty((n, d), np.float32)
+    for s in range(0, n, _CHUNK):
+        e = min(n, s + _CHUNK)
+        pick = rng.integers(0, n_centres, size=e - s)
+        noise = rng.standard_normal((e - s, d), dtype=np.float32)
+        out[s:e] = centres[pick] + np.float32(within_std) * noise
+    return out
+
+
+def unit_rows(x):
+    out = np.empty_like(x, dtype=np.float32)
+    for s in range(0, x.shape[0], _CHUNK):
+        blk = x[s:s + _CHUNK].astype(np.float64)
+        nrm = np.sqrt((blk * blk).sum(axis=1, keepdims=True))
+        nrm[nrm == 0.0] = 1.0
+        out[s:s + _CHUNK] = (blk / nrm).astype(np.float32)
+    return out
+
+
+def targets(m, k, seed=TARGET_SEED):
+    """Seeded N(0,1) weights t[m, k] for the softmax-over-top-K loss."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    return rng.standard_normal((m, k)).astype(np.float32)
+
+
+# Named workloads. Each returns (X, Q) as float32 numpy arrays plus the
+# search parameters; ``scale`` < 1 shrinks N (and M) for quick runs.
+def workload(name, scale=1.0):
+    def n_of(n):
+        return max(1, int(round(n * scale)))
+
+    if name == "iid_ip_16k":          # plain FP32, IP, K=10, L=1024
+        N, D, M = n_of(16384), 128, 64
+        X = iid_normal(N, D, DATA_SEED)
+        Q = iid_normal(M, D, QUERY_SEED)
+        return dict(X=X, Q=Q, metric="ip", K=10, L=1024, dtype="f32")
+    if name == "mix_l2_1m":           # BF16, L2, K=10, recall 0.95
+        N, D, M = n_of(1_000_000), 128, 1024
+        X = mixture(N, D, 256, DATA_SEED)
+        Q = mixture(M, D, 256, QUERY_SEED)
+        return dict(X=X, Q=Q, metric="l2", K=10, recall=0.95, dtype="bf16", rerank=2)
+    if name == "mix_cos_10m":         # E4M3, cosine, K=100, recall 0.95
+        N, D, M = n_of(10_000_000), 96, n_of(10_000)
+        X = unit_rows(mixture(N, D, 1024, DATA_SEED))
+        Q = unit_rows(mixture(M, D, 1024, QUERY_SEED))
+        return dict(X=X, Q=Q, metric="cos", K=100, recall=0.95, dtype="e4m3", rerank=2)
+    if name == "iid_ip_grad_1m":      # BF16, IP, K=32, backward
+        N, D, M = n_of(1_000_000), 256, n_of(4096)
+        X = iid_normal(N, D, DATA_SEED, std=1.0 / np.sqrt(D))
+        Q = iid_normal(M, D, QUERY_SEED, std=1.0 / np.sqrt(D))
+        return dict(X=X, Q=Q, metric="ip", K=32, recall=0.95, dtype="bf16")
+    raise KeyError(name)
