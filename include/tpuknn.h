@@ -1,0 +1,213 @@
+/*
+ * tpuknn.h -- C ABI of the GB300 (sm_103a) K-nearest-neighbour search library.
+ *
+ * The library implements the search of arXiv 2206.14286 ("TPU-KNN"):
+ *   1. a distance contraction between the queries Q (M x D) and the database
+ *      X (N x D) fused with PartialReduce (Alg. 1): for every query and every
+ *      bin l in [0, L) keep the best score and its index over the rows
+ *      j with j mod L == l, so the M x N score matrix never reaches memory;
+ *   2. ExactRescoring (Sec. 5): an exact top-K' over the L bin winners;
+ *   3. a re-rank of the K' candidates with FP32 scores, returning the top K.
+ * The problem statement is Sec. 2 (Eq. 1 K-argmin of a distance, Eq. 2 MIPS).
+ *
+ * Conventions for every entry point
+ *   - All array arguments are DEVICE pointers unless stated otherwise; the
+ *     caller owns every buffer. Matrices are row-major.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = the legacy default
+ *     stream). Work is enqueued asynchronously; nothing synchronises unless
+ *     stated. A non-OK return means nothing was enqueued, except
+ *     KNN_ECUDA (a launch failed; see knn_last_cuda_error).
+ *   - Device-side waits are bounded. A kernel that gives up sets a sticky
+ *     device flag; knn_sync_status() synchronises the device and returns
+ *     KNN_ETIMEOUT once, then clears it.
+ *   - Scores are "larger is better" internally: IP <q,x>; L2 the relaxed
+ *     <q,x> - ||x||^2/2 (App. A.2, Eq. 19, negated); COS <q,x> of rows
+ *     scaled to unit length (Sec. 2). Equal scores rank the smaller index
+ *     first. Returned values: IP <q,x>, L2 ||q-x||^2, COS cosine similarity,
+ *     each computed in FP32 (best first: IP/COS descending, L2 ascending).
+ *   - Inputs must be finite. Indices are int32 (N < 2^31).
+ *   - No C++ exception crosses this boundary.
+ */
+#ifndef TPUKNN_H_
+#define TPUKNN_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  KNN_OK = 0,
+  KNN_EINVAL = 1,        /* an argument is out of range, NULL or misaligned */
+  KNN_ENOMEM = 2,        /* the caller's workspace is smaller than required */
+  KNN_ECUDA = 3,         /* a CUDA call or launch failed */
+  KNN_ETIMEOUT = 4,      /* a device-side wait ran out (see knn_sync_status) */
+  KNN_EUNSUPPORTED = 5   /* valid request this build does not handle */
+} knn_status;
+
+typedef enum { KNN_IP = 0, KNN_L2 = 1, KNN_COS = 2 } knn_metric;
+
+/* Element type the contraction runs in. The database and the queries are
+ * stored in it; products accumulate in FP32. E4M3 uses one FP32 scale per
+ * row: value = code * scale. */
+typedef enum { KNN_F32 = 0, KNN_BF16 = 1, KNN_E4M3 = 2 } knn_dtype;
+
+const char* knn_status_string(int status);
+/* The last CUDA error code seen by the library on this thread (0 = none). */
+int knn_last_cuda_error(void);
+
+/* Bytes per element of `dtype` (4, 2, 1), or 0 for an unknown dtype. */
+int32_t knn_dtype_bytes(int32_t dtype);
+
+/* Row pitch, in elements, of a prepared database or query buffer: D rounded
+ * up to a multiple of 16 (so every row starts on a 16-byte boundary for the
+ * tensor-memory copies). Returns -1 if D < 1. */
+int32_t knn_row_pitch(int32_t D);
+
+/*
+ * Number of bins L for a recall target (Sec. 5.1, Eq. 13-14): the smallest
+ * L >= 1 with ((L-1)/L)^(K-1) >= recall_target, rounded up to a multiple of
+ * `round_to` (if round_to > 1), then clamped to N. K = 1 gives 1.
+ * Returns L, or -1 if N < 1, K < 1, K > N or recall_target is not in (0, 1).
+ * Host-only; needs no GPU.
+ */
+int64_t knn_plan_bins(int64_t N, int32_t K, double recall_target, int32_t round_to);
+
+/*
+ * Preparation of rows for the contraction (the database once, or queries).
+ *   x        : rows x D FP32 input rows (device).
+ *   out_lp   : rows x knn_row_pitch(D) elements of `dtype` (device). Columns
+ *              D..pitch-1 are written as zero. For KNN_F32 the rows are
+ *              copied (and normalised for KNN_COS).
+ *   out_scale: rows FP32 scales, required for KNN_E4M3 (scale = max|x|/448,
+ *              code = E4M3(x/scale), round-to-nearest-even, saturating; a
+ *              zero row gets scale 1), else ignored (may be NULL).
+ *   out_hnorm: rows FP32 values ||x^||^2/2 of the stored (rounded) rows,
+ *              required for KNN_L2 (the half-norm of App. A.2, Eq. 19), else
+ *              ignored (may be NULL).
+ *   out_f32  : rows x D FP32 unit-length rows, required for KNN_COS (the
+ *              FP32 source of the re-rank; normalisation sums squares in
+ *              FP64 in index order), else ignored (may be NULL).
+ * For KNN_COS every row is first scaled to unit length (Sec. 2: cosine
+ * search is MIPS on normalised rows) and the stored form is made from that.
+ * Errors: KNN_EINVAL for rows < 0, D < 1, a required pointer NULL, or a
+ * pointer not 16-byte aligned.
+ */
+knn_status knn_prepare(const float* x, int64_t rows, int32_t D, int32_t metric, int32_t dtype,
+                       void* out_lp, float* out_scale, float* out_hnorm, float* out_f32,
+                       void* stream);
+
+/*
+ * Approximate K-NN search: PartialReduce (Alg. 1) + ExactRescoring (Sec. 5)
+ * + FP32 re-rank.
+ *   db_lp, db_scale, db_hnorm : the prepared database (knn_prepare), N rows.
+ *   db_f32    : N x D FP32 rows used to score the final candidates (for COS
+ *               the unit-length rows from knn_prepare). NULL = score the
+ *               candidates from db_lp (dequantised).
+ *   q         : M x D FP32 queries (device); prepared inside the call.
+ *   K         : neighbours per query, 1 <= K <= min(L, 4096).
+ *   L         : number of bins (bin of row j = j mod L), 1 <= L <= N; if
+ *               L <= 0, L = knn_plan_bins(N, K, recall_target, 1).
+ *   rerank_mult: K' = max(1, rerank_mult) * K candidates (capped at L) leave
+ *               ExactRescoring and are scored in FP32; the best K are kept.
+ *   out_val   : M x K FP32 values (reported form), best first.
+ *   out_idx   : M x K int32 database indices.
+ *   workspace : device scratch of at least knn_search_workspace(...) bytes,
+ *               256-byte aligned. Its contents on entry do not matter.
+ * M = 0 is a valid no-op. Errors: KNN_EINVAL (sizes, NULL, alignment),
+ * KNN_ENOMEM (workspace too small), KNN_EUNSUPPORTED (D > 4096).
+ */
+knn_status knn_search(const void* db_lp, const float* db_scale, const float* db_hnorm,
+                      const float* db_f32, int64_t N, int32_t D, int32_t dtype, int32_t metric,
+                      const float* q, int64_t M, int32_t K, int64_t L, double recall_target,
+                      int32_t rerank_mult, float* out_val, int32_t* out_idx,
+                      void* workspace, size_t ws_bytes, void* stream);
+
+size_t knn_search_workspace(int64_t N, int32_t D, int32_t dtype, int32_t metric, int64_t M,
+                            int32_t K, int64_t L, double recall_target, int32_t rerank_mult);
+
+/*
+ * The same search with HOST queries and HOST outputs: copies q (M x D FP32)
+ * to the device, searches, copies the results back and synchronises
+ * `stream` before returning. The database and the workspace stay on the
+ * device; the workspace must also hold the staged queries and results
+ * (knn_search_host_workspace bytes). Pinned host memory makes the copies
+ * asynchronous DMA; pageable memory works but is slower.
+ */
+knn_status knn_search_host(const void* db_lp, const float* db_scale, const float* db_hnorm,
+                           const float* db_f32, int64_t N, int32_t D, int32_t dtype,
+                           int32_t metric, const float* q_host, int64_t M, int32_t K, int64_t L,
+                           double recall_target, int32_t rerank_mult, float* out_val_host,
+                           int32_t* out_idx_host, void* workspace, size_t ws_bytes, void* stream);
+
+size_t knn_search_host_workspace(int64_t N, int32_t D, int32_t dtype, int32_t metric, int64_t M,
+                                 int32_t K, int64_t L, double recall_target, int32_t rerank_mult);
+
+/*
+ * PartialReduce alone (Alg. 1; the paper's aggregate_to_topk = False,
+ * App. A.1): for every query i and bin l the best internal score and its
+ * index, out_v[i*L + l], out_a[i*L + l]. Scores are in the internal
+ * orientation (see the conventions above; L2 is the relaxed score).
+ * For KNN_BF16 / KNN_E4M3 the values carry the contraction's rounding: the
+ * kernel keeps only the top 32 - c bits of each FP32 score, c <= 13, while
+ * it reduces (the low bits hold the row's position in its bin); for E4M3 the
+ * per-query scale is left out of the value (it does not change the order
+ * within a query).
+ */
+knn_status knn_partial_reduce(const void* db_lp, const float* db_scale, const float* db_hnorm,
+                              int64_t N, int32_t D, int32_t dtype, int32_t metric, const float* q,
+                              int64_t M, int64_t L, float* out_v, int32_t* out_a,
+                              void* workspace, size_t ws_bytes, void* stream);
+
+size_t knn_partial_reduce_workspace(int64_t N, int32_t D, int32_t dtype, int32_t metric,
+                                    int64_t M, int64_t L);
+
+/*
+ * Exact K-NN (Eq. 1-2): the top K over all N rows, scored in `dtype` with
+ * FP32 accumulation (the L = N case of PartialReduce), then values recomputed
+ * in FP32 from db_f32 (or db_lp if NULL). Same arguments and rules as
+ * knn_search without L, recall_target and rerank_mult.
+ */
+knn_status knn_search_exact(const void* db_lp, const float* db_scale, const float* db_hnorm,
+                            const float* db_f32, int64_t N, int32_t D, int32_t dtype,
+                            int32_t metric, const float* q, int64_t M, int32_t K,
+                            float* out_val, int32_t* out_idx, void* workspace, size_t ws_bytes,
+                            void* stream);
+
+size_t knn_search_exact_workspace(int64_t N, int32_t D, int32_t dtype, int32_t metric, int64_t M,
+                                  int32_t K);
+
+/*
+ * Backward of the selected values (the differentiation pattern): with the
+ * indices idx (M x K, int32, -1 = skip) held constant, the gradient of
+ *   sum_{i,k} grad_val[i,k] * value(q_i, x_idx[i,k])
+ * where value is the reported form (IP <q,x>; L2 ||q-x||^2; COS the cosine
+ * of the rows as given). Rows are read as FP32 from x_f32 (N x D) if not
+ * NULL, else from the prepared db_lp/db_scale (dequantised); queries q are
+ * FP32 (M x D).
+ *   dq : M x D FP32, overwritten (NULL = not needed).
+ *   dx : N x D FP32 (NULL = not needed). If zero_dx != 0 the kernel first
+ *        writes zeros over all of dx, else it adds into dx.
+ *   deterministic: 0 = FP32 atomic adds (order-dependent rounding);
+ *        1 = rows gathered in (i, k) order per touched row, bit-reproducible
+ *        (needs knn_backward_workspace bytes; otherwise ws may be NULL).
+ */
+knn_status knn_backward(const void* db_lp, const float* db_scale, const float* x_f32, int64_t N,
+                        int32_t D, int32_t dtype, int32_t metric, const float* q, int64_t M,
+                        int32_t K, const int32_t* idx, const float* grad_val, float* dq,
+                        float* dx, int32_t zero_dx, int32_t deterministic, void* workspace,
+                        size_t ws_bytes, void* stream);
+
+size_t knn_backward_workspace(int64_t N, int32_t D, int64_t M, int32_t K, int32_t deterministic);
+
+/* Synchronise the current device and report a device-side wait timeout
+ * (KNN_ETIMEOUT, flag then cleared) or a CUDA error (KNN_ECUDA). */
+knn_status knn_sync_status(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TPUKNN_H_ */

@@ -1,0 +1,567 @@
+// api.cu -- the extern "C" boundary: argument checks, the bin planner
+// (Eq. 13-14), work decomposition, workspace layout and kernel launches.
+#include <cmath>
+#include <cstring>
+
+#include "common.cuh"
+#include "kernels.h"
+
+using namespace tpuknn;
+
+namespace tpuknn {
+
+thread_local int g_last_cuda = 0;
+
+int device_sm_count() {
+  static int cache[64] = {0};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+    cudaGetLastError();
+    return 152;
+  }
+  if (cache[dev] == 0) {
+    int n = 0;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) {
+      cudaGetLastError();
+      n = 152;
+    }
+    cache[dev] = n;
+  }
+  return cache[dev];
+}
+
+}  // namespace tpuknn
+
+namespace {
+
+constexpr size_t kAlign = 256;
+inline size_t al(size_t x) { return (x + kAlign - 1) & ~(kAlign - 1); }
+inline bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
+inline bool valid_metric(int m) { return m == KNN_IP || m == KNN_L2 || m == KNN_COS; }
+inline bool valid_dtype(int d) { return d == KNN_F32 || d == KNN_BF16 || d == KNN_E4M3; }
+
+knn_status cuda_status(cudaError_t e) {
+  if (e == cudaSuccess) return KNN_OK;
+  g_last_cuda = (int)e;
+  return KNN_ECUDA;
+}
+
+// Eq. 13 at L: ((L-1)/L)^(K-1).
+double paper_recall(int64_t L, int K) {
+  if (K <= 1) return 1.0;
+  return std::pow((double)(L - 1) / (double)L, (double)(K - 1));
+}
+
+int64_t plan_bins(int64_t N, int K, double r, int round_to) {
+  if (N < 1 || K < 1 || K > N || !(r > 0.0 && r < 1.0)) return -1;
+  int64_t L = 1;
+  if (K > 1) {
+    // Eq. 14: L >= 1 / (1 - r^(1/(K-1))); then the smallest L meeting Eq. 13.
+    double est = 1.0 / (1.0 - std::pow(r, 1.0 / (double)(K - 1)));
+    if (!(est < 9.0e18)) return -1;
+    L = (int64_t)std::ceil(est);
+    if (L < 1) L = 1;
+    while (L > 1 && paper_recall(L - 1, K) >= r) --L;
+    while (paper_recall(L, K) < r) ++L;
+  }
+  if (round_to > 1) L = round_up(L, round_to);
+  if (L > N) L = N;
+  return L;
+}
+
+// Tile shape of each K1 variant.
+void k1_tile(int dtype, int* BW, int* BQ) {
+  if (dtype == KNN_F32) {
+    *BW = 64;
+    *BQ = 64;
+  } else {
+    *BW = 128;
+    *BQ = 256;
+  }
+}
+
+int bits_for(int64_t n) {  // bits to hold values 0..n-1
+  int b = 0;
+  while (((int64_t)1 << b) < n) ++b;
+  return b;
+}
+
+constexpr int kMaxCodeBits = 13;
+
+K1Plan make_plan(int64_t N, int64_t M, int64_t L, int D, int metric, int dtype,
+                 int64_t force_splits) {
+  K1Plan p{};
+  p.N = N;
+  p.M = M;
+  p.L = L;
+  p.D = D;
+  p.pitch = (int)round_up(D, 16);
+  p.metric = metric;
+  p.dtype = dtype;
+  k1_tile(dtype, &p.BW, &p.BQ);
+  p.g = L < p.BW ? (int)(p.BW / L) : 1;
+  p.Lk = (int64_t)p.g * L;
+  p.nstrips = cdiv(p.Lk, p.BW);
+  p.nqtiles = cdiv(M, p.BQ);
+  p.ntiles = cdiv(N, p.Lk);
+  const int64_t units = p.nstrips * (p.nqtiles > 0 ? p.nqtiles : 1);
+  int64_t splits;
+  if (force_splits > 0) {
+    splits = force_splits;
+  } else {
+    const int64_t target = (int64_t)device_sm_count() * (dtype == KNN_F32 ? 4 : 1);
+    splits = cdiv(target, units);
+  }
+  if (splits < 1) splits = 1;
+  if (splits > p.ntiles) splits = p.ntiles;
+  if (dtype != KNN_F32) {
+    const int64_t min_splits = cdiv(p.ntiles, (int64_t)1 << kMaxCodeBits);
+    if (splits < min_splits) splits = min_splits;
+  }
+  p.tiles_per_split = cdiv(p.ntiles, splits);
+  p.nsplits = cdiv(p.ntiles, p.tiles_per_split);
+  p.code_bits = dtype == KNN_F32 ? 0 : bits_for(p.tiles_per_split);
+  return p;
+}
+
+// Per-call query preparation buffers.
+struct QueryBufs {
+  size_t lp, scale, f32;
+};
+QueryBufs query_bytes(int64_t M, int D, int dtype, int metric) {
+  QueryBufs b{};
+  const int pitch = (int)round_up(D, 16);
+  const int esz = dtype == KNN_F32 ? 4 : (dtype == KNN_BF16 ? 2 : 1);
+  b.lp = al((size_t)M * pitch * esz);
+  b.scale = dtype == KNN_E4M3 ? al((size_t)M * 4) : 0;
+  b.f32 = (metric == KNN_COS && dtype != KNN_F32) ? al((size_t)M * D * 4) : 0;
+  return b;
+}
+
+struct SearchArgs {
+  const void* db_lp;
+  const float* db_scale;
+  const float* db_hnorm;
+  const float* db_f32;
+  int64_t N;
+  int D, dtype, metric;
+  const float* q;
+  int64_t M;
+  int K;
+  int64_t L;
+  double recall;
+  int rerank;
+};
+
+// Checks that do not need the data pointers.
+knn_status check_sizes(int64_t N, int D, int dtype, int metric, int64_t M, int K) {
+  if (N < 1 || D < 1 || M < 0 || K < 1 || K > N) return KNN_EINVAL;
+  if (!valid_dtype(dtype) || !valid_metric(metric)) return KNN_EINVAL;
+  if (N >= ((int64_t)1 << 31) - 1) return KNN_EINVAL;
+  if (D > kMaxD || K > kMaxK) return KNN_EUNSUPPORTED;
+  return KNN_OK;
+}
+
+knn_status resolve_L(const SearchArgs& a, int64_t* L) {
+  int64_t l = a.L;
+  if (l <= 0) l = plan_bins(a.N, a.K, a.recall, 1);
+  if (l < 1 || l > a.N || a.K > l) return KNN_EINVAL;
+  *L = l;
+  return KNN_OK;
+}
+
+int kprime(int K, int rerank, int64_t L) {
+  int64_t kp = (int64_t)(rerank < 1 ? 1 : rerank) * K;
+  if (kp > L) kp = L;
+  if (kp > kMaxK) kp = kMaxK;
+  if (kp < K) kp = K;
+  return (int)kp;
+}
+
+struct SearchLayout {
+  K1Plan plan;
+  int Kp;
+  QueryBufs qb;
+  size_t off_qlp, off_qscale, off_qf32, off_part_v, off_part_a, off_cand, total;
+};
+
+knn_status layout_search(const SearchArgs& a, SearchLayout* s) {
+  knn_status st = check_sizes(a.N, a.D, a.dtype, a.metric, a.M, a.K);
+  if (st != KNN_OK) return st;
+  int64_t L;
+  if ((st = resolve_L(a, &L)) != KNN_OK) return st;
+  s->plan = make_plan(a.N, a.M, L, a.D, a.metric, a.dtype, 0);
+  s->Kp = kprime(a.K, a.rerank, L);
+  s->qb = query_bytes(a.M, a.D, a.dtype, a.metric);
+  size_t o = 0;
+  s->off_qlp = o;
+  o += s->qb.lp;
+  s->off_qscale = o;
+  o += s->qb.scale;
+  s->off_qf32 = o;
+  o += s->qb.f32;
+  const size_t n = (size_t)(s->plan.nsplits * s->plan.M * s->plan.Lk);
+  s->off_part_v = o;
+  o += al(n * 4);
+  s->off_part_a = o;
+  if (a.dtype == KNN_F32) o += al(n * 4);
+  s->off_cand = o;
+  o += al((size_t)a.M * s->Kp * 8);
+  s->total = o;
+  return KNN_OK;
+}
+
+knn_status check_pointers(const SearchArgs& a, const float* out_val, const int32_t* out_idx) {
+  if (!a.db_lp || !a.q || !out_val || !out_idx) return KNN_EINVAL;
+  if (a.metric == KNN_L2 && !a.db_hnorm) return KNN_EINVAL;
+  if (a.dtype == KNN_E4M3 && !a.db_scale) return KNN_EINVAL;
+  if (!aligned(a.db_lp, 16) || !aligned(a.q, 4) || !aligned(out_val, 4) || !aligned(out_idx, 4))
+    return KNN_EINVAL;
+  if (a.db_f32 && !aligned(a.db_f32, 4)) return KNN_EINVAL;
+  return KNN_OK;
+}
+
+// Prepare queries into the workspace; returns the FP32 query rows the
+// re-rank reads and their stride.
+cudaError_t prep_queries(const SearchArgs& a, const SearchLayout& s, char* ws, const float** qf32,
+                         int64_t* q_stride, cudaStream_t st) {
+  void* qlp = ws + s.off_qlp;
+  float* qscale = s.qb.scale ? reinterpret_cast<float*>(ws + s.off_qscale) : nullptr;
+  float* qf = s.qb.f32 ? reinterpret_cast<float*>(ws + s.off_qf32) : nullptr;
+  cudaError_t e = launch_prep(a.q, a.M, a.D, s.plan.pitch, a.metric, a.dtype, qlp, qscale, nullptr,
+                              qf, st);
+  if (a.dtype == KNN_F32) {
+    *qf32 = reinterpret_cast<const float*>(qlp);
+    *q_stride = s.plan.pitch;
+  } else if (a.metric == KNN_COS) {
+    *qf32 = qf;
+    *q_stride = a.D;
+  } else {
+    *qf32 = a.q;
+    *q_stride = a.D;
+  }
+  return e;
+}
+
+cudaError_t run_k1(const K1Plan& p, const SearchArgs& a, const void* xlp, const float* xscale,
+                   const float* hnorm, const void* qlp, const float* qscale, Partials parts,
+                   cudaStream_t st) {
+  if (a.dtype == KNN_F32)
+    return launch_k1_simt(p, reinterpret_cast<const float*>(xlp), hnorm,
+                          reinterpret_cast<const float*>(qlp), parts, st);
+  return launch_k1_tc(p, xlp, xscale, hnorm, qlp, qscale, parts, st);
+}
+
+knn_status search_impl(const SearchArgs& a, float* out_val, int32_t* out_idx, void* workspace,
+                       size_t ws_bytes, cudaStream_t st) {
+  SearchLayout s;
+  knn_status rc = layout_search(a, &s);
+  if (rc != KNN_OK) return rc;
+  if (a.M == 0) return KNN_OK;
+  if ((rc = check_pointers(a, out_val, out_idx)) != KNN_OK) return rc;
+  if (!workspace || !aligned(workspace, kAlign)) return KNN_EINVAL;
+  if (ws_bytes < s.total) return KNN_ENOMEM;
+  char* ws = reinterpret_cast<char*>(workspace);
+  const float* qf32;
+  int64_t q_stride;
+  cudaError_t e = prep_queries(a, s, ws, &qf32, &q_stride, st);
+  if (e != cudaSuccess) return cuda_status(e);
+  Partials parts{reinterpret_cast<float*>(ws + s.off_part_v),
+                 a.dtype == KNN_F32 ? reinterpret_cast<int32_t*>(ws + s.off_part_a) : nullptr, 0};
+  const float* qscale = s.qb.scale ? reinterpret_cast<const float*>(ws + s.off_qscale) : nullptr;
+  e = run_k1(s.plan, a, a.db_lp, a.db_scale, a.db_hnorm, ws + s.off_qlp, qscale, parts, st);
+  if (e == cudaErrorNotSupported) return KNN_EUNSUPPORTED;
+  if (e != cudaSuccess) return cuda_status(e);
+  uint64_t* cand = reinterpret_cast<uint64_t*>(ws + s.off_cand);
+  e = launch_k2(s.plan, parts, s.Kp, nullptr, cand, st);
+  if (e != cudaSuccess) return cuda_status(e);
+  e = launch_k3(a.M, a.D, a.metric, cand, s.Kp, a.K, qf32, q_stride, a.db_f32, a.db_lp, a.dtype,
+                s.plan.pitch, a.db_scale, a.N, out_val, out_idx, st);
+  return cuda_status(e);
+}
+
+// ---------------------------------------------------------------------------
+// Exact search: chunks of Nc rows, each a PartialReduce with one bin per row
+// (L = Nc: every bin holds exactly one row, so the bin winners are all
+// scores), merged into a running top-K per query.
+// ---------------------------------------------------------------------------
+struct ExactLayout {
+  int64_t Nc;
+  K1Plan plan;  // for a full chunk
+  QueryBufs qb;
+  size_t off_qlp, off_qscale, off_qf32, off_part_v, off_part_a, off_run, total;
+};
+
+constexpr int64_t kExactPartialBudget = (int64_t)1 << 26;  // entries per chunk
+
+knn_status layout_exact(const SearchArgs& a, ExactLayout* s) {
+  knn_status st = check_sizes(a.N, a.D, a.dtype, a.metric, a.M, a.K);
+  if (st != KNN_OK) return st;
+  int BW, BQ;
+  k1_tile(a.dtype, &BW, &BQ);
+  int64_t mq = a.M > 0 ? a.M : 1;
+  int64_t nc = (kExactPartialBudget / mq) / BW * BW;
+  if (nc < BW) nc = BW;
+  if (nc > a.N) nc = a.N;
+  s->Nc = nc;
+  s->plan = make_plan(nc, a.M, nc, a.D, a.metric, a.dtype, 1);
+  s->qb = query_bytes(a.M, a.D, a.dtype, a.metric);
+  size_t o = 0;
+  s->off_qlp = o;
+  o += s->qb.lp;
+  s->off_qscale = o;
+  o += s->qb.scale;
+  s->off_qf32 = o;
+  o += s->qb.f32;
+  const size_t n = (size_t)(s->plan.M * s->plan.Lk);
+  s->off_part_v = o;
+  o += al(n * 4);
+  s->off_part_a = o;
+  if (a.dtype == KNN_F32) o += al(n * 4);
+  s->off_run = o;
+  o += al((size_t)a.M * a.K * 8);
+  s->total = o;
+  return KNN_OK;
+}
+
+knn_status exact_impl(const SearchArgs& a, float* out_val, int32_t* out_idx, void* workspace,
+                      size_t ws_bytes, cudaStream_t st) {
+  ExactLayout s;
+  knn_status rc = layout_exact(a, &s);
+  if (rc != KNN_OK) return rc;
+  if (a.M == 0) return KNN_OK;
+  if ((rc = check_pointers(a, out_val, out_idx)) != KNN_OK) return rc;
+  if (!workspace || !aligned(workspace, kAlign)) return KNN_EINVAL;
+  if (ws_bytes < s.total) return KNN_ENOMEM;
+  char* ws = reinterpret_cast<char*>(workspace);
+  SearchLayout sl;
+  sl.plan = s.plan;
+  sl.qb = s.qb;
+  sl.off_qlp = s.off_qlp;
+  sl.off_qscale = s.off_qscale;
+  sl.off_qf32 = s.off_qf32;
+  const float* qf32;
+  int64_t q_stride;
+  cudaError_t e = prep_queries(a, sl, ws, &qf32, &q_stride, st);
+  if (e != cudaSuccess) return cuda_status(e);
+  const float* qscale = s.qb.scale ? reinterpret_cast<const float*>(ws + s.off_qscale) : nullptr;
+  uint64_t* run = reinterpret_cast<uint64_t*>(ws + s.off_run);
+  const int esz = knn_dtype_bytes(a.dtype);
+  for (int64_t n0 = 0; n0 < a.N; n0 += s.Nc) {
+    const int64_t nc = (a.N - n0) < s.Nc ? (a.N - n0) : s.Nc;
+    K1Plan p = make_plan(nc, a.M, nc, a.D, a.metric, a.dtype, 1);
+    Partials parts{reinterpret_cast<float*>(ws + s.off_part_v),
+                   a.dtype == KNN_F32 ? reinterpret_cast<int32_t*>(ws + s.off_part_a) : nullptr,
+                   n0};
+    const char* xlp = reinterpret_cast<const char*>(a.db_lp) + (size_t)n0 * p.pitch * esz;
+    const float* xs = a.db_scale ? a.db_scale + n0 : nullptr;
+    const float* hn = a.db_hnorm ? a.db_hnorm + n0 : nullptr;
+    e = run_k1(p, a, xlp, xs, hn, ws + s.off_qlp, qscale, parts, st);
+    if (e == cudaErrorNotSupported) return KNN_EUNSUPPORTED;
+    if (e != cudaSuccess) return cuda_status(e);
+    e = launch_k2(p, parts, a.K, n0 == 0 ? nullptr : run, run, st);
+    if (e != cudaSuccess) return cuda_status(e);
+  }
+  e = launch_k3(a.M, a.D, a.metric, run, a.K, a.K, qf32, q_stride, a.db_f32, a.db_lp, a.dtype,
+                s.plan.pitch, a.db_scale, a.N, out_val, out_idx, st);
+  return cuda_status(e);
+}
+
+}  // namespace
+
+// ===========================================================================
+// extern "C"
+// ===========================================================================
+extern "C" {
+
+const char* knn_status_string(int s) {
+  switch (s) {
+    case KNN_OK: return "ok";
+    case KNN_EINVAL: return "invalid argument";
+    case KNN_ENOMEM: return "workspace too small";
+    case KNN_ECUDA: return "CUDA error";
+    case KNN_ETIMEOUT: return "device-side wait timed out";
+    case KNN_EUNSUPPORTED: return "unsupported";
+    default: return "unknown status";
+  }
+}
+
+int knn_last_cuda_error(void) { return g_last_cuda; }
+
+int32_t knn_dtype_bytes(int32_t dtype) {
+  switch (dtype) {
+    case KNN_F32: return 4;
+    case KNN_BF16: return 2;
+    case KNN_E4M3: return 1;
+    default: return 0;
+  }
+}
+
+int32_t knn_row_pitch(int32_t D) { return D < 1 ? -1 : (int32_t)round_up(D, 16); }
+
+int64_t knn_plan_bins(int64_t N, int32_t K, double recall_target, int32_t round_to) {
+  return plan_bins(N, K, recall_target, round_to);
+}
+
+knn_status knn_prepare(const float* x, int64_t rows, int32_t D, int32_t metric, int32_t dtype,
+                       void* out_lp, float* out_scale, float* out_hnorm, float* out_f32,
+                       void* stream) {
+  if (rows < 0 || D < 1 || !valid_metric(metric) || !valid_dtype(dtype)) return KNN_EINVAL;
+  if (D > kMaxD) return KNN_EUNSUPPORTED;
+  if (rows == 0) return KNN_OK;
+  if (!x || !out_lp || !aligned(out_lp, 16) || !aligned(x, 4)) return KNN_EINVAL;
+  if (dtype == KNN_E4M3 && !out_scale) return KNN_EINVAL;
+  if (metric == KNN_L2 && !out_hnorm) return KNN_EINVAL;
+  if (metric == KNN_COS && !out_f32) return KNN_EINVAL;
+  return cuda_status(launch_prep(x, rows, D, knn_row_pitch(D), metric, dtype, out_lp, out_scale,
+                                 out_hnorm, out_f32, (cudaStream_t)stream));
+}
+
+size_t knn_search_workspace(int64_t N, int32_t D, int32_t dtype, int32_t metric, int64_t M,
+                            int32_t K, int64_t L, double recall_target, int32_t rerank_mult) {
+  SearchArgs a{nullptr, nullptr, nullptr, nullptr, N, D, dtype, metric, nullptr, M, K, L,
+               recall_target, rerank_mult};
+  SearchLayout s;
+  if (layout_search(a, &s) != KNN_OK) return 0;
+  return s.total;
+}
+
+knn_status knn_search(const void* db_lp, const float* db_scale, const float* db_hnorm,
+                      const float* db_f32, int64_t N, int32_t D, int32_t dtype, int32_t metric,
+                      const float* q, int64_t M, int32_t K, int64_t L, double recall_target,
+                      int32_t rerank_mult, float* out_val, int32_t* out_idx, void* workspace,
+                      size_t ws_bytes, void* stream) {
+  SearchArgs a{db_lp, db_scale, db_hnorm, db_f32, N, D, dtype, metric, q, M, K, L,
+               recall_target, rerank_mult};
+  return search_impl(a, out_val, out_idx, workspace, ws_bytes, (cudaStream_t)stream);
+}
+
+size_t knn_search_host_workspace(int64_t N, int32_t D, int32_t dtype, int32_t metric, int64_t M,
+                                 int32_t K, int64_t L, double recall_target, int32_t rerank_mult) {
+  size_t base = knn_search_workspace(N, D, dtype, metric, M, K, L, recall_target, rerank_mult);
+  if (base == 0) return 0;
+  return al(base) + al((size_t)M * D * 4) + al((size_t)M * K * 4) * 2;
+}
+
+knn_status knn_search_host(const void* db_lp, const float* db_scale, const float* db_hnorm,
+                           const float* db_f32, int64_t N, int32_t D, int32_t dtype,
+                           int32_t metric, const float* q_host, int64_t M, int32_t K, int64_t L,
+                           double recall_target, int32_t rerank_mult, float* out_val_host,
+                           int32_t* out_idx_host, void* workspace, size_t ws_bytes,
+                           void* stream) {
+  size_t base = knn_search_workspace(N, D, dtype, metric, M, K, L, recall_target, rerank_mult);
+  if (base == 0) return KNN_EINVAL;
+  if (M == 0) return KNN_OK;
+  if (!q_host || !out_val_host || !out_idx_host) return KNN_EINVAL;
+  if (!workspace || !aligned(workspace, kAlign)) return KNN_EINVAL;
+  size_t need = knn_search_host_workspace(N, D, dtype, metric, M, K, L, recall_target,
+                                          rerank_mult);
+  if (ws_bytes < need) return KNN_ENOMEM;
+  char* ws = reinterpret_cast<char*>(workspace);
+  float* qd = reinterpret_cast<float*>(ws + al(base));
+  float* vd = reinterpret_cast<float*>(ws + al(base) + al((size_t)M * D * 4));
+  int32_t* id = reinterpret_cast<int32_t*>(ws + al(base) + al((size_t)M * D * 4) +
+                                           al((size_t)M * K * 4));
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaError_t e = cudaMemcpyAsync(qd, q_host, (size_t)M * D * 4, cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) return cuda_status(e);
+  knn_status rc = knn_search(db_lp, db_scale, db_hnorm, db_f32, N, D, dtype, metric, qd, M, K, L,
+                             recall_target, rerank_mult, vd, id, ws, base, stream);
+  if (rc != KNN_OK) return rc;
+  e = cudaMemcpyAsync(out_val_host, vd, (size_t)M * K * 4, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(out_idx_host, id, (size_t)M * K * 4, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  return cuda_status(e);
+}
+
+size_t knn_partial_reduce_workspace(int64_t N, int32_t D, int32_t dtype, int32_t metric,
+                                    int64_t M, int64_t L) {
+  if (L < 1 || L > N) return 0;
+  SearchArgs a{nullptr, nullptr, nullptr, nullptr, N, D, dtype, metric, nullptr, M, 1, L, 0.5, 1};
+  SearchLayout s;
+  if (layout_search(a, &s) != KNN_OK) return 0;
+  return s.total;
+}
+
+knn_status knn_partial_reduce(const void* db_lp, const float* db_scale, const float* db_hnorm,
+                              int64_t N, int32_t D, int32_t dtype, int32_t metric, const float* q,
+                              int64_t M, int64_t L, float* out_v, int32_t* out_a,
+                              void* workspace, size_t ws_bytes, void* stream) {
+  if (L < 1 || L > N) return KNN_EINVAL;
+  SearchArgs a{db_lp, db_scale, db_hnorm, nullptr, N, D, dtype, metric, q, M, 1, L, 0.5, 1};
+  SearchLayout s;
+  knn_status rc = layout_search(a, &s);
+  if (rc != KNN_OK) return rc;
+  if (M == 0) return KNN_OK;
+  if ((rc = check_pointers(a, out_v, out_a)) != KNN_OK) return rc;
+  if (!workspace || !aligned(workspace, kAlign)) return KNN_EINVAL;
+  if (ws_bytes < s.total) return KNN_ENOMEM;
+  cudaStream_t st = (cudaStream_t)stream;
+  char* ws = reinterpret_cast<char*>(workspace);
+  const float* qf32;
+  int64_t q_stride;
+  cudaError_t e = prep_queries(a, s, ws, &qf32, &q_stride, st);
+  if (e != cudaSuccess) return cuda_status(e);
+  Partials parts{reinterpret_cast<float*>(ws + s.off_part_v),
+                 dtype == KNN_F32 ? reinterpret_cast<int32_t*>(ws + s.off_part_a) : nullptr, 0};
+  const float* qscale = s.qb.scale ? reinterpret_cast<const float*>(ws + s.off_qscale) : nullptr;
+  e = run_k1(s.plan, a, db_lp, db_scale, db_hnorm, ws + s.off_qlp, qscale, parts, st);
+  if (e == cudaErrorNotSupported) return KNN_EUNSUPPORTED;
+  if (e != cudaSuccess) return cuda_status(e);
+  return cuda_status(launch_merge_bins(s.plan, parts, out_v, out_a, st));
+}
+
+size_t knn_search_exact_workspace(int64_t N, int32_t D, int32_t dtype, int32_t metric, int64_t M,
+                                  int32_t K) {
+  SearchArgs a{nullptr, nullptr, nullptr, nullptr, N, D, dtype, metric, nullptr, M, K, N, 0.5, 1};
+  ExactLayout s;
+  if (layout_exact(a, &s) != KNN_OK) return 0;
+  return s.total;
+}
+
+knn_status knn_search_exact(const void* db_lp, const float* db_scale, const float* db_hnorm,
+                            const float* db_f32, int64_t N, int32_t D, int32_t dtype,
+                            int32_t metric, const float* q, int64_t M, int32_t K,
+                            float* out_val, int32_t* out_idx, void* workspace, size_t ws_bytes,
+                            void* stream) {
+  SearchArgs a{db_lp, db_scale, db_hnorm, db_f32, N, D, dtype, metric, q, M, K, N, 0.5, 1};
+  return exact_impl(a, out_val, out_idx, workspace, ws_bytes, (cudaStream_t)stream);
+}
+
+size_t knn_backward_workspace(int64_t N, int32_t D, int64_t M, int32_t K, int32_t deterministic) {
+  (void)D;
+  return backward_ws_bytes(N, M, K, deterministic);
+}
+
+knn_status knn_backward(const void* db_lp, const float* db_scale, const float* x_f32, int64_t N,
+                        int32_t D, int32_t dtype, int32_t metric, const float* q, int64_t M,
+                        int32_t K, const int32_t* idx, const float* grad_val, float* dq,
+                        float* dx, int32_t zero_dx, int32_t deterministic, void* workspace,
+                        size_t ws_bytes, void* stream) {
+  if (N < 1 || D < 1 || M < 0 || K < 1 || !valid_metric(metric) || !valid_dtype(dtype))
+    return KNN_EINVAL;
+  if (D > kMaxD) return KNN_EUNSUPPORTED;
+  if (!x_f32 && !db_lp) return KNN_EINVAL;
+  if (!x_f32 && dtype == KNN_E4M3 && !db_scale) return KNN_EINVAL;
+  if (M > 0 && (!q || !idx || !grad_val)) return KNN_EINVAL;
+  if (M * (int64_t)K >= ((int64_t)1 << 31)) return KNN_EUNSUPPORTED;
+  const size_t need = backward_ws_bytes(N, M, K, deterministic);
+  if (dx && deterministic && M > 0) {
+    if (!workspace || !aligned(workspace, kAlign)) return KNN_EINVAL;
+    if (ws_bytes < need) return KNN_ENOMEM;
+  }
+  if (!dq && !dx) return KNN_OK;
+  return cuda_status(launch_backward(M, D, K, metric, q, x_f32, db_lp, dtype, knn_row_pitch(D),
+                                     db_scale, N, idx, grad_val, dq, dx, zero_dx, deterministic,
+                                     workspace, (cudaStream_t)stream));
+}
+
+knn_status knn_sync_status(void) {
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return cuda_status(e);
+  if (k1_tc_take_timeout()) return KNN_ETIMEOUT;
+  return KNN_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,86 @@
+// common.cuh -- small device/host helpers shared by the library's kernels.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string.h>
+
+#include "../../include/tpuknn.h"
+
+namespace tpuknn {
+
+constexpr int kMaxK = 4096;       // largest K (and K') a search accepts
+constexpr int kMaxD = 4096;       // largest row length
+constexpr uint32_t kNegInfBits = 0xff800000u;
+
+// ---------------------------------------------------------------------------
+// Ordered 64-bit keys: (score, index) pairs that compare as unsigned integers
+// in the order "larger score first, then smaller index" (the tie rule).
+// The high word maps the IEEE float to an unsigned integer whose order is the
+// float order; the low word is the bitwise complement of the index, so the
+// smaller index gives the larger key. Key 0 is below every real pair and
+// marks an empty slot.
+// ---------------------------------------------------------------------------
+__host__ __device__ __forceinline__ uint32_t f2u(float f) {
+  uint32_t u;
+  memcpy(&u, &f, 4);
+  return u;
+}
+__host__ __device__ __forceinline__ float u2f(uint32_t u) {
+  float f;
+  memcpy(&f, &u, 4);
+  return f;
+}
+__host__ __device__ __forceinline__ uint32_t float_to_ordered(float f) {
+  uint32_t u = f2u(f);
+  return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+__host__ __device__ __forceinline__ float ordered_to_float(uint32_t o) {
+  uint32_t u = (o & 0x80000000u) ? (o & 0x7fffffffu) : ~o;
+  return u2f(u);
+}
+__host__ __device__ __forceinline__ uint64_t make_key(float score, int32_t idx) {
+  return ((uint64_t)float_to_ordered(score) << 32) | (uint64_t)(~(uint32_t)idx);
+}
+__host__ __device__ __forceinline__ float key_score(uint64_t k) {
+  return ordered_to_float((uint32_t)(k >> 32));
+}
+__host__ __device__ __forceinline__ int32_t key_index(uint64_t k) {
+  return (int32_t)(~(uint32_t)(k & 0xffffffffu));
+}
+
+__device__ __forceinline__ float neg_inf() { return __uint_as_float(kNegInfBits); }
+
+// ---------------------------------------------------------------------------
+// In-place bitonic sort of n (a power of two) 64-bit keys in shared memory,
+// descending, by all threads of the block. Ends with __syncthreads().
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void bitonic_sort_desc(uint64_t* s, int n) {
+  for (int size = 2; size <= n; size <<= 1) {
+    for (int stride = size >> 1; stride > 0; stride >>= 1) {
+      __syncthreads();
+      for (int t = threadIdx.x; t < (n >> 1); t += blockDim.x) {
+        int lo = 2 * t - (t & (stride - 1));
+        int hi = lo + stride;
+        bool desc = ((lo & size) == 0);
+        uint64_t a = s[lo], b = s[hi];
+        if ((a < b) == desc) {
+          s[lo] = b;
+          s[hi] = a;
+        }
+      }
+    }
+  }
+  __syncthreads();
+}
+
+__host__ __device__ __forceinline__ int next_pow2(int v) {
+  int p = 1;
+  while (p < v) p <<= 1;
+  return p;
+}
+
+// Round-up helpers.
+__host__ __device__ __forceinline__ int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
+__host__ __device__ __forceinline__ int64_t round_up(int64_t a, int64_t b) { return cdiv(a, b) * b; }
+
+}  // namespace tpuknn

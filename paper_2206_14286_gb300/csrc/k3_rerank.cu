@@ -1,0 +1,78 @@
+// k3_rerank.cu -- FP32 scoring of the Kp candidates that leave ExactRescoring
+// and selection of the final K (the precision pattern: BF16 / E4M3 decide
+// the candidates, FP32 decides their order and values).
+//
+// One CTA per query; each warp scores candidates one at a time with lanes
+// splitting D (coalesced row reads), then the Kp keys are sorted in shared
+// memory. Values: IP <q,x>; L2 sum (q-x)^2 evaluated directly; COS <q,x> of
+// the unit-length rows.
+#include "common.cuh"
+#include "dtypes.cuh"
+#include "kernels.h"
+
+namespace tpuknn {
+
+namespace {
+__global__ void __launch_bounds__(256)
+k3_rerank_kernel(const uint64_t* __restrict__ cand, int Kp, int K, int P2, int D, int metric,
+                 const float* __restrict__ qf32, int64_t q_stride,
+                 const float* __restrict__ xf32, const void* __restrict__ xlp, int dtype,
+                 int pitch, const float* __restrict__ xscale, int64_t N,
+                 float* __restrict__ out_val, int32_t* __restrict__ out_idx) {
+  extern __shared__ uint64_t sk[];
+  const int64_t i = blockIdx.x;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  const float* q = qf32 + i * q_stride;
+  for (int c = warp; c < Kp; c += nwarps) {
+    const uint64_t key = cand[i * Kp + c];
+    const int32_t j = key ? key_index(key) : -1;
+    if (j < 0 || j >= N) {
+      if (lane == 0) sk[c] = 0;
+      continue;
+    }
+    float acc = 0.0f;
+    for (int d = lane; d < D; d += 32) {
+      const float x = xf32 ? xf32[(int64_t)j * D + d] : load_stored(xlp, dtype, j, pitch, d, xscale);
+      const float qq = q[d];
+      if (metric == KNN_L2) {
+        const float t = qq - x;
+        acc = fmaf(t, t, acc);
+      } else {
+        acc = fmaf(qq, x, acc);
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) sk[c] = make_key(metric == KNN_L2 ? -acc : acc, j);
+  }
+  for (int t = Kp + threadIdx.x; t < P2; t += blockDim.x) sk[t] = 0;
+  bitonic_sort_desc(sk, P2);
+  for (int t = threadIdx.x; t < K; t += blockDim.x) {
+    const uint64_t key = t < Kp ? sk[t] : 0;
+    const float s = key_score(key);
+    out_idx[i * K + t] = key ? key_index(key) : -1;
+    out_val[i * K + t] = key ? (metric == KNN_L2 ? -s : s) : __int_as_float(0x7fc00000);
+  }
+}
+}  // namespace
+
+cudaError_t launch_k3(int64_t M, int D, int metric, const uint64_t* cand, int Kp, int K,
+                      const float* qf32, int64_t q_stride, const float* xf32, const void* xlp,
+                      int dtype, int pitch, const float* xscale, int64_t N, float* out_val,
+                      int32_t* out_idx, cudaStream_t st) {
+  if (M <= 0) return cudaSuccess;
+  const int P2 = next_pow2(Kp > K ? Kp : K);
+  const size_t smem = (size_t)P2 * sizeof(uint64_t);
+  if (smem > 200 * 1024) return cudaErrorInvalidValue;
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(k3_rerank_kernel,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  k3_rerank_kernel<<<(unsigned)M, 256, smem, st>>>(cand, Kp, K, P2, D, metric, qf32, q_stride,
+                                                   xf32, xlp, dtype, pitch, xscale, N, out_val,
+                                                   out_idx);
+  return cudaGetLastError();
+}
+
+}  // namespace tpuknn

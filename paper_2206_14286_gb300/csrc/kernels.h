@@ -1,0 +1,82 @@
+// kernels.h -- host-side launchers of the library's kernels (internal).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace tpuknn {
+
+// ----------------------------------------------------------------------------
+// Work decomposition of PartialReduce (K1), shared by every K1 variant.
+//
+// Bins: row j belongs to bin j mod L. K1 runs with Lk = g*L bins (g >= 1 a
+// fold factor so that a strip of BW tile rows is filled when L < BW); K2 then
+// merges bins b, b+L, ..., b+(g-1)L, which together hold exactly the rows of
+// bin b. Viewing the database as a [ntiles x Lk] grid (row j = t*Lk + b), a
+// "strip" is BW consecutive bins and a "tile" is one strip of one grid row t:
+// BW consecutive database rows whose bins are fixed per lane. Every CTA owns
+// (strip, query tile, split) and walks tiles t in its split's range, keeping
+// the running best of each (query, bin) it owns in registers.
+// ----------------------------------------------------------------------------
+struct K1Plan {
+  int64_t N, M, L, Lk;
+  int g;
+  int D, pitch;
+  int metric, dtype;
+  int BW, BQ;               // tile rows (bins per strip), queries per tile
+  int64_t nstrips, nqtiles, ntiles, tiles_per_split, nsplits;
+  int code_bits;            // packed partials: bits of the in-split tile ordinal
+};
+
+// Partial results of K1, one entry per (split, query, bin):
+//   pair form  : float value + int32 index (exact; FP32 path)
+//   packed form: one 32-bit float whose low code_bits bits encode the tile
+//                ordinal inside the split (tensor-core paths).
+struct Partials {
+  float* v;         // pair form values, or packed keys (as float bits)
+  int32_t* a;       // pair form indices (nullptr for packed)
+  int64_t index_offset;  // added to every decoded index (chunked exact search)
+};
+
+cudaError_t launch_prep(const float* x, int64_t rows, int D, int pitch, int metric, int dtype,
+                        void* out_lp, float* out_scale, float* out_hnorm, float* out_f32,
+                        cudaStream_t st);
+
+cudaError_t launch_k1_simt(const K1Plan& p, const float* X, const float* hnorm, const float* Qp,
+                           Partials out, cudaStream_t st);
+
+// Tensor-core K1 (BF16 / E4M3). Returns cudaErrorNotSupported when the shape is
+// outside what the kernel handles.
+cudaError_t launch_k1_tc(const K1Plan& p, const void* X, const float* xscale, const float* hnorm,
+                         const void* Qp, const float* qscale, Partials out, cudaStream_t st);
+
+// K2: per query, merge the partials of every split and fold and select the
+// best Kp (score, index) keys, sorted. If run_in is given its Kp keys per
+// query join the selection (running top-K of a chunked search).
+cudaError_t launch_k2(const K1Plan& p, Partials parts, int Kp, const uint64_t* run_in,
+                      uint64_t* out_keys, cudaStream_t st);
+
+// PartialReduce output alone: per (query, bin) the merged best value and
+// index (index -1 and value -inf for a bin no row reached).
+cudaError_t launch_merge_bins(const K1Plan& p, Partials parts, float* out_v, int32_t* out_a,
+                              cudaStream_t st);
+
+// K3: score the Kp candidates of each query in FP32 and keep the best K.
+// Rows come from xf32 (N x D) when given, else from the stored rows.
+cudaError_t launch_k3(int64_t M, int D, int metric, const uint64_t* cand, int Kp, int K,
+                      const float* qf32, int64_t q_stride, const float* xf32, const void* xlp,
+                      int dtype, int pitch, const float* xscale, int64_t N, float* out_val,
+                      int32_t* out_idx, cudaStream_t st);
+
+cudaError_t launch_backward(int64_t M, int D, int K, int metric, const float* q,
+                            const float* xf32, const void* xlp, int dtype, int pitch,
+                            const float* xscale, int64_t N, const int32_t* idx,
+                            const float* g, float* dq, float* dx, int zero_dx, int deterministic,
+                            void* ws, cudaStream_t st);
+size_t backward_ws_bytes(int64_t N, int64_t M, int K, int deterministic);
+
+// Number of SMs of the current device (cached).
+int device_sm_count();
+// Take and clear the tensor-core kernels' timeout flag (synchronous).
+bool k1_tc_take_timeout();
+
+}  // namespace tpuknn

@@ -1,0 +1,190 @@
+"""Python binding of the C ABI (argument marshalling only).
+
+Every step of the search runs in libtpuknn.so; torch provides device memory
+and streams. See include/tpuknn.h for the semantics of each call.
+"""
+import torch
+
+from . import _lib
+from ._lib import METRIC, DTYPE, check
+
+_ESIZE = {"f32": 4, "bf16": 2, "e4m3": 1}
+
+
+def _stream(stream):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return s.cuda_stream
+
+
+def _ptr(t):
+    return None if t is None else t.data_ptr()
+
+
+def plan_bins(N, K, recall_target=0.95, round_to=1):
+    """Eq. 14: bins for an expected recall (Eq. 13) of at least recall_target."""
+    L = _lib.get().knn_plan_bins(int(N), int(K), float(recall_target), int(round_to))
+    if L < 1:
+        raise ValueError("no bin count for N=%d K=%d r=%g" % (N, K, recall_target))
+    return int(L)
+
+
+def row_pitch(D):
+    return int(_lib.get().knn_row_pitch(int(D)))
+
+
+def _workspace(nbytes, device):
+    return torch.empty(max(int(nbytes), 256), dtype=torch.uint8, device=device)
+
+
+class Database:
+    """A device-resident database prepared for search (knn_prepare).
+
+    x: N x D float32 CUDA tensor. metric: 'ip' | 'l2' | 'cos'.
+    dtype: 'f32' | 'bf16' | 'e4m3' (the contraction's element type).
+    keep_f32: keep FP32 rows for the final re-rank (for 'cos' the
+    unit-length copy is always kept; otherwise this holds a reference to x).
+    """
+
+    def __init__(self, x, metric="l2", dtype="bf16", keep_f32=True, stream=None):
+        if not (x.is_cuda and x.dtype == torch.float32 and x.dim() == 2):
+            raise ValueError("x must be a 2-D float32 CUDA tensor")
+        x = x.contiguous()
+        self.N, self.D = x.shape
+        self.metric, self.dtype = metric, dtype
+        self.device = x.device
+        self.pitch = row_pitch(self.D)
+        dev = x.device
+        self.lp = torch.empty(self.N * self.pitch * _ESIZE[dtype], dtype=torch.uint8, device=dev)
+        self.scale = torch.empty(self.N, dtype=torch.float32, device=dev) if dtype == "e4m3" else None
+        self.hnorm = torch.empty(self.N, dtype=torch.float32, device=dev) if metric == "l2" else None
+        if metric == "cos":
+            self.f32 = torch.empty((self.N, self.D), dtype=torch.float32, device=dev)
+        else:
+            self.f32 = x if keep_f32 else None
+        with torch.cuda.device(dev):
+            check(_lib.get().knn_prepare(x.data_ptr(), self.N, self.D, METRIC[metric], DTYPE[dtype],
+                                         self.lp.data_ptr(), _ptr(self.scale), _ptr(self.hnorm),
+                                         _ptr(self.f32) if metric == "cos" else None,
+                                         _stream(stream)), "knn_prepare")
+        self._ws = {}
+
+    # -- helpers ---------------------------------------------------------------
+    def _args(self):
+        return (self.lp.data_ptr(), _ptr(self.scale), _ptr(self.hnorm), _ptr(self.f32),
+                self.N, self.D, DTYPE[self.dtype], METRIC[self.metric])
+
+    def _get_ws(self, key, nbytes):
+        ws = self._ws.get(key)
+        if ws is None or ws.numel() < nbytes:
+            ws = _workspace(nbytes, self.device)
+            self._ws[key] = ws
+        return ws
+
+    def resolve_L(self, K, L=None, recall_target=0.95):
+        return int(L) if L else plan_bins(self.N, K, recall_target)
+
+    # -- calls -----------------------------------------------------------------
+    def search(self, q, K, L=None, recall_target=0.95, rerank=2, stream=None, out=None):
+        """Approximate search; returns (values M x K float32, indices M x K int32)."""
+        q = q.contiguous()
+        M = q.shape[0]
+        L = self.resolve_L(K, L, recall_target)
+        lib = _lib.get()
+        nb = lib.knn_search_workspace(self.N, self.D, DTYPE[self.dtype], METRIC[self.metric], M, K,
+                                      L, recall_target, rerank)
+        if nb == 0:
+            raise ValueError("invalid search arguments (N=%d D=%d M=%d K=%d L=%d)"
+                             % (self.N, self.D, M, K, L))
+        ws = self._get_ws(("search", M, K, L, rerank), nb)
+        if out is None:
+            val = torch.empty((M, K), dtype=torch.float32, device=self.device)
+            idx = torch.empty((M, K), dtype=torch.int32, device=self.device)
+        else:
+            val, idx = out
+        with torch.cuda.device(self.device):
+            check(lib.knn_search(*self._args(), q.data_ptr(), M, K, L, recall_target, rerank,
+                                 val.data_ptr(), idx.data_ptr(), ws.data_ptr(), ws.numel(),
+                                 _stream(stream)), "knn_search")
+        return val, idx
+
+    def search_host(self, q_host, K, L=None, recall_target=0.95, rerank=2, stream=None,
+                    out=None):
+        """Search with host queries and host outputs (copies inside the call)."""
+        M = q_host.shape[0]
+        L = self.resolve_L(K, L, recall_target)
+        lib = _lib.get()
+        nb = lib.knn_search_host_workspace(self.N, self.D, DTYPE[self.dtype], METRIC[self.metric],
+                                           M, K, L, recall_target, rerank)
+        ws = self._get_ws(("host", M, K, L, rerank), nb)
+        if out is None:
+            val = torch.empty((M, K), dtype=torch.float32, pin_memory=True)
+            idx = torch.empty((M, K), dtype=torch.int32, pin_memory=True)
+        else:
+            val, idx = out
+        with torch.cuda.device(self.device):
+            check(lib.knn_search_host(*self._args(), q_host.data_ptr(), M, K, L, recall_target,
+                                      rerank, val.data_ptr(), idx.data_ptr(), ws.data_ptr(),
+                                      ws.numel(), _stream(stream)), "knn_search_host")
+        return val, idx
+
+    def search_exact(self, q, K, stream=None):
+        q = q.contiguous()
+        M = q.shape[0]
+        lib = _lib.get()
+        nb = lib.knn_search_exact_workspace(self.N, self.D, DTYPE[self.dtype], METRIC[self.metric],
+                                            M, K)
+        if nb == 0:
+            raise ValueError("invalid exact-search arguments")
+        ws = self._get_ws(("exact", M, K), nb)
+        val = torch.empty((M, K), dtype=torch.float32, device=self.device)
+        idx = torch.empty((M, K), dtype=torch.int32, device=self.device)
+        with torch.cuda.device(self.device):
+            check(lib.knn_search_exact(*self._args(), q.data_ptr(), M, K, val.data_ptr(),
+                                       idx.data_ptr(), ws.data_ptr(), ws.numel(),
+                                       _stream(stream)), "knn_search_exact")
+        return val, idx
+
+    def partial_reduce(self, q, L, stream=None):
+        """Alg. 1 alone: (V, A), each M x L (internal scores, indices)."""
+        q = q.contiguous()
+        M = q.shape[0]
+        lib = _lib.get()
+        nb = lib.knn_partial_reduce_workspace(self.N, self.D, DTYPE[self.dtype],
+                                              METRIC[self.metric], M, L)
+        if nb == 0:
+            raise ValueError("invalid partial-reduce arguments")
+        ws = self._get_ws(("pr", M, L), nb)
+        V = torch.empty((M, L), dtype=torch.float32, device=self.device)
+        A = torch.empty((M, L), dtype=torch.int32, device=self.device)
+        a = self._args()
+        with torch.cuda.device(self.device):
+            check(lib.knn_partial_reduce(a[0], a[1], a[2], self.N, self.D, a[6], a[7],
+                                         q.data_ptr(), M, L, V.data_ptr(), A.data_ptr(),
+                                         ws.data_ptr(), ws.numel(), _stream(stream)),
+                  "knn_partial_reduce")
+        return V, A
+
+    def backward(self, q, idx, grad_val, want_dq=True, want_dx=True, deterministic=False,
+                 x_f32=None, stream=None):
+        """Gradient of sum(grad_val * value(q_i, x_idx)) w.r.t. q and the rows."""
+        q = q.contiguous()
+        idx = idx.contiguous()
+        grad_val = grad_val.contiguous().float()
+        M, K = idx.shape
+        lib = _lib.get()
+        xf = x_f32 if x_f32 is not None else self.f32
+        dq = torch.empty((M, self.D), dtype=torch.float32, device=self.device) if want_dq else None
+        dx = torch.empty((self.N, self.D), dtype=torch.float32, device=self.device) if want_dx else None
+        nb = lib.knn_backward_workspace(self.N, self.D, M, K, int(deterministic))
+        ws = self._get_ws(("bwd", M, K), nb) if nb else None
+        with torch.cuda.device(self.device):
+            check(lib.knn_backward(self.lp.data_ptr(), _ptr(self.scale), _ptr(xf), self.N, self.D,
+                                   DTYPE[self.dtype], METRIC[self.metric], q.data_ptr(), M, K,
+                                   idx.data_ptr(), grad_val.data_ptr(), _ptr(dq), _ptr(dx), 1,
+                                   int(deterministic), _ptr(ws), ws.numel() if ws is not None else 0,
+                                   _stream(stream)), "knn_backward")
+        return dq, dx
+
+
+def sync_status():
+    check(_lib.get().knn_sync_status(), "knn_sync_status")

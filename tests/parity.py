@@ -1,0 +1,124 @@
+"""Comparison rules between the CUDA path and the FP64 oracle.
+
+A query is *decided* when every score margin that fixes the answer exceeds
+twice the tolerance (both sides may err by one tolerance):
+  * bin-wise step (scores of the stored, possibly low-precision rows): the
+    gap between the Kp-th and (Kp+1)-th bin winners, and the gap between the
+    best and second-best row of every bin whose winner is among the best
+    Kp+1;
+  * final step (FP32-row scores of the oracle's Kp candidates): the gap
+    between the K-th and (K+1)-th candidate (if Kp > K) and between adjacent
+    ranks of the first K.
+Decided queries must return the oracle's indices exactly. Undecided queries
+must return, at every rank, a value within tolerance of the oracle's value at
+that rank, and indices whose own oracle score matches the returned value and
+which are within tolerance of their bin's best.
+
+Tolerances are relative to the natural scale of a score: ||q|| max||x|| for
+IP/COS, ||q||^2 + max||x||^2 for L2.
+"""
+import numpy as np
+
+REL_F32 = 1e-5
+REL_LOWP = 1e-2
+
+
+def score_matrix(Q, X, metric, chunk=1 << 14):
+    """FP64 larger-is-better scores: IP <q,x>, L2 -||q-x||^2, COS cosine."""
+    Q = np.asarray(Q, np.float64)
+    M, N = Q.shape[0], X.shape[0]
+    out = np.empty((M, N), np.float64)
+    qn2 = (Q * Q).sum(1)
+    for s in range(0, N, chunk):
+        Xc = np.asarray(X[s:s + chunk], np.float64)
+        G = Q @ Xc.T
+        if metric == "ip":
+            out[:, s:s + chunk] = G
+        elif metric == "l2":
+            xn2 = (Xc * Xc).sum(1)
+            out[:, s:s + chunk] = -(qn2[:, None] + xn2[None, :] - 2.0 * G)
+        else:
+            xn = np.sqrt((Xc * Xc).sum(1))
+            qn = np.sqrt(qn2)
+            with np.errstate(invalid="ignore", divide="ignore"):
+                c = G / (qn[:, None] * xn[None, :])
+            out[:, s:s + chunk] = np.nan_to_num(c)
+    return out
+
+
+def query_scale(Q, X, metric):
+    Q = np.asarray(Q, np.float64)
+    qn2 = (Q * Q).sum(1)
+    xmax2 = float(max((np.asarray(X[s:s + 65536], np.float64) ** 2).sum(1).max()
+                      for s in range(0, X.shape[0], 65536)))
+    if metric == "l2":
+        return qn2 + xmax2
+    if metric == "cos":
+        return np.ones_like(qn2)
+    return np.sqrt(qn2 * xmax2)
+
+
+def reported(S, metric):
+    return -S if metric == "l2" else S
+
+
+def bin_best_second(S, L):
+    M, N = S.shape
+    nb = -(-N // L)
+    P = np.full((M, nb * L), -np.inf)
+    P[:, :N] = S
+    P = P.reshape(M, nb, L)
+    if nb >= 2:
+        part = -np.partition(-P, 1, axis=1)
+        return part[:, 0, :], part[:, 1, :]
+    return P[:, 0, :], np.full((M, L), -np.inf)
+
+
+def decided_mask(S_lp, L, Kp, S_f32, cand, K, tol):
+    """Boolean per query; cand = the oracle's Kp candidates (M x Kp)."""
+    M = S_lp.shape[0]
+    ok = np.ones(M, bool)
+    best, second = bin_best_second(S_lp, L)
+    w = -np.sort(-best, axis=1)
+    if L > Kp:
+        ok &= (w[:, Kp - 1] - w[:, Kp]) > 2 * tol
+    thr = w[:, min(Kp, L - 1)]
+    relevant = best >= thr[:, None]
+    ok &= np.all(~relevant | ((best - second) > 2 * tol[:, None]), axis=1)
+    sc = np.take_along_axis(S_f32, np.maximum(cand, 0), 1)
+    sc = np.where(cand >= 0, sc, -np.inf)
+    sc = -np.sort(-sc, axis=1)
+    upto = min(K + 1, Kp) if Kp > K else K
+    if upto >= 2:
+        gaps = sc[:, :upto - 1] - sc[:, 1:upto]
+        ok &= np.all(gaps > 2 * tol[:, None], axis=1)
+    return ok
+
+
+def check_search(gpu_val, gpu_idx, orc_val, orc_idx, S_lp, S_f32, L, metric, tol, decided):
+    """Asserts the rules above; returns the fraction of decided queries."""
+    gpu_val = np.asarray(gpu_val, np.float64)
+    gpu_idx = np.asarray(gpu_idx, np.int64)
+    M, K = gpu_idx.shape
+    best, _ = bin_best_second(S_lp, L)
+    bad = []
+    for i in range(M):
+        if decided[i]:
+            if not np.array_equal(gpu_idx[i], orc_idx[i]):
+                bad.append((i, "idx", gpu_idx[i][:8], orc_idx[i][:8]))
+                continue
+        if np.any(np.abs(gpu_val[i] - orc_val[i]) > tol[i]):
+            bad.append((i, "val-by-rank", gpu_val[i][:6], orc_val[i][:6]))
+            continue
+        j = gpu_idx[i]
+        if np.any(j < 0) or len(set(j.tolist())) != K:
+            bad.append((i, "invalid idx", j[:8]))
+            continue
+        own = reported(S_f32[i, j], metric)
+        if np.any(np.abs(own - gpu_val[i]) > tol[i]):
+            bad.append((i, "own value", own[:6], gpu_val[i][:6]))
+            continue
+        if np.any(S_lp[i, j] < best[i, j % L] - tol[i]):
+            bad.append((i, "not a bin maximum", j[:8]))
+    assert not bad, "%d of %d queries disagree, e.g. %s" % (len(bad), M, bad[:3])
+    return float(np.mean(decided))

@@ -1,0 +1,100 @@
+"""The C ABI library builds, loads and exports what include/tpuknn.h declares;
+host-only entry points (planner, pitch, argument checks) behave as stated.
+No GPU is needed: no call here launches a kernel."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_2206_14286_gb300 import build as B
+from paper_2206_14286_gb300 import _lib
+from oracle import recall as R
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    B.build()
+    return _lib.get()
+
+
+def declared_functions():
+    text = open(os.path.join(ROOT, "include", "tpuknn.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(knn_[a-z_0-9]+)\s*\(", text)))
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_functions()
+    assert len(names) >= 15
+    for n in names:
+        assert hasattr(lib, n), n
+        assert n in _lib.SIGNATURES, "binding lacks " + n
+
+
+def test_binding_declares_only_header_functions():
+    assert set(_lib.SIGNATURES) <= set(declared_functions())
+
+
+@pytest.mark.parametrize("N,K,r", [(16384, 10, 0.95), (10 ** 6, 10, 0.95), (10 ** 7, 100, 0.95),
+                                   (10 ** 6, 32, 0.95), (1000, 2, 0.5), (10 ** 6, 10, 0.99)])
+def test_plan_bins_matches_oracle_eq14(lib, N, K, r):
+    assert lib.knn_plan_bins(N, K, r, 1) == min(R.min_bins(K, r), N)
+
+
+def test_plan_bins_rounding_and_edges(lib):
+    assert lib.knn_plan_bins(10 ** 6, 10, 0.95, 128) == 256
+    assert lib.knn_plan_bins(10 ** 7, 100, 0.95, 128) == 2048
+    assert lib.knn_plan_bins(100, 10, 0.95, 1) == 100        # clamped to N
+    assert lib.knn_plan_bins(1000, 1, 0.99, 1) == 1          # K = 1
+    assert lib.knn_plan_bins(1000, 1, 0.99, 128) == 128
+    for bad in [(0, 1, 0.9, 1), (10, 0, 0.9, 1), (10, 11, 0.9, 1), (10, 2, 1.0, 1),
+                (10, 2, 0.0, 1)]:
+        assert lib.knn_plan_bins(*bad) == -1
+
+
+def test_pitch_and_dtype_bytes(lib):
+    assert [lib.knn_row_pitch(d) for d in (1, 16, 17, 96, 100, 128)] == [16, 16, 32, 96, 112, 128]
+    assert lib.knn_row_pitch(0) == -1
+    assert [lib.knn_dtype_bytes(t) for t in (0, 1, 2, 7)] == [4, 2, 1, 0]
+
+
+def test_status_strings(lib):
+    for s in range(6):
+        assert lib.knn_status_string(s)
+
+
+def test_invalid_arguments_rejected_before_any_launch(lib):
+    f = lib.knn_search
+    # N = 0, K > N, bad metric, bad dtype, K > L: all EINVAL without touching a device
+    base = dict(db=None, sc=None, hn=None, f32=None, N=100, D=8, dt=0, me=0, q=None, M=4, K=3,
+                L=10, r=0.9, rr=1, ov=None, oi=None, ws=None, wsb=0, st=None)
+
+    def call(**kw):
+        a = dict(base, **kw)
+        return f(a["db"], a["sc"], a["hn"], a["f32"], a["N"], a["D"], a["dt"], a["me"], a["q"],
+                 a["M"], a["K"], a["L"], a["r"], a["rr"], a["ov"], a["oi"], a["ws"], a["wsb"],
+                 a["st"])
+
+    assert call(N=0) == _lib.KNN_EINVAL
+    assert call(K=101) == _lib.KNN_EINVAL
+    assert call(me=5) == _lib.KNN_EINVAL
+    assert call(dt=9) == _lib.KNN_EINVAL
+    assert call(K=20, L=10) == _lib.KNN_EINVAL
+    assert call(L=101) == _lib.KNN_EINVAL
+    assert call(D=5000) == _lib.KNN_EUNSUPPORTED
+    assert call() == _lib.KNN_EINVAL           # null pointers
+    assert call(M=0) == _lib.KNN_OK            # empty query set is a no-op
+    # workspace queries return 0 for invalid requests
+    assert lib.knn_search_workspace(0, 8, 0, 0, 4, 3, 10, 0.9, 1) == 0
+    assert lib.knn_search_exact_workspace(100, 8, 0, 0, 4, 101) == 0
+    assert lib.knn_partial_reduce_workspace(100, 8, 0, 0, 4, 101) == 0
+
+
+def test_workspace_grows_with_queries(lib):
+    a = lib.knn_search_workspace(10 ** 6, 128, 1, 1, 1024, 10, 256, 0.95, 2)
+    b = lib.knn_search_workspace(10 ** 6, 128, 1, 1, 2048, 10, 256, 0.95, 2)
+    assert 0 < a < b
+    assert lib.knn_search_host_workspace(10 ** 6, 128, 1, 1, 1024, 10, 256, 0.95, 2) > a
