@@ -69,14 +69,15 @@ int64_t plan_bins(int64_t N, int K, double r, int round_to) {
   return L;
 }
 
-// Tile shape of each K1 variant.
-void k1_tile(int dtype, int* BW, int* BQ) {
+// Tile shape of each K1 variant (BQ = 0: the row length is not supported).
+void k1_tile(int dtype, int D, int64_t M, int* BW, int* BQ) {
   if (dtype == KNN_F32) {
     *BW = 64;
     *BQ = 64;
   } else {
     *BW = 128;
-    *BQ = 256;
+    const int maxq = k1_tc_query_tile(dtype, D);
+    *BQ = (maxq == 256 && M <= 128) ? 128 : maxq;
   }
 }
 
@@ -98,7 +99,8 @@ K1Plan make_plan(int64_t N, int64_t M, int64_t L, int D, int metric, int dtype,
   p.pitch = (int)round_up(D, 16);
   p.metric = metric;
   p.dtype = dtype;
-  k1_tile(dtype, &p.BW, &p.BQ);
+  k1_tile(dtype, D, M, &p.BW, &p.BQ);
+  if (p.BQ == 0) return p;
   p.g = L < p.BW ? (int)(p.BW / L) : 1;
   p.Lk = (int64_t)p.g * L;
   p.nstrips = cdiv(p.Lk, p.BW);
@@ -191,6 +193,7 @@ knn_status layout_search(const SearchArgs& a, SearchLayout* s) {
   int64_t L;
   if ((st = resolve_L(a, &L)) != KNN_OK) return st;
   s->plan = make_plan(a.N, a.M, L, a.D, a.metric, a.dtype, 0);
+  if (s->plan.BQ == 0) return KNN_EUNSUPPORTED;
   s->Kp = kprime(a.K, a.rerank, L);
   s->qb = query_bytes(a.M, a.D, a.dtype, a.metric);
   size_t o = 0;
@@ -207,7 +210,7 @@ knn_status layout_search(const SearchArgs& a, SearchLayout* s) {
   if (a.dtype == KNN_F32) o += al(n * 4);
   s->off_cand = o;
   o += al((size_t)a.M * s->Kp * 8);
-  s->total = o;
+  s->total = o > kAlign ? o : kAlign;
   return KNN_OK;
 }
 
@@ -298,7 +301,8 @@ knn_status layout_exact(const SearchArgs& a, ExactLayout* s) {
   knn_status st = check_sizes(a.N, a.D, a.dtype, a.metric, a.M, a.K);
   if (st != KNN_OK) return st;
   int BW, BQ;
-  k1_tile(a.dtype, &BW, &BQ);
+  k1_tile(a.dtype, a.D, a.M, &BW, &BQ);
+  if (BQ == 0) return KNN_EUNSUPPORTED;
   int64_t mq = a.M > 0 ? a.M : 1;
   int64_t nc = (kExactPartialBudget / mq) / BW * BW;
   if (nc < BW) nc = BW;
@@ -320,7 +324,7 @@ knn_status layout_exact(const SearchArgs& a, ExactLayout* s) {
   if (a.dtype == KNN_F32) o += al(n * 4);
   s->off_run = o;
   o += al((size_t)a.M * a.K * 8);
-  s->total = o;
+  s->total = o > kAlign ? o : kAlign;
   return KNN_OK;
 }
 

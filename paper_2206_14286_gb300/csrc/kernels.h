@@ -74,6 +74,10 @@ cudaError_t launch_backward(int64_t M, int D, int K, int metric, const float* q,
                             void* ws, cudaStream_t st);
 size_t backward_ws_bytes(int64_t N, int64_t M, int K, int deterministic);
 
+// Largest resident query tile of the tensor-core K1 for this row length
+// (256 or 128), or 0 if the rows are too long.
+int k1_tc_query_tile(int dtype, int D);
+
 // Number of SMs of the current device (cached).
 int device_sm_count();
 // Take and clear the tensor-core kernels' timeout flag (synchronous).

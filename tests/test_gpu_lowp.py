@@ -1,0 +1,161 @@
+"""Parity of the tensor-core paths (BF16 and FP8-E4M3 with per-row scales)
+against the FP64 oracle run on the same dequantised values the GPU saw.
+
+The bin step runs on the stored (rounded) rows and queries; the final values
+are FP32 scores of the FP32 rows (re-rank). The oracle mirrors both steps.
+Tolerance: rel 1e-2 of the natural score scale for the bin step (BF16/FP8),
+rel 1e-5 for re-ranked FP32 values."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2206_14286_gb300 import synth
+from tests import parity as PT
+from tests.gpu_util import db, dev, host
+
+pytestmark = pytest.mark.gpu
+METRICS = ["ip", "l2", "cos"]
+
+
+def rng(seed):
+    return np.random.Generator(np.random.PCG64(seed))
+
+
+def inputs(N, M, D, seed=0):
+    g = rng(seed)
+    return g.standard_normal((N, D)).astype(np.float32), g.standard_normal((M, D)).astype(np.float32)
+
+
+def stored(A, metric, dtype):
+    """(dequantised stored rows, FP32 rows used by the re-rank) per the oracle."""
+    src = oracle.normalize_rows(A) if metric == "cos" else A.astype(np.float32)
+    if dtype == "bf16":
+        return oracle.bf16_round(src), src.astype(np.float64)
+    deq, _ = oracle.e4m3_rows(src)
+    return deq, src.astype(np.float64)
+
+
+def om(metric):
+    return "ip" if metric == "cos" else metric
+
+
+# ----------------------------------------------------------------------------
+# PartialReduce alone
+# ----------------------------------------------------------------------------
+@pytest.mark.parametrize("dtype", ["bf16", "e4m3"])
+@pytest.mark.parametrize("metric", METRICS)
+@pytest.mark.parametrize("shape", [(3001, 70, 72), (5000, 300, 128), (2500, 40, 256), (700, 9, 16)])
+def test_partial_reduce_lowp(dtype, metric, shape):
+    N, M, D = shape
+    X, Q = inputs(N, M, D, seed=N + M)
+    Xs, _ = stored(X, metric, dtype)
+    Qs, _ = stored(Q, metric, dtype)
+    d = db(X, metric, dtype)
+    Sm = PT.score_matrix(Qs, Xs, om(metric))
+    for L in (1, 5, 100, 128, 300, N):
+        V, A = d.partial_reduce(dev(Q), L)
+        V, A = host(V).astype(np.float64), host(A)
+        Vo, Ao = oracle.partial_reduce(Qs, Xs, L, om(metric))
+        if metric == "l2":
+            Vo = (Vo + (Qs ** 2).sum(1)[:, None]) / 2.0
+        if dtype == "e4m3" and metric != "l2":
+            # the kernel leaves the per-query scale out of the value
+            _, qsc = oracle.e4m3_rows(oracle.normalize_rows(Q) if metric == "cos" else Q)
+            Vo = Vo / qsc[:, None].astype(np.float64)
+        scale = PT.query_scale(Qs, Xs, metric)
+        tol_bin = PT.REL_LOWP * scale
+        best, second = PT.bin_best_second(Sm, L)
+        decided = (best - second) > 2 * tol_bin[:, None]
+        assert np.all(A % L == np.arange(L)[None, :])
+        np.testing.assert_array_equal(A[decided], Ao[decided])
+        # values: FP32 accumulation plus the packed key's truncation (< 2^-10 relative)
+        vs = Vo if not (dtype == "e4m3" and metric != "l2") else Vo
+        tight = 2.0 ** -9 * np.abs(vs) + 1e-5 * (scale[:, None] if metric != "l2" else scale[:, None])
+        if dtype == "e4m3" and metric != "l2":
+            tight = 2.0 ** -9 * np.abs(vs) + 1e-5 * scale[:, None] / qsc[:, None]
+        err = np.abs(V - Vo)
+        # undecided bins may hold a different near-best member: compare by its own score
+        own = Sm[np.arange(M)[:, None], A]
+        if metric == "l2":
+            own = (own + (Qs ** 2).sum(1)[:, None]) / 2.0
+        if dtype == "e4m3" and metric != "l2":
+            own = own / qsc[:, None]
+        assert np.all(err[decided] <= tight[decided]), (L, err[decided].max())
+        assert np.all(np.abs(V - own) <= tight), (L,)
+
+
+# ----------------------------------------------------------------------------
+# Search with FP32 re-rank
+# ----------------------------------------------------------------------------
+def run_lowp(X, Q, metric, dtype, K, L, rerank):
+    d = db(X, metric, dtype)
+    val, idx = d.search(dev(Q), K, L=L, rerank=rerank)
+    gv, gi = host(val), host(idx)
+    Xs, Xf = stored(X, metric, dtype)
+    Qs, Qf = stored(Q, metric, dtype)
+    Kp = min(max(1, rerank) * K, L)
+    V, A = oracle.partial_reduce(Qs, Xs, L, om(metric))
+    _, cand = oracle.topk_pairs(V, A, Kp)
+    ov, oi = oracle.rerank(Qf, Xf, cand, K, om(metric))
+    S_lp = PT.score_matrix(Qs, Xs, om(metric))
+    S_f = PT.score_matrix(Qf, Xf, om(metric))
+    tol_lp = PT.REL_LOWP * PT.query_scale(Qs, Xs, metric)
+    tol_f = PT.REL_F32 * PT.query_scale(Qf, Xf, metric)
+    dec = PT.decided_mask(S_lp, L, Kp, S_f, cand, K, np.maximum(tol_lp, 0))
+    # values are FP32 re-ranked: check them at the FP32 tolerance where decided
+    frac = PT.check_search(gv, gi, ov, oi, S_lp, S_f, L, om(metric), np.maximum(tol_f, tol_lp), dec)
+    dd = dec
+    np.testing.assert_allclose(gv[dd], ov[dd], rtol=0, atol=float(np.max(tol_f)) + 1e-6)
+    return frac, gi
+
+
+@pytest.mark.parametrize("dtype", ["bf16", "e4m3"])
+@pytest.mark.parametrize("metric", METRICS)
+def test_search_lowp_small(dtype, metric):
+    X, Q = inputs(6007, 131, 64, seed=21)
+    for K, L, rr in [(10, 176, 2), (10, 256, 1), (4, 4, 1), (1, 1, 1), (8, 6007, 1)]:
+        frac, _ = run_lowp(X, Q, metric, dtype, K, L, rr)
+        assert frac > 0.5, (K, L, rr, frac)
+
+
+def test_search_bf16_mixture_l2_1m_sampled():
+    """BF16 / L2 / 1M x 128 Gaussian mixture, M = 1024, K = 10, L from recall 0.95
+    (rounded to the 128-row tile): parity and recall on sampled queries."""
+    w = synth.workload("mix_l2_1m")
+    X, Q = w["X"], w["Q"]
+    from paper_2206_14286_gb300 import search as S
+    L = S.plan_bins(X.shape[0], 10, 0.95, round_to=128)
+    d = db(X, "l2", "bf16")
+    val, idx = d.search(dev(Q), 10, L=L, rerank=2)
+    gv, gi = host(val), host(idx)
+    samp = rng(5).choice(Q.shape[0], size=24, replace=False)
+    Xs = oracle.bf16_round(X)
+    Qs = oracle.bf16_round(Q[samp])
+    V, A = oracle.partial_reduce(Qs, Xs, L, "l2")
+    _, cand = oracle.topk_pairs(V, A, 20)
+    ov, oi = oracle.rerank(Q[samp], X, cand, 10, "l2")
+    agree = np.mean([len(set(gi[s]) & set(oi[k])) / 10 for k, s in enumerate(samp)])
+    assert agree > 0.97
+    np.testing.assert_allclose(np.sort(gv[samp], 1), np.sort(ov, 1), rtol=1e-4, atol=1e-3)
+    ev, ei = oracle.exact_topk(Q[samp], X, 10, "l2")
+    rec = np.mean([len(set(gi[s]) & set(ei[k])) / 10 for k, s in enumerate(samp)])
+    assert rec >= 0.9   # expected ~0.98 (exact law at L=256), sampled
+
+
+@pytest.mark.parametrize("dtype", ["bf16", "e4m3"])
+@pytest.mark.parametrize("metric", ["ip", "l2"])
+def test_exact_search_lowp(dtype, metric):
+    X, Q = inputs(9000, 150, 96, seed=22)
+    d = db(X, metric, dtype)
+    val, idx = d.search_exact(dev(Q), 7)
+    gv, gi = host(val), host(idx)
+    Xs, Xf = stored(X, metric, dtype)
+    Qs, Qf = stored(Q, metric, dtype)
+    _, cand = oracle.exact_topk(Qs, Xs, 7, metric)
+    ov, oi = oracle.rerank(Qf, Xf, cand, 7, metric)
+    S_lp = PT.score_matrix(Qs, Xs, metric)
+    S_f = PT.score_matrix(Qf, Xf, metric)
+    tol = PT.REL_LOWP * PT.query_scale(Qs, Xs, metric)
+    dec = PT.decided_mask(S_lp, 9000, 7, S_f, cand, 7, tol)
+    PT.check_search(gv, gi, ov, oi, S_lp, S_f, 9000, metric, tol, dec)
