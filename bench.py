@@ -1,0 +1,346 @@
+#!/usr/bin/env python
+"""Benchmark of the fused search: queries/s at recall@10 >= 0.95.
+
+One step = one knn_search call over the whole query batch: query preparation,
+fused BF16 contraction + PartialReduce (tcgen05), ExactRescoring top-2K, FP32
+re-rank to the top K. Default workload: 1,000,000 x 128 database rows from a
+256-centre Gaussian mixture, 1024 queries from the same mixture, L2 metric,
+K = 10, L from the recall law for 0.95 rounded up to the 128-row tile.
+
+Reported beside it: the plain FP32 path (SIMT contraction, same workload),
+recall@10 against the exact FP32 search, p50/p99 step latency, the end-to-end
+rate through the host-buffer entry point, the dominant kernel's roofline and
+the FP64 CPU oracle timed on a bounded sample.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+Multi-GPU (torchrun): every rank runs an independent replica (the search does
+not shard on one box); the value is the total over ranks.
+"""
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="mix_l2_1m")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--fp32-steps", type=int, default=10)
+    return ap.parse_args()
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d, "measured"
+    return PEAKS_FALLBACK, "fallback"
+
+
+# ----------------------------------------------------------------------------
+# nvidia-smi clock sampling during the timed region
+# ----------------------------------------------------------------------------
+class Clocks:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(index), "--query-gpu=" + self.Q,
+                                       "--format=csv,noheader,nounits", "-lms", "100"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+        time.sleep(0.3)
+
+    def stop(self):
+        if self.p is None:
+            return None
+        time.sleep(0.2)
+        self.p.terminate()
+        self.p.wait()
+        self.f.flush()
+        rows = []
+        for line in open(self.f.name):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), parts[5:9]))
+            except ValueError:
+                continue
+        os.unlink(self.f.name)
+        if not rows:
+            return None
+        mx = max(r[1] for r in rows)
+        loaded = [r for r in rows if r[0] > 0.5 * mx] or rows
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[2][k].lower() == "active"})
+        return {"sm_mhz": statistics.median(r[0] for r in loaded), "sm_max_mhz": mx,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ----------------------------------------------------------------------------
+# CPU oracle (baseline and the reference arm)
+# ----------------------------------------------------------------------------
+def oracle_sample_rate(w, L, K, target_s=12.0, max_queries=None):
+    """Queries/s of the FP64 oracle running the same method on a bounded sample."""
+    import oracle
+    X, Q = w["X"], w["Q"]
+    Xs = oracle.bf16_round(X) if w["dtype"] == "bf16" else X.astype(np.float64)
+    metric = w["metric"]
+
+    def run(n):
+        Qs = oracle.bf16_round(Q[:n]) if w["dtype"] == "bf16" else Q[:n].astype(np.float64)
+        t0 = time.perf_counter()
+        V, A = oracle.partial_reduce(Qs, Xs, L, metric)
+        _, cand = oracle.topk_pairs(V, A, 2 * K)
+        oracle.rerank(Q[:n], X, cand, K, metric)
+        return time.perf_counter() - t0
+
+    t = run(8)
+    n = int(max(8, min(max_queries or Q.shape[0], target_s / max(t / 8, 1e-6))))
+    n = min(n, Q.shape[0])
+    t = run(n)
+    return n / t, n, t
+
+
+# ----------------------------------------------------------------------------
+def main():
+    args = parse()
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    from paper_2206_14286_gb300 import synth
+
+    if args.impl == "reference":
+        if rank != 0:
+            return 0
+        import oracle
+        oracle.build()
+        from oracle import recall as R
+        w = synth.workload(args.workload)
+        K = w["K"]
+        L = min(w["X"].shape[0], -(-R.min_bins(K, w["recall"]) // 128) * 128)
+        per = []
+        nq = 0
+        budget = max(1.0, 150.0 / max(1, args.steps + args.warmup))
+        for s in range(args.warmup + args.steps):
+            rate, n, t = oracle_sample_rate(w, L, K, target_s=budget, max_queries=256)
+            if s >= args.warmup:
+                per.append((n, t))
+                nq += n
+        tot = sum(t for _, t in per)
+        value = nq / tot
+        cores = os.cpu_count()
+        line = {"impl": "reference", "metric": "queries/s at recall@10>=0.95", "value": value,
+                "unit": "queries/s", "n_gpus": args.gpus, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": 1e3 * tot / len(per),
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                "data": "synthetic", "config": config_of(w, L),
+                "cpu_baseline": {"value": value, "unit": "queries/s", "cores": cores,
+                                 "kind": "oracle",
+                                 "sample": "%d queries per step of the %d-query batch, full %d-row database"
+                                           % (per[0][0], w["Q"].shape[0], w["X"].shape[0])},
+                "e2e": {"value": value, "unit": "queries/s", "h2d_bytes_per_step": 0,
+                        "d2h_bytes_per_step": 0}}
+        print(json.dumps(line))
+        return 0
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2206_14286_gb300 import search as S
+    from paper_2206_14286_gb300 import _lib
+    lib = _lib.get()
+
+    w = synth.workload(args.workload)
+    X, Q, K, metric = w["X"], w["Q"], w["K"], w["metric"]
+    N, D = X.shape
+    M = Q.shape[0]
+    L = S.plan_bins(N, K, w["recall"], round_to=128)
+    L_min = S.plan_bins(N, K, w["recall"])
+    rerank = w.get("rerank", 2)
+    Xd = torch.from_numpy(X).cuda()
+    Qd = torch.from_numpy(Q).cuda()
+    db = S.Database(Xd, metric=metric, dtype=w["dtype"], keep_f32=True)
+    val = torch.empty((M, K), dtype=torch.float32, device="cuda")
+    idx = torch.empty((M, K), dtype=torch.int32, device="cuda")
+
+    def step():
+        db.search(Qd, K, L=L, rerank=rerank, out=(val, idx))
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+    S.sync_status()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+
+    _lib.check(lib.knn_profile_enable(1))
+    clocks = Clocks(local)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
+    for a, b in evs:
+        a.record()
+        step()
+        b.record()
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    _lib.check(lib.knn_profile_enable(0))
+    step_ms = [a.elapsed_time(b) for a, b in evs]
+    total_ms = evs[0][0].elapsed_time(evs[-1][1])
+    t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    total_ms = float(t.item())
+    value = world * M * args.steps / (total_ms / 1e3)
+
+    prof = {}
+    import ctypes
+    for c, name in enumerate(["prep", "k1_partial_reduce", "k2_rescoring", "k3_rerank"]):
+        tot = ctypes.c_double()
+        n = ctypes.c_int64()
+        _lib.check(lib.knn_profile_read(c, ctypes.byref(tot), ctypes.byref(n)))
+        prof[name] = {"ms_avg": tot.value / max(1, n.value), "launches": n.value}
+    S.sync_status()
+
+    # recall@10 against the exact FP32 search on the same data
+    dbx = S.Database(Xd, metric=metric, dtype="f32", keep_f32=True)
+    _, ei = dbx.search_exact(Qd, K)
+    gi = idx.cpu().numpy()
+    ei = ei.cpu().numpy()
+    recall = float(np.mean([len(set(gi[i]) & set(ei[i])) / K for i in range(M)]))
+
+    # the plain FP32 path on the same workload
+    def step32():
+        dbx.search(Qd, K, L=L, rerank=rerank)
+    for _ in range(2):
+        step32()
+    torch.cuda.synchronize()
+    a32, b32 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a32.record()
+    for _ in range(args.fp32_steps):
+        step32()
+    b32.record()
+    torch.cuda.synchronize()
+    ms32 = a32.elapsed_time(b32) / args.fp32_steps
+    v32, i32 = dbx.search(Qd, K, L=L, rerank=rerank)
+    i32 = i32.cpu().numpy()
+    recall32 = float(np.mean([len(set(i32[i]) & set(ei[i])) / K for i in range(M)]))
+    del dbx
+
+    # end to end through the host-buffer entry point (pinned buffers)
+    qh = torch.from_numpy(Q).pin_memory()
+    vh = torch.empty((M, K), dtype=torch.float32, pin_memory=True)
+    ih = torch.empty((M, K), dtype=torch.int32, pin_memory=True)
+    for _ in range(3):
+        db.search_host(qh, K, L=L, rerank=rerank, out=(vh, ih))
+    e2e_steps = max(5, args.steps)
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        db.search_host(qh, K, L=L, rerank=rerank, out=(vh, ih))
+    e2e_s = time.perf_counter() - t0
+    e2e = {"value": world * M * e2e_steps / e2e_s, "unit": "queries/s",
+           "h2d_bytes_per_step": int(M * D * 4), "d2h_bytes_per_step": int(M * K * 8)}
+
+    # roofline of the dominant kernel (K1)
+    pk, pk_kind = peaks()
+    k1_ms = prof["k1_partial_reduce"]["ms_avg"]
+    flops = 2.0 * M * N * D
+    achieved = flops / (k1_ms / 1e3) / 1e12
+    peak = pk["bf16_tflops"]
+    k1_bytes = N * D * 2 + (N * 4 if metric == "l2" else 0) + M * D * 2
+    traffic = k1_traffic(M, N, D)
+    roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": achieved / peak, "traffic": traffic,
+            "peak_source": "%s bf16 dense burst (MEASURED_PEAKS.json)" % pk_kind,
+            "kernel": "k1_tc_kernel (fused BF16 contraction + PartialReduce)",
+            "algorithmic": "2*M*N*D = %.4g FLOP per launch" % flops,
+            "hbm_context": {"algorithmic_bytes": k1_bytes,
+                            "achieved_gbs": k1_bytes / (k1_ms / 1e3) / 1e9,
+                            "peak_gbs": pk["hbm_gbs"]}}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+        oracle.build()
+        rate, n, tt = oracle_sample_rate(w, L, K, target_s=12.0)
+        cpu = {"value": rate, "unit": "queries/s", "cores": os.cpu_count(), "kind": "oracle",
+               "sample": "%d of the %d queries against the full %d-row database (FP64), %.1f s"
+                         % (n, M, N, tt)}
+
+    if rank == 0:
+        sm = sorted(step_ms)
+        line = {"metric": "queries/s at recall@10>=0.95 (fused BF16; plain FP32 alongside)",
+                "value": value, "unit": "queries/s", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "bf16", "data": "synthetic", "config": config_of(w, L, L_min),
+                "recall_at_10": recall,
+                "p50_ms": sm[len(sm) // 2], "p99_ms": sm[min(len(sm) - 1, int(0.99 * len(sm)))],
+                "fp32_path": {"value": world * M / (ms32 / 1e3), "unit": "queries/s",
+                              "ms_per_step": ms32, "recall_at_10": recall32},
+                "kernels": prof, "roofline": roof, "e2e": e2e,
+                "gpu_launches": 4 * args.steps, "clocks": clk, "cpu_baseline": cpu}
+        print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def config_of(w, L, L_min=None):
+    X, Q = w["X"], w["Q"]
+    return {"workload": "gaussian-mixture-256c L2 N=%d D=%d M=%d K=%d" % (X.shape[0], X.shape[1],
+                                                                          Q.shape[0], w["K"]),
+            "N": X.shape[0], "D": X.shape[1], "global_batch": Q.shape[0], "K": w["K"],
+            "L": L, "L_min_eq14": L_min, "metric": w["metric"], "rerank": "FP32 top-%dK" % w.get("rerank", 2),
+            "l2_flush": "inputs larger than L2 (database %d MB in BF16 streamed every step)"
+                        % (X.shape[0] * X.shape[1] * 2 // 2 ** 20),
+            "parallelism": "replicas"}
+
+
+def k1_traffic(M, N, D):
+    """DRAM bytes per K1 launch from the committed ncu summary, if it was taken
+    on the current kernel source (else None)."""
+    p = os.path.join(ROOT, "profiles", "k1_tc_traffic.json")
+    src = os.path.join(ROOT, "paper_2206_14286_gb300", "csrc", "k1_tc.cu")
+    if not os.path.exists(p):
+        return None
+    d = json.load(open(p))
+    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    if d.get("k1_tc_sha") != h:
+        return None
+    if d.get("M") != M or d.get("D") != D:
+        return None
+    # the database stream dominates: scale by the rows of the launch
+    return d["dram_bytes_per_launch"] * N / d["N"]
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -202,6 +202,19 @@ knn_status knn_backward(const void* db_lp, const float* db_scale, const float* x
 
 size_t knn_backward_workspace(int64_t N, int32_t D, int64_t M, int32_t K, int32_t deterministic);
 
+/*
+ * Measurement aid (no counterpart in the paper): while enabled, every search
+ * call records a pair of CUDA events on its stream around each of its kernel
+ * classes: 0 = query preparation, 1 = PartialReduce (K1), 2 = ExactRescoring
+ * (K2), 3 = re-rank (K3). knn_profile_enable(1) (re)starts the record and
+ * creates the events; knn_profile_enable(0) stops recording. knn_profile_read
+ * synchronises on the recorded events and returns the summed elapsed time in
+ * milliseconds and the number of launches of one class (at most 16384 are
+ * kept per class). Not thread-safe with concurrent searches.
+ */
+knn_status knn_profile_enable(int32_t on);
+knn_status knn_profile_read(int32_t kernel_class, double* total_ms, int64_t* launches);
+
 /* Synchronise the current device and report a device-side wait timeout
  * (KNN_ETIMEOUT, flag then cleared) or a CUDA error (KNN_ECUDA). */
 knn_status knn_sync_status(void);

@@ -38,6 +38,8 @@ SIGNATURES = {
                                     I32, P, SZ, P]),
     "knn_backward_workspace": (SZ, [I64, I32, I64, I32, I32]),
     "knn_sync_status": (ctypes.c_int, []),
+    "knn_profile_enable": (ctypes.c_int, [I32]),
+    "knn_profile_read": (ctypes.c_int, [I32, P, P]),
 }
 
 _lib = None

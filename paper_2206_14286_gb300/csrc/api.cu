@@ -2,6 +2,7 @@
 // (Eq. 13-14), work decomposition, workspace layout and kernel launches.
 #include <cmath>
 #include <cstring>
+#include <new>
 
 #include "common.cuh"
 #include "kernels.h"
@@ -33,6 +34,31 @@ int device_sm_count() {
 }  // namespace tpuknn
 
 namespace {
+
+// ---------------------------------------------------------------------------
+// Event pairs around kernel classes (knn_profile_*).
+// ---------------------------------------------------------------------------
+constexpr int kProfClasses = 4, kProfCap = 16384;
+struct Profiler {
+  bool on = false;
+  cudaEvent_t* ev[kProfClasses] = {nullptr, nullptr, nullptr, nullptr};  // 2 * kProfCap each
+  int64_t n[kProfClasses] = {0, 0, 0, 0};
+} g_prof;
+
+struct ProfScope {
+  int cls;
+  cudaStream_t st;
+  int64_t slot;
+  ProfScope(int c, cudaStream_t s) : cls(c), st(s), slot(-1) {
+    if (g_prof.on && g_prof.ev[c] && g_prof.n[c] < kProfCap) {
+      slot = g_prof.n[c]++;
+      cudaEventRecord(g_prof.ev[c][2 * slot], st);
+    }
+  }
+  ~ProfScope() {
+    if (slot >= 0) cudaEventRecord(g_prof.ev[cls][2 * slot + 1], st);
+  }
+};
 
 constexpr size_t kAlign = 256;
 inline size_t al(size_t x) { return (x + kAlign - 1) & ~(kAlign - 1); }
@@ -267,19 +293,32 @@ knn_status search_impl(const SearchArgs& a, float* out_val, int32_t* out_idx, vo
   char* ws = reinterpret_cast<char*>(workspace);
   const float* qf32;
   int64_t q_stride;
-  cudaError_t e = prep_queries(a, s, ws, &qf32, &q_stride, st);
+  cudaError_t e;
+  {
+    ProfScope ps(0, st);
+    e = prep_queries(a, s, ws, &qf32, &q_stride, st);
+  }
   if (e != cudaSuccess) return cuda_status(e);
   Partials parts{reinterpret_cast<float*>(ws + s.off_part_v),
                  a.dtype == KNN_F32 ? reinterpret_cast<int32_t*>(ws + s.off_part_a) : nullptr, 0};
   const float* qscale = s.qb.scale ? reinterpret_cast<const float*>(ws + s.off_qscale) : nullptr;
-  e = run_k1(s.plan, a, a.db_lp, a.db_scale, a.db_hnorm, ws + s.off_qlp, qscale, parts, st);
+  {
+    ProfScope ps(1, st);
+    e = run_k1(s.plan, a, a.db_lp, a.db_scale, a.db_hnorm, ws + s.off_qlp, qscale, parts, st);
+  }
   if (e == cudaErrorNotSupported) return KNN_EUNSUPPORTED;
   if (e != cudaSuccess) return cuda_status(e);
   uint64_t* cand = reinterpret_cast<uint64_t*>(ws + s.off_cand);
-  e = launch_k2(s.plan, parts, s.Kp, nullptr, cand, st);
+  {
+    ProfScope ps(2, st);
+    e = launch_k2(s.plan, parts, s.Kp, nullptr, cand, st);
+  }
   if (e != cudaSuccess) return cuda_status(e);
-  e = launch_k3(a.M, a.D, a.metric, cand, s.Kp, a.K, qf32, q_stride, a.db_f32, a.db_lp, a.dtype,
-                s.plan.pitch, a.db_scale, a.N, out_val, out_idx, st);
+  {
+    ProfScope ps(3, st);
+    e = launch_k3(a.M, a.D, a.metric, cand, s.Kp, a.K, qf32, q_stride, a.db_f32, a.db_lp,
+                  a.dtype, s.plan.pitch, a.db_scale, a.N, out_val, out_idx, st);
+  }
   return cuda_status(e);
 }
 
@@ -559,6 +598,44 @@ knn_status knn_backward(const void* db_lp, const float* db_scale, const float* x
   return cuda_status(launch_backward(M, D, K, metric, q, x_f32, db_lp, dtype, knn_row_pitch(D),
                                      db_scale, N, idx, grad_val, dq, dx, zero_dx, deterministic,
                                      workspace, (cudaStream_t)stream));
+}
+
+knn_status knn_profile_enable(int32_t on) {
+  g_prof.on = false;
+  if (!on) return KNN_OK;
+  for (int c = 0; c < kProfClasses; ++c) {
+    if (!g_prof.ev[c]) {
+      cudaEvent_t* ev = new (std::nothrow) cudaEvent_t[2 * kProfCap];
+      if (!ev) return KNN_ENOMEM;
+      for (int i = 0; i < 2 * kProfCap; ++i) {
+        cudaError_t e = cudaEventCreate(&ev[i]);
+        if (e != cudaSuccess) return cuda_status(e);
+      }
+      g_prof.ev[c] = ev;
+    }
+    g_prof.n[c] = 0;
+  }
+  g_prof.on = true;
+  return KNN_OK;
+}
+
+knn_status knn_profile_read(int32_t kernel_class, double* total_ms, int64_t* launches) {
+  if (kernel_class < 0 || kernel_class >= kProfClasses || !total_ms || !launches)
+    return KNN_EINVAL;
+  double t = 0.0;
+  const int64_t n = g_prof.n[kernel_class];
+  for (int64_t i = 0; i < n; ++i) {
+    float ms = 0.f;
+    cudaError_t e = cudaEventSynchronize(g_prof.ev[kernel_class][2 * i + 1]);
+    if (e == cudaSuccess)
+      e = cudaEventElapsedTime(&ms, g_prof.ev[kernel_class][2 * i],
+                               g_prof.ev[kernel_class][2 * i + 1]);
+    if (e != cudaSuccess) return cuda_status(e);
+    t += ms;
+  }
+  *total_ms = t;
+  *launches = n;
+  return KNN_OK;
 }
 
 knn_status knn_sync_status(void) {

@@ -100,13 +100,21 @@ def run_lowp(X, Q, metric, dtype, K, L, rerank):
     ov, oi = oracle.rerank(Qf, Xf, cand, K, om(metric))
     S_lp = PT.score_matrix(Qs, Xs, om(metric))
     S_f = PT.score_matrix(Qf, Xf, om(metric))
-    tol_lp = PT.REL_LOWP * PT.query_scale(Qs, Xs, metric)
+    scale_lp = PT.query_scale(Qs, Xs, metric)
+    tol_lp = PT.REL_LOWP * scale_lp
     tol_f = PT.REL_F32 * PT.query_scale(Qf, Xf, metric)
-    dec = PT.decided_mask(S_lp, L, Kp, S_f, cand, K, np.maximum(tol_lp, 0))
-    # values are FP32 re-ranked: check them at the FP32 tolerance where decided
-    frac = PT.check_search(gv, gi, ov, oi, S_lp, S_f, L, om(metric), np.maximum(tol_f, tol_lp), dec)
-    dd = dec
-    np.testing.assert_allclose(gv[dd], ov[dd], rtol=0, atol=float(np.max(tol_f)) + 1e-6)
+    # the stated rule: rel 1e-2 (BF16/FP8) for the bin step
+    dec = PT.decided_mask(S_lp, L, Kp, S_f, cand, K, tol_lp)
+    PT.check_search(gv, gi, ov, oi, S_lp, S_f, L, om(metric), tol_lp, dec)
+    # a stricter rule derived from the kernel's arithmetic: the packed key keeps
+    # scores to 2^-10 of their magnitude, FP32 accumulation adds ~D u ||q|| ||x||
+    tol_d = 2.0 ** -9 * (scale_lp if metric == "l2" else np.abs(S_lp).max(1)) + 3e-5 * scale_lp
+    tol_df = np.maximum(tol_f, 3e-5 * PT.query_scale(Qf, Xf, metric))
+    dec2 = PT.decided_mask(S_lp, L, Kp, S_f, cand, K, tol_d) & \
+        PT.decided_mask(S_f, L, Kp, S_f, cand, K, tol_df) | dec
+    frac = PT.check_search(gv, gi, ov, oi, S_lp, S_f, L, om(metric), np.maximum(tol_d, tol_df), dec2)
+    # values are FP32 re-ranked: FP32 tolerance where decided
+    np.testing.assert_allclose(gv[dec2], ov[dec2], rtol=0, atol=float(np.max(tol_df)) + 1e-6)
     return frac, gi
 
 
