@@ -102,26 +102,32 @@ class Clocks:
 # ----------------------------------------------------------------------------
 # CPU oracle (baseline and the reference arm)
 # ----------------------------------------------------------------------------
-def oracle_sample_rate(w, L, K, target_s=12.0, max_queries=None):
-    """Queries/s of the FP64 oracle running the same method on a bounded sample."""
-    import oracle
-    X, Q = w["X"], w["Q"]
-    Xs = oracle.bf16_round(X) if w["dtype"] == "bf16" else X.astype(np.float64)
-    metric = w["metric"]
+class OracleRunner:
+    """The FP64 oracle running the same method (PartialReduce, top-2K, re-rank)
+    on a bounded sample of the workload's queries."""
 
-    def run(n):
-        Qs = oracle.bf16_round(Q[:n]) if w["dtype"] == "bf16" else Q[:n].astype(np.float64)
+    def __init__(self, w, L, K):
+        import oracle
+        self.o = oracle
+        self.X, self.Q, self.L, self.K, self.metric = w["X"], w["Q"], L, K, w["metric"]
+        self.lowp = w["dtype"] == "bf16"
+        self.Xs = oracle.bf16_round(self.X) if self.lowp else self.X.astype(np.float64)
+        self.cursor = 0
+
+    def run(self, n):
+        o = self.o
+        q = np.take(self.Q, np.arange(self.cursor, self.cursor + n) % self.Q.shape[0], axis=0)
+        self.cursor = (self.cursor + n) % self.Q.shape[0]
+        Qs = o.bf16_round(q) if self.lowp else q.astype(np.float64)
         t0 = time.perf_counter()
-        V, A = oracle.partial_reduce(Qs, Xs, L, metric)
-        _, cand = oracle.topk_pairs(V, A, 2 * K)
-        oracle.rerank(Q[:n], X, cand, K, metric)
+        V, A = o.partial_reduce(Qs, self.Xs, self.L, self.metric)
+        _, cand = o.topk_pairs(V, A, 2 * self.K)
+        o.rerank(q, self.X, cand, self.K, self.metric)
         return time.perf_counter() - t0
 
-    t = run(8)
-    n = int(max(8, min(max_queries or Q.shape[0], target_s / max(t / 8, 1e-6))))
-    n = min(n, Q.shape[0])
-    t = run(n)
-    return n / t, n, t
+    def size_for(self, seconds, cap):
+        t = self.run(8)
+        return int(max(8, min(cap, seconds / max(t / 8, 1e-6))))
 
 
 # ----------------------------------------------------------------------------
@@ -144,11 +150,12 @@ def main():
         w = synth.workload(args.workload)
         K = w["K"]
         L = min(w["X"].shape[0], -(-R.min_bins(K, w["recall"]) // 128) * 128)
+        runner = OracleRunner(w, L, K)
+        n = runner.size_for(max(0.5, 120.0 / max(1, args.steps + args.warmup)), 256)
         per = []
         nq = 0
-        budget = max(1.0, 150.0 / max(1, args.steps + args.warmup))
         for s in range(args.warmup + args.steps):
-            rate, n, t = oracle_sample_rate(w, L, K, target_s=budget, max_queries=256)
+            t = runner.run(n)
             if s >= args.warmup:
                 per.append((n, t))
                 nq += n
@@ -290,7 +297,10 @@ def main():
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import oracle
         oracle.build()
-        rate, n, tt = oracle_sample_rate(w, L, K, target_s=12.0)
+        runner = OracleRunner(w, L, K)
+        n = runner.size_for(12.0, M)
+        tt = runner.run(n)
+        rate = n / tt
         cpu = {"value": rate, "unit": "queries/s", "cores": os.cpu_count(), "kind": "oracle",
                "sample": "%d of the %d queries against the full %d-row database (FP64), %.1f s"
                          % (n, M, N, tt)}
