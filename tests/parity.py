@@ -74,8 +74,11 @@ def bin_best_second(S, L):
     return P[:, 0, :], np.full((M, L), -np.inf)
 
 
-def decided_mask(S_lp, L, Kp, S_f32, cand, K, tol):
-    """Boolean per query; cand = the oracle's Kp candidates (M x Kp)."""
+def decided_mask(S_lp, L, Kp, S_f32, cand, K, tol, tol_final=None):
+    """Boolean per query; cand = the oracle's Kp candidates (M x Kp).
+    tol applies to the bin step, tol_final (default tol) to the FP32 order."""
+    if tol_final is None:
+        tol_final = tol
     M = S_lp.shape[0]
     ok = np.ones(M, bool)
     best, second = bin_best_second(S_lp, L)
@@ -91,7 +94,7 @@ def decided_mask(S_lp, L, Kp, S_f32, cand, K, tol):
     upto = min(K + 1, Kp) if Kp > K else K
     if upto >= 2:
         gaps = sc[:, :upto - 1] - sc[:, 1:upto]
-        ok &= np.all(gaps > 2 * tol[:, None], axis=1)
+        ok &= np.all(gaps > 2 * tol_final[:, None], axis=1)
     return ok
 
 

@@ -110,8 +110,7 @@ def run_lowp(X, Q, metric, dtype, K, L, rerank):
     # scores to 2^-10 of their magnitude, FP32 accumulation adds ~D u ||q|| ||x||
     tol_d = 2.0 ** -9 * (scale_lp if metric == "l2" else np.abs(S_lp).max(1)) + 3e-5 * scale_lp
     tol_df = np.maximum(tol_f, 3e-5 * PT.query_scale(Qf, Xf, metric))
-    dec2 = PT.decided_mask(S_lp, L, Kp, S_f, cand, K, tol_d) & \
-        PT.decided_mask(S_f, L, Kp, S_f, cand, K, tol_df) | dec
+    dec2 = PT.decided_mask(S_lp, L, Kp, S_f, cand, K, tol_d, tol_df) | dec
     frac = PT.check_search(gv, gi, ov, oi, S_lp, S_f, L, om(metric), np.maximum(tol_d, tol_df), dec2)
     # values are FP32 re-ranked: FP32 tolerance where decided
     np.testing.assert_allclose(gv[dec2], ov[dec2], rtol=0, atol=float(np.max(tol_df)) + 1e-6)
