@@ -148,7 +148,10 @@ K1Plan make_plan(int64_t N, int64_t M, int64_t L, int D, int metric, int dtype,
   }
   p.tiles_per_split = cdiv(p.ntiles, splits);
   p.nsplits = cdiv(p.ntiles, p.tiles_per_split);
-  p.code_bits = dtype == KNN_F32 ? 0 : bits_for(p.tiles_per_split);
+  // Tensor-core partials merge in K1 (one [M][Lk] array, code = global tile
+  // ordinal) when the global ordinal fits the code; otherwise per split.
+  p.atomic_merge = dtype != KNN_F32 && force_splits <= 0 && bits_for(p.ntiles) <= kMaxCodeBits;
+  p.code_bits = dtype == KNN_F32 ? 0 : bits_for(p.atomic_merge ? p.ntiles : p.tiles_per_split);
   return p;
 }
 
@@ -229,7 +232,7 @@ knn_status layout_search(const SearchArgs& a, SearchLayout* s) {
   o += s->qb.scale;
   s->off_qf32 = o;
   o += s->qb.f32;
-  const size_t n = (size_t)(s->plan.nsplits * s->plan.M * s->plan.Lk);
+  const size_t n = (size_t)((s->plan.atomic_merge ? 1 : s->plan.nsplits) * s->plan.M * s->plan.Lk);
   s->off_part_v = o;
   o += al(n * 4);
   s->off_part_a = o;
@@ -257,8 +260,11 @@ cudaError_t prep_queries(const SearchArgs& a, const SearchLayout& s, char* ws, c
   void* qlp = ws + s.off_qlp;
   float* qscale = s.qb.scale ? reinterpret_cast<float*>(ws + s.off_qscale) : nullptr;
   float* qf = s.qb.f32 ? reinterpret_cast<float*>(ws + s.off_qf32) : nullptr;
+  // the merged partials start at zero: the same launch clears them
+  uint32_t* zbuf = s.plan.atomic_merge ? reinterpret_cast<uint32_t*>(ws + s.off_part_v) : nullptr;
+  const int64_t zn = s.plan.atomic_merge ? s.plan.M * s.plan.Lk : 0;
   cudaError_t e = launch_prep(a.q, a.M, a.D, s.plan.pitch, a.metric, a.dtype, qlp, qscale, nullptr,
-                              qf, st);
+                              qf, st, zbuf, zn);
   if (a.dtype == KNN_F32) {
     *qf32 = reinterpret_cast<const float*>(qlp);
     *q_stride = s.plan.pitch;
@@ -300,7 +306,8 @@ knn_status search_impl(const SearchArgs& a, float* out_val, int32_t* out_idx, vo
   }
   if (e != cudaSuccess) return cuda_status(e);
   Partials parts{reinterpret_cast<float*>(ws + s.off_part_v),
-                 a.dtype == KNN_F32 ? reinterpret_cast<int32_t*>(ws + s.off_part_a) : nullptr, 0};
+                 a.dtype == KNN_F32 ? reinterpret_cast<int32_t*>(ws + s.off_part_a) : nullptr, 0,
+                 s.plan.atomic_merge};
   const float* qscale = s.qb.scale ? reinterpret_cast<const float*>(ws + s.off_qscale) : nullptr;
   {
     ProfScope ps(1, st);
@@ -395,7 +402,7 @@ knn_status exact_impl(const SearchArgs& a, float* out_val, int32_t* out_idx, voi
     K1Plan p = make_plan(nc, a.M, nc, a.D, a.metric, a.dtype, 1);
     Partials parts{reinterpret_cast<float*>(ws + s.off_part_v),
                    a.dtype == KNN_F32 ? reinterpret_cast<int32_t*>(ws + s.off_part_a) : nullptr,
-                   n0};
+                   n0, false};
     const char* xlp = reinterpret_cast<const char*>(a.db_lp) + (size_t)n0 * p.pitch * esz;
     const float* xs = a.db_scale ? a.db_scale + n0 : nullptr;
     const float* hn = a.db_hnorm ? a.db_hnorm + n0 : nullptr;
@@ -547,7 +554,8 @@ knn_status knn_partial_reduce(const void* db_lp, const float* db_scale, const fl
   cudaError_t e = prep_queries(a, s, ws, &qf32, &q_stride, st);
   if (e != cudaSuccess) return cuda_status(e);
   Partials parts{reinterpret_cast<float*>(ws + s.off_part_v),
-                 dtype == KNN_F32 ? reinterpret_cast<int32_t*>(ws + s.off_part_a) : nullptr, 0};
+                 dtype == KNN_F32 ? reinterpret_cast<int32_t*>(ws + s.off_part_a) : nullptr, 0,
+                 s.plan.atomic_merge};
   const float* qscale = s.qb.scale ? reinterpret_cast<const float*>(ws + s.off_qscale) : nullptr;
   e = run_k1(s.plan, a, db_lp, db_scale, db_hnorm, ws + s.off_qlp, qscale, parts, st);
   if (e == cudaErrorNotSupported) return KNN_EUNSUPPORTED;

@@ -42,7 +42,7 @@ namespace {
 __device__ unsigned int g_tc_timeout = 0;
 constexpr uint64_t kTimeoutNs = 2000000000ull;
 constexpr int kThreads = 384;
-constexpr int kCtrlRegs = 96, kEpiRegs = 200;  // 128*96 + 256*200 <= 384*168 (launch)
+constexpr int kCtrlRegs = 88, kEpiRegs = 208;  // 128*88 + 256*208 <= 384*168 (launch)
 constexpr int kRows = 128;          // database rows per tile (MMA M)
 constexpr int kKBlockBytes = 128;   // one 128-byte swizzle span along D
 
@@ -53,6 +53,7 @@ struct TcArgs {
   int stages;
   uint32_t q_bytes, stage_bytes;
   uint32_t code_bits;
+  int atomic_merge;   // 1: red.max of order-mapped keys into part[M][Lk], code = global tile
   uint32_t idesc;
   const float* hnorm;
   const float* xscale;
@@ -157,13 +158,12 @@ __device__ __forceinline__ void tc_mma(uint32_t d_tmem, uint64_t adesc, uint64_t
         : "memory");
   }
 }
-// 32 consecutive FP32 columns of this thread's TMEM lane, waited for.
+// Start loading 32 consecutive FP32 columns of this thread's TMEM lane.
 __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
   asm volatile(
       "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
       "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
-      "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];\n\t"
-      "tcgen05.wait::ld.sync.aligned;"
+      "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
       : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
         "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
         "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
@@ -171,6 +171,19 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
         "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
       : "r"(taddr)
       : "memory");
+}
+// Wait for this thread's outstanding TMEM loads; the registers are tied to the
+// wait so no use of them can be scheduled before it.
+__device__ __forceinline__ void tmem_wait(uint32_t (&r)[32]) {
+  asm volatile("tcgen05.wait::ld.sync.aligned;"
+               : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]),
+                 "+r"(r[6]), "+r"(r[7]), "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]),
+                 "+r"(r[12]), "+r"(r[13]), "+r"(r[14]), "+r"(r[15]), "+r"(r[16]), "+r"(r[17]),
+                 "+r"(r[18]), "+r"(r[19]), "+r"(r[20]), "+r"(r[21]), "+r"(r[22]), "+r"(r[23]),
+                 "+r"(r[24]), "+r"(r[25]), "+r"(r[26]), "+r"(r[27]), "+r"(r[28]), "+r"(r[29]),
+                 "+r"(r[30]), "+r"(r[31])
+               :
+               : "memory");
 }
 
 // Shared-memory matrix descriptor of a K-major operand laid out by TMA with
@@ -312,51 +325,71 @@ k1_tc_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CU
 
   // ------------------------------------------------------------ epilogue
   asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(kEpiRegs));
+  constexpr int NC = HALF / 32;
   const int quad = warp & 3;
   const int half = (warp - 4) >> 2;
   const int lrow = quad * 32 + lane;
   const int64_t bin = strip * kRows + lrow;
+  const bool bin_ok = bin < a.Lk;
   const uint32_t mask = a.code_bits ? ((1u << a.code_bits) - 1u) : 0u;
   const uint32_t nmask = ~mask;
+  const int64_t code_t0 = a.atomic_merge ? t_begin : 0;
   float v[HALF];
 #pragma unroll
   for (int c = 0; c < HALF; ++c) v[c] = __uint_as_float(kNegInfBits);
 
+  // per-row factors of the next tile are loaded one tile ahead
+  float bias_n = 0.0f, mul_n = 1.0f;
+  {
+    const int64_t j = t_begin * a.Lk + bin;
+    if (bin_ok && j < a.N) {
+      if (METRIC == KNN_L2) bias_n = a.hnorm[j];
+      if (DT == KNN_E4M3) mul_n = a.xscale[j];
+    }
+  }
   for (int it = 0; it < nt; ++it) {
     const int ab = it & 1;
     const uint32_t aph = (uint32_t)((it >> 1) & 1);
+    const int64_t j = (t_begin + it) * a.Lk + bin;
+    const bool valid = bin_ok && (j < a.N);
+    const float bias = bias_n, mul = mul_n;
+    if (it + 1 < nt) {
+      const int64_t jn = j + a.Lk;
+      if (bin_ok && jn < a.N) {
+        if (METRIC == KNN_L2) bias_n = a.hnorm[jn];
+        if (DT == KNN_E4M3) mul_n = a.xscale[jn];
+      }
+    }
     if (!mbar_wait(b_accf + 8 * ab, aph, abort_flag)) break;
     tc_fence_after();
-    const int64_t j = (t_begin + it) * a.Lk + bin;
-    const bool valid = (bin < a.Lk) && (j < a.N);
-    float bias = 0.0f, mul = 1.0f;
-    if (valid) {
-      if (METRIC == KNN_L2) bias = a.hnorm[j];
-      if (DT == KNN_E4M3) mul = a.xscale[j];
-    }
-    const uint32_t code = mask - (uint32_t)it;
+    // invalid lanes turn every key into -inf: no divergence, no extra select
+    const uint32_t km = valid ? nmask : 0u;
+    const uint32_t kc = valid ? (mask - (uint32_t)(code_t0 + it)) : kNegInfBits;
     const uint32_t col0 =
         tmem_base + ((uint32_t)(quad * 32) << 16) + (uint32_t)(ab * BQ + half * HALF);
+    uint32_t ra[32], rb[32];
+    tmem_ld32(col0, ra);
+    tmem_wait(ra);
 #pragma unroll
-    for (int c = 0; c < HALF / 32; ++c) {
-      uint32_t r[32];
-      tmem_ld32(col0 + c * 32, r);
-      if (valid) {
+    for (int c = 0; c < NC; ++c) {
+      uint32_t(&cur)[32] = (c & 1) ? rb : ra;
+      uint32_t(&nxt)[32] = (c & 1) ? ra : rb;
+      if (c + 1 < NC) tmem_ld32(col0 + (uint32_t)((c + 1) * 32), nxt);
 #pragma unroll
-        for (int k = 0; k < 32; ++k) {
-          float sc = __uint_as_float(r[k]);
-          if (DT == KNN_E4M3) {
-            if (METRIC == KNN_L2)
-              sc = fmaf(sc, mul * s_qscale[half * HALF + c * 32 + k], -bias);
-            else
-              sc = sc * mul;
-          } else if (METRIC == KNN_L2) {
-            sc = sc - bias;
-          }
-          const float key = __uint_as_float((__float_as_uint(sc) & nmask) | code);
-          v[c * 32 + k] = fmaxf(v[c * 32 + k], key);
+      for (int k = 0; k < 32; ++k) {
+        float sc = __uint_as_float(cur[k]);
+        if (DT == KNN_E4M3) {
+          if (METRIC == KNN_L2)
+            sc = fmaf(sc, mul * s_qscale[half * HALF + c * 32 + k], -bias);
+          else
+            sc = sc * mul;
+        } else if (METRIC == KNN_L2) {
+          sc = sc - bias;
         }
+        const float key = __uint_as_float((__float_as_uint(sc) & km) | kc);
+        v[c * 32 + k] = fmaxf(v[c * 32 + k], key);
       }
+      if (c + 1 < NC) tmem_wait(nxt);
     }
     tc_fence_before();
     __syncwarp();
@@ -364,11 +397,17 @@ k1_tc_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CU
   }
   tc_fence_before();
   asm volatile("bar.arrive 1, %0;" ::"n"(32 + 256) : "memory");
-  if (bin < a.Lk) {
+  if (bin_ok) {
 #pragma unroll
     for (int c = 0; c < HALF; ++c) {
       const int64_t i = qtile * BQ + half * HALF + c;
-      if (i < a.M) a.part[(split * a.M + i) * a.Lk + bin] = __float_as_uint(v[c]);
+      if (i >= a.M) continue;
+      const uint32_t u = __float_as_uint(v[c]);
+      if (a.atomic_merge) {
+        if (u != kNegInfBits) atomicMax(&a.part[i * a.Lk + bin], float_to_ordered(v[c]));
+      } else {
+        a.part[(split * a.M + i) * a.Lk + bin] = u;
+      }
     }
   }
 }
@@ -456,6 +495,7 @@ cudaError_t launch_k1_tc(const K1Plan& p, const void* X, const float* xscale, co
   int stages = (int)((budget - a.q_bytes) / a.stage_bytes);
   a.stages = stages > 6 ? 6 : stages;
   a.code_bits = (uint32_t)p.code_bits;
+  a.atomic_merge = p.atomic_merge ? 1 : 0;
   // instruction descriptor: D = F32, A/B = BF16 (kind::f16) or E4M3 (kind::f8f6f4),
   // both K-major, N = BQ, M = 128
   uint32_t idesc = (1u << 4);

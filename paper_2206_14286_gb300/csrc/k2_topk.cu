@@ -64,6 +64,105 @@ struct PackedSource {
   }
 };
 
+// Merged partials: G[i][bin] = order-mapped packed key (0 = empty) whose
+// low `bits` bits hold (2^bits - 1 - t), t the global tile ordinal; the row is
+// j = t * Lk + bin.
+struct MergedSource {
+  const uint32_t* G;
+  int64_t M, Lk, L, index_offset;
+  int g, bits;
+  __device__ __forceinline__ uint64_t key(int64_t i, int64_t b) const {
+    const uint32_t mask = bits ? ((1u << bits) - 1u) : 0u;
+    uint64_t best = 0;
+    for (int f = 0; f < g; ++f) {
+      const int64_t bin = b + (int64_t)f * L;
+      const uint32_t u = G[i * Lk + bin];
+      if (u == 0u) continue;
+      const uint32_t w = __float_as_uint(ordered_to_float(u));
+      const int64_t t = (int64_t)(mask - (w & mask));
+      const int64_t j = t * Lk + bin + index_offset;
+      const uint64_t k = make_key(__uint_as_float(w & ~mask), (int32_t)j);
+      best = k > best ? k : best;
+    }
+    return best;
+  }
+};
+
+// Descending sort of KPL keys held in registers (bitonic network).
+template <int KPL>
+__device__ __forceinline__ void reg_sort_desc(uint64_t (&k)[KPL]) {
+#pragma unroll
+  for (int size = 2; size <= KPL; size <<= 1) {
+#pragma unroll
+    for (int stride = size >> 1; stride > 0; stride >>= 1) {
+#pragma unroll
+      for (int t = 0; t < KPL / 2; ++t) {
+        const int lo = 2 * t - (t & (stride - 1));
+        const int hi = lo + stride;
+        const bool desc = (lo & size) == 0;
+        const uint64_t x = k[lo], y = k[hi];
+        const bool sw = desc ? (x < y) : (x > y);
+        k[lo] = sw ? y : x;
+        k[hi] = sw ? x : y;
+      }
+    }
+  }
+}
+
+__device__ __forceinline__ uint64_t shfl_xor_u64(uint64_t v, int o) {
+  const uint32_t lo = __shfl_xor_sync(0xffffffffu, (uint32_t)v, o);
+  const uint32_t hi = __shfl_xor_sync(0xffffffffu, (uint32_t)(v >> 32), o);
+  return ((uint64_t)hi << 32) | lo;
+}
+
+// One warp per query: lane l holds candidates l, l+32, ... (KPL of them),
+// sorted; Kp rounds each take the warp-wide maximum of the lane heads and pop
+// it from its lane. Keys are unique (distinct indices), so one lane pops.
+template <class Src, int KPL>
+__global__ void __launch_bounds__(256)
+k2_warp_kernel(Src src, int64_t M, int64_t L, int Kp, uint64_t* __restrict__ out_keys) {
+  const int lane = threadIdx.x & 31;
+  const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (i >= M) return;
+  uint64_t k[KPL];
+#pragma unroll
+  for (int r = 0; r < KPL; ++r) {
+    const int64_t b = lane + 32 * r;
+    k[r] = b < L ? src.key(i, b) : 0;
+  }
+  reg_sort_desc<KPL>(k);
+  for (int r = 0; r < Kp; ++r) {
+    uint64_t m = k[0];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const uint64_t y = shfl_xor_u64(m, o);
+      m = y > m ? y : m;
+    }
+    if (lane == 0) out_keys[i * Kp + r] = m;
+    if (m != 0 && k[0] == m) {
+#pragma unroll
+      for (int t = 0; t + 1 < KPL; ++t) k[t] = k[t + 1];
+      k[KPL - 1] = 0;
+    }
+  }
+}
+
+template <class Src>
+cudaError_t run_k2_warp(const Src& src, int64_t M, int64_t L, int Kp, uint64_t* out,
+                        cudaStream_t st) {
+  const int kpl = next_pow2((int)cdiv(L, 32));
+  const unsigned blocks = (unsigned)cdiv(M * 32, 256);
+  switch (kpl) {
+    case 1: k2_warp_kernel<Src, 1><<<blocks, 256, 0, st>>>(src, M, L, Kp, out); break;
+    case 2: k2_warp_kernel<Src, 2><<<blocks, 256, 0, st>>>(src, M, L, Kp, out); break;
+    case 4: k2_warp_kernel<Src, 4><<<blocks, 256, 0, st>>>(src, M, L, Kp, out); break;
+    case 8: k2_warp_kernel<Src, 8><<<blocks, 256, 0, st>>>(src, M, L, Kp, out); break;
+    case 16: k2_warp_kernel<Src, 16><<<blocks, 256, 0, st>>>(src, M, L, Kp, out); break;
+    default: k2_warp_kernel<Src, 32><<<blocks, 256, 0, st>>>(src, M, L, Kp, out); break;
+  }
+  return cudaGetLastError();
+}
+
 template <class Src>
 __global__ void __launch_bounds__(256)
 k2_topk_kernel(Src src, int64_t nelem, int Kp, int CH, int CAP, const uint64_t* __restrict__ run_in,
@@ -143,6 +242,10 @@ cudaError_t launch_merge_bins(const K1Plan& p, Partials parts, float* out_v, int
   if (parts.a) {
     PairSource s{parts.v, parts.a, p.M, p.Lk, p.L, p.nsplits, parts.index_offset, p.g};
     merge_bins_kernel<<<blocks, 256, 0, st>>>(s, p.M, p.L, out_v, out_a);
+  } else if (parts.merged) {
+    MergedSource s{reinterpret_cast<const uint32_t*>(parts.v), p.M, p.Lk, p.L,
+                   parts.index_offset, p.g, p.code_bits};
+    merge_bins_kernel<<<blocks, 256, 0, st>>>(s, p.M, p.L, out_v, out_a);
   } else {
     PackedSource s{reinterpret_cast<const uint32_t*>(parts.v), p.M, p.Lk, p.L, p.nsplits,
                    p.tiles_per_split, parts.index_offset, p.g, p.code_bits};
@@ -151,15 +254,31 @@ cudaError_t launch_merge_bins(const K1Plan& p, Partials parts, float* out_v, int
   return cudaGetLastError();
 }
 
+// The warp kernel serves up to 1024 candidates and 64 selected per query
+// (no running input); the CTA kernel everything else.
+static bool use_warp(int64_t L, int Kp, const uint64_t* run_in) {
+  return run_in == nullptr && L <= 1024 && Kp <= 64;
+}
+
 cudaError_t launch_k2(const K1Plan& p, Partials parts, int Kp, const uint64_t* run_in,
                       uint64_t* out_keys, cudaStream_t st) {
+  if (p.M <= 0) return cudaSuccess;
+  const bool warp = use_warp(p.L, Kp, run_in);
   if (parts.a) {
     PairSource s{parts.v, parts.a, p.M, p.Lk, p.L, p.nsplits, parts.index_offset, p.g};
-    return run_k2(s, p.M, p.L, Kp, run_in, out_keys, st);
+    return warp ? run_k2_warp(s, p.M, p.L, Kp, out_keys, st)
+                : run_k2(s, p.M, p.L, Kp, run_in, out_keys, st);
+  }
+  if (parts.merged) {
+    MergedSource s{reinterpret_cast<const uint32_t*>(parts.v), p.M, p.Lk, p.L,
+                   parts.index_offset, p.g, p.code_bits};
+    return warp ? run_k2_warp(s, p.M, p.L, Kp, out_keys, st)
+                : run_k2(s, p.M, p.L, Kp, run_in, out_keys, st);
   }
   PackedSource s{reinterpret_cast<const uint32_t*>(parts.v), p.M, p.Lk, p.L, p.nsplits,
                  p.tiles_per_split, parts.index_offset, p.g, p.code_bits};
-  return run_k2(s, p.M, p.L, Kp, run_in, out_keys, st);
+  return warp ? run_k2_warp(s, p.M, p.L, Kp, out_keys, st)
+              : run_k2(s, p.M, p.L, Kp, run_in, out_keys, st);
 }
 
 }  // namespace tpuknn

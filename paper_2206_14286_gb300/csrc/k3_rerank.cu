@@ -54,6 +54,63 @@ k3_rerank_kernel(const uint64_t* __restrict__ cand, int Kp, int K, int P2, int D
     out_val[i * K + t] = key ? (metric == KNN_L2 ? -s : s) : __int_as_float(0x7fc00000);
   }
 }
+__device__ __forceinline__ uint64_t shfl_xor_u64(uint64_t v, int o) {
+  const uint32_t lo = __shfl_xor_sync(0xffffffffu, (uint32_t)v, o);
+  const uint32_t hi = __shfl_xor_sync(0xffffffffu, (uint32_t)(v >> 32), o);
+  return ((uint64_t)hi << 32) | lo;
+}
+
+// One warp per query for Kp <= 32: the warp scores the candidates one after
+// another (lanes split D), lane c keeps candidate c's key, and a bitonic
+// network across the lanes sorts the keys (lane 0 = best).
+__global__ void __launch_bounds__(256)
+k3_warp_kernel(int64_t M, const uint64_t* __restrict__ cand, int Kp, int K, int D, int metric,
+               const float* __restrict__ qf32, int64_t q_stride,
+               const float* __restrict__ xf32, const void* __restrict__ xlp, int dtype,
+               int pitch, const float* __restrict__ xscale, int64_t N,
+               float* __restrict__ out_val, int32_t* __restrict__ out_idx) {
+  const int lane = threadIdx.x & 31;
+  const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (i >= M) return;
+  const float* q = qf32 + i * q_stride;
+  const uint64_t mykey_in = lane < Kp ? cand[i * Kp + lane] : 0;
+  uint64_t mine = 0;
+  for (int c = 0; c < Kp; ++c) {
+    const uint64_t key = __shfl_sync(0xffffffffu, mykey_in, c);
+    const int32_t j = key ? key_index(key) : -1;
+    if (j < 0 || j >= N) continue;  // warp-uniform
+    float acc = 0.0f;
+    for (int d = lane; d < D; d += 32) {
+      const float x = xf32 ? xf32[(int64_t)j * D + d] : load_stored(xlp, dtype, j, pitch, d, xscale);
+      const float qq = q[d];
+      if (metric == KNN_L2) {
+        const float t = qq - x;
+        acc = fmaf(t, t, acc);
+      } else {
+        acc = fmaf(qq, x, acc);
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == c) mine = make_key(metric == KNN_L2 ? -acc : acc, j);
+  }
+  // descending bitonic sort across the 32 lanes
+#pragma unroll
+  for (int k = 2; k <= 32; k <<= 1) {
+#pragma unroll
+    for (int jj = k >> 1; jj > 0; jj >>= 1) {
+      const uint64_t other = shfl_xor_u64(mine, jj);
+      const bool up = (lane & k) == 0, lower = (lane & jj) == 0;
+      const bool keep_max = (up == lower);
+      mine = keep_max ? (other > mine ? other : mine) : (other < mine ? other : mine);
+    }
+  }
+  if (lane < K) {
+    const float sc = key_score(mine);
+    out_idx[i * K + lane] = mine ? key_index(mine) : -1;
+    out_val[i * K + lane] = mine ? (metric == KNN_L2 ? -sc : sc) : __int_as_float(0x7fc00000);
+  }
+}
 }  // namespace
 
 cudaError_t launch_k3(int64_t M, int D, int metric, const uint64_t* cand, int Kp, int K,
@@ -61,6 +118,12 @@ cudaError_t launch_k3(int64_t M, int D, int metric, const uint64_t* cand, int Kp
                       int dtype, int pitch, const float* xscale, int64_t N, float* out_val,
                       int32_t* out_idx, cudaStream_t st) {
   if (M <= 0) return cudaSuccess;
+  if (Kp <= 32 && K <= 32) {
+    k3_warp_kernel<<<(unsigned)cdiv(M * 32, 256), 256, 0, st>>>(
+        M, cand, Kp, K, D, metric, qf32, q_stride, xf32, xlp, dtype, pitch, xscale, N, out_val,
+        out_idx);
+    return cudaGetLastError();
+  }
   const int P2 = next_pow2(Kp > K ? Kp : K);
   const size_t smem = (size_t)P2 * sizeof(uint64_t);
   if (smem > 200 * 1024) return cudaErrorInvalidValue;

@@ -24,22 +24,30 @@ struct K1Plan {
   int metric, dtype;
   int BW, BQ;               // tile rows (bins per strip), queries per tile
   int64_t nstrips, nqtiles, ntiles, tiles_per_split, nsplits;
-  int code_bits;            // packed partials: bits of the in-split tile ordinal
+  int code_bits;            // packed partials: bits of the tile ordinal
+  bool atomic_merge;        // packed partials merged in K1 into one [M][Lk] array
 };
 
-// Partial results of K1, one entry per (split, query, bin):
-//   pair form  : float value + int32 index (exact; FP32 path)
-//   packed form: one 32-bit float whose low code_bits bits encode the tile
-//                ordinal inside the split (tensor-core paths).
+// Partial results of K1:
+//   pair form   : per (split, query, bin) a float value + int32 index (exact;
+//                 FP32 path);
+//   packed form : per (split, query, bin) one 32-bit float whose low
+//                 code_bits bits encode the tile ordinal inside the split;
+//   merged form : per (query, bin) the maximum over splits of the packed keys
+//                 (code = global tile ordinal), stored order-mapped (see
+//                 float_to_ordered) so that unsigned atomicMax merges them;
+//                 0 marks a bin no row reached. The array must start at zero.
 struct Partials {
-  float* v;         // pair form values, or packed keys (as float bits)
-  int32_t* a;       // pair form indices (nullptr for packed)
+  float* v;         // pair form values, or packed / merged keys
+  int32_t* a;       // pair form indices (nullptr otherwise)
   int64_t index_offset;  // added to every decoded index (chunked exact search)
+  bool merged;
 };
 
+// Row preparation; optionally also zeroes zero_n 32-bit words of zero_buf.
 cudaError_t launch_prep(const float* x, int64_t rows, int D, int pitch, int metric, int dtype,
                         void* out_lp, float* out_scale, float* out_hnorm, float* out_f32,
-                        cudaStream_t st);
+                        cudaStream_t st, uint32_t* zero_buf = nullptr, int64_t zero_n = 0);
 
 cudaError_t launch_k1_simt(const K1Plan& p, const float* X, const float* hnorm, const float* Qp,
                            Partials out, cudaStream_t st);

@@ -11,29 +11,42 @@
 
 namespace tpuknn {
 
-// One thread per row: the row-wise reductions that decide a rounded code
-// (the E4M3 scale, the cosine norm) run sequentially in index order so that
-// the result is defined bit for bit.
+// One warp per row; lanes split the row. The only order-dependent reduction
+// that decides rounded codes, the cosine norm, is summed by lane 0 in index
+// order in FP64, so the result is defined bit for bit. The E4M3 scale uses a
+// maximum (order-free); the half norm (tolerance-level only) a warp sum.
+// If zero_buf is given, the CTAs also clear zero_n 32-bit words of it.
 template <int DT>
-__global__ void prep_rows_kernel(const float* __restrict__ x, int64_t rows, int D, int pitch,
-                                 int metric, void* __restrict__ out_lp,
-                                 float* __restrict__ out_scale, float* __restrict__ out_hnorm,
-                                 float* __restrict__ out_f32) {
-  int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+__global__ void __launch_bounds__(256)
+prep_rows_kernel(const float* __restrict__ x, int64_t rows, int D, int pitch, int metric,
+                 void* __restrict__ out_lp, float* __restrict__ out_scale,
+                 float* __restrict__ out_hnorm, float* __restrict__ out_f32,
+                 uint32_t* __restrict__ zero_buf, int64_t zero_n) {
+  if (zero_buf) {
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < zero_n;
+         t += (int64_t)gridDim.x * blockDim.x)
+      zero_buf[t] = 0u;
+  }
+  const int lane = threadIdx.x & 31;
+  const int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   if (r >= rows) return;
   const float* xr = x + r * (int64_t)D;
   double inv = 1.0;
   bool zero_row = false;
   if (metric == KNN_COS) {
     double n2 = 0.0;
-    for (int d = 0; d < D; ++d) {
-      double t = (double)xr[d];
-      n2 = __dadd_rn(n2, __dmul_rn(t, t));
+    if (lane == 0) {
+      for (int d = 0; d < D; ++d) {
+        const double t = (double)xr[d];
+        n2 = __dadd_rn(n2, __dmul_rn(t, t));
+      }
     }
+    n2 = __shfl_sync(0xffffffffu, n2, 0);
     if (n2 == 0.0) zero_row = true;
     else inv = __ddiv_rn(1.0, __dsqrt_rn(n2));
   }
   auto yval = [&](int d) -> float {
+    if (d >= D) return 0.0f;
     if (metric != KNN_COS) return xr[d];
     if (zero_row) return 0.0f;
     return __double2float_rn(__dmul_rn((double)xr[d], inv));
@@ -41,52 +54,61 @@ __global__ void prep_rows_kernel(const float* __restrict__ x, int64_t rows, int 
   float s = 1.0f;
   if (DT == KNN_E4M3) {
     float mx = 0.0f;
-    for (int d = 0; d < D; ++d) mx = fmaxf(mx, fabsf(yval(d)));
+    for (int d = lane; d < D; d += 32) mx = fmaxf(mx, fabsf(yval(d)));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
     s = mx > 0.0f ? __fdiv_rn(mx, 448.0f) : 1.0f;
-    if (out_scale) out_scale[r] = s;
+    if (out_scale && lane == 0) out_scale[r] = s;
   }
   double h2 = 0.0;
-  for (int d = 0; d < pitch; ++d) {
-    float y = d < D ? yval(d) : 0.0f;
+  for (int d = lane; d < pitch; d += 32) {
+    const float y = yval(d);
     float stored;
     if (DT == KNN_F32) {
       reinterpret_cast<float*>(out_lp)[r * pitch + d] = y;
       stored = y;
     } else if (DT == KNN_BF16) {
-      __nv_bfloat16 b = __float2bfloat16_rn(y);
+      const __nv_bfloat16 b = __float2bfloat16_rn(y);
       reinterpret_cast<__nv_bfloat16*>(out_lp)[r * pitch + d] = b;
       stored = __bfloat162float(b);
     } else {
-      __nv_fp8_storage_t c = __nv_cvt_float_to_fp8(__fdiv_rn(y, s), __NV_SATFINITE, __NV_E4M3);
+      const __nv_fp8_storage_t c =
+          __nv_cvt_float_to_fp8(__fdiv_rn(y, s), __NV_SATFINITE, __NV_E4M3);
       reinterpret_cast<uint8_t*>(out_lp)[r * pitch + d] = (uint8_t)c;
       stored = e4m3_code_to_float((uint8_t)c) * s;
     }
     h2 += (double)stored * (double)stored;
     if (out_f32 && d < D) out_f32[r * (int64_t)D + d] = y;
   }
-  if (out_hnorm) out_hnorm[r] = (float)(0.5 * h2);
+  if (out_hnorm) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) h2 += __shfl_xor_sync(0xffffffffu, h2, o);
+    if (lane == 0) out_hnorm[r] = (float)(0.5 * h2);
+  }
 }
 
 cudaError_t launch_prep(const float* x, int64_t rows, int D, int pitch, int metric, int dtype,
                         void* out_lp, float* out_scale, float* out_hnorm, float* out_f32,
-                        cudaStream_t st) {
-  if (rows <= 0) return cudaSuccess;
-  int threads = 128;
-  unsigned blocks = (unsigned)cdiv(rows, threads);
+                        cudaStream_t st, uint32_t* zero_buf, int64_t zero_n) {
+  if (rows <= 0 && zero_n <= 0) return cudaSuccess;
+  const int threads = 256;
+  int64_t blocks = cdiv(rows * 32, threads);
+  if (zero_buf && blocks < 64) blocks = 64;
+  if (blocks < 1) blocks = 1;
   float* h = metric == KNN_L2 ? out_hnorm : nullptr;
   float* f = metric == KNN_COS ? out_f32 : nullptr;
   switch (dtype) {
     case KNN_F32:
-      prep_rows_kernel<KNN_F32><<<blocks, threads, 0, st>>>(x, rows, D, pitch, metric, out_lp,
-                                                            nullptr, h, f);
+      prep_rows_kernel<KNN_F32><<<(unsigned)blocks, threads, 0, st>>>(
+          x, rows, D, pitch, metric, out_lp, nullptr, h, f, zero_buf, zero_n);
       break;
     case KNN_BF16:
-      prep_rows_kernel<KNN_BF16><<<blocks, threads, 0, st>>>(x, rows, D, pitch, metric, out_lp,
-                                                             nullptr, h, f);
+      prep_rows_kernel<KNN_BF16><<<(unsigned)blocks, threads, 0, st>>>(
+          x, rows, D, pitch, metric, out_lp, nullptr, h, f, zero_buf, zero_n);
       break;
     default:
-      prep_rows_kernel<KNN_E4M3><<<blocks, threads, 0, st>>>(x, rows, D, pitch, metric, out_lp,
-                                                             out_scale, h, f);
+      prep_rows_kernel<KNN_E4M3><<<(unsigned)blocks, threads, 0, st>>>(
+          x, rows, D, pitch, metric, out_lp, out_scale, h, f, zero_buf, zero_n);
       break;
   }
   return cudaGetLastError();
