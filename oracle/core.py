@@ -50,6 +50,7 @@ def _load():
             i64, i32 = ctypes.c_int64, ctypes.c_int
             lib.orc_exact_topk.argtypes = [P, i64, P, i64, i32, i32, i32, P, P]
             lib.orc_partial_reduce.argtypes = [P, i64, P, i64, i32, i32, i64, P, P]
+            lib.orc_partial_reduce_contiguous.argtypes = [P, i64, P, i64, i32, i32, i64, P, P]
             lib.orc_topk_pairs.argtypes = [P, P, i64, i64, i32, P, P]
             lib.orc_rerank.argtypes = [P, i64, P, i64, i32, i32, P, i32, i32, P, P]
             lib.orc_grad.argtypes = [P, i64, P, i64, i32, i32, P, i32, P, P, P]
@@ -104,9 +105,11 @@ def exact_topk(Q, X, K, metric):
     return val, idx
 
 
-def partial_reduce(Q, X, L, metric):
-    """PartialReduce (Alg. 1) with bin l = j mod L: (V, A), each M x L.
+def partial_reduce(Q, X, L, metric, bins="mod"):
+    """PartialReduce (Alg. 1): (V, A), each M x L.
 
+    bins="mod": bin l = j mod L. bins="contiguous": bin l is the l-th of L
+    balanced runs of consecutive rows (Alg. 1's ShiftRight for any L).
     V holds larger-is-better scores (L2: -||q-x||^2); empty bins have
     V = -inf, A = -1.
     """
@@ -115,7 +118,8 @@ def partial_reduce(Q, X, L, metric):
     N = X.shape[0]
     V = np.empty((M, L), np.float64)
     A = np.empty((M, L), np.int64)
-    _load().orc_partial_reduce(_p(Q), M, _p(X), N, D, _metric(metric), L, _p(V), _p(A))
+    fn = _load().orc_partial_reduce if bins == "mod" else _load().orc_partial_reduce_contiguous
+    fn(_p(Q), M, _p(X), N, D, _metric(metric), L, _p(V), _p(A))
     return V, A
 
 
@@ -133,12 +137,12 @@ def _report(v, metric):
     return -v if _metric(metric) == L2 else v
 
 
-def binwise_topk(Q, X, K, L, metric):
+def binwise_topk(Q, X, K, L, metric, bins="mod"):
     """The approximate method end to end: PartialReduce then ExactRescoring.
 
     Returns reported values and indices, M x K, best first.
     """
-    V, A = partial_reduce(Q, X, L, metric)
+    V, A = partial_reduce(Q, X, L, metric, bins)
     val, idx = topk_pairs(V, A, K)
     return _report(val, metric), idx
 

@@ -148,6 +148,41 @@ void orc_partial_reduce(const double *Q, int64_t M, const double *X, int64_t N, 
 }
 
 /* ---------------------------------------------------------------------- */
+/* PartialReduce with contiguous bins (Alg. 1 uses l = ShiftRight(j, W): a  */
+/* bin is a run of consecutive rows). For an L that does not divide N the  */
+/* runs are balanced: with q = N / L and r = N mod L, bin l holds rows     */
+/* [l*q + min(l, r), (l+1)*q + min(l+1, r)), so the first r bins have one   */
+/* row more. Same outputs and tie rule as orc_partial_reduce.              */
+/* ---------------------------------------------------------------------- */
+static int64_t contiguous_bin(int64_t j, int64_t N, int64_t L) {
+  const int64_t q = N / L, r = N % L;
+  const int64_t big = r * (q + 1); /* rows held by the first r bins */
+  return j < big ? j / (q + 1) : r + (j - big) / q;
+}
+
+void orc_partial_reduce_contiguous(const double *Q, int64_t M, const double *X, int64_t N, int D,
+                                   int metric, int64_t L, double *V, int64_t *A) {
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int64_t i = 0; i < M; ++i) {
+    double *v = V + i * L;
+    int64_t *a = A + i * L;
+    for (int64_t l = 0; l < L; ++l) {
+      v[l] = -INFINITY;
+      a[l] = -1;
+    }
+    const double *q = Q + i * D;
+    for (int64_t j = 0; j < N; ++j) {
+      double y = score(q, X + j * D, D, metric);
+      int64_t l = contiguous_bin(j, N, L);
+      if (y > v[l]) {
+        v[l] = y;
+        a[l] = j;
+      }
+    }
+  }
+}
+
+/* ---------------------------------------------------------------------- */
 /* ExactRescoring (Sec. 5): the top-K of the L (score, index) pairs of     */
 /* each query, best first. Empty bins (A = -1) are skipped. Values stay in */
 /* the internal orientation; indices -1 pad when fewer than K are valid.   */

@@ -25,7 +25,8 @@ def paper_expected_recall(L, K):
 
 
 def bin_sizes(N, L):
-    """Sizes of the bins j mod L over rows 0..N-1."""
+    """Sizes of the bins j mod L over rows 0..N-1 (the balanced contiguous
+    bins have the same sizes, so the recall law below covers both maps)."""
     base, extra = divmod(N, L)
     return [base + (1 if b < extra else 0) for b in range(L)]
 

@@ -114,6 +114,49 @@ def test_partial_reduce_brute_force_every_L(metric):
             np.testing.assert_allclose(V[:, b], S[np.arange(M), best], rtol=1e-12, atol=1e-12)
 
 
+@pytest.mark.parametrize("metric", METRICS)
+def test_partial_reduce_contiguous_brute_force_every_L(metric):
+    """Contiguous bins (Alg. 1's ShiftRight) against NumPy's balanced split."""
+    g = rng(23)
+    M, N, D = 4, 29, 5
+    Q, X = g.standard_normal((M, D)), g.standard_normal((N, D))
+    S = numpy_scores(Q, X, metric)
+    for L in range(1, N + 1):
+        V, A = oracle.partial_reduce(Q, X, L, metric, bins="contiguous")
+        for b, rows in enumerate(np.array_split(np.arange(N), L)):
+            best = rows[np.argmax(S[:, rows], axis=1)]
+            np.testing.assert_array_equal(A[:, b], best)
+            np.testing.assert_allclose(V[:, b], S[np.arange(M), best], rtol=1e-12, atol=1e-12)
+
+
+def test_contiguous_power_of_two_is_shift_right():
+    """When L divides N into runs of 2^W rows, the bin is j >> W (Alg. 1)."""
+    g = rng(24)
+    Q, X = g.standard_normal((3, 4)), g.standard_normal((64, 4))
+    _, A = oracle.partial_reduce(Q, X, 8, "ip", bins="contiguous")
+    assert np.all(A >> 3 == np.arange(8)[None, :])
+
+
+@pytest.mark.parametrize("metric", METRICS)
+def test_contiguous_L_equal_N_is_exact_and_recall_law(metric):
+    g = rng(25)
+    Q, X = g.standard_normal((9, 12)), g.standard_normal((150, 12))
+    v1, i1 = oracle.binwise_topk(Q, X, 10, 150, metric, bins="contiguous")
+    v2, i2 = oracle.exact_topk(Q, X, 10, metric)
+    np.testing.assert_array_equal(i1, i2)
+
+
+def test_empirical_recall_contiguous_bins():
+    g = rng(26)
+    N, D, M, K, L = 4096, 16, 400, 10, 60
+    X, Q = g.standard_normal((N, D)), g.standard_normal((M, D))
+    _, ie = oracle.exact_topk(Q, X, K, "ip")
+    _, ib = oracle.binwise_topk(Q, X, K, L, "ip", bins="contiguous")
+    rec = np.array([len(set(ie[i]) & set(ib[i])) / K for i in range(M)])
+    sem = rec.std() / math.sqrt(M)
+    assert abs(rec.mean() - R.exact_expected_recall(N, L, K)) < 5 * sem
+
+
 def test_partial_reduce_tie_keeps_smaller_index():
     X = np.zeros((12, 3))
     X[:, 0] = 1.0                    # every row scores the same
