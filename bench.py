@@ -43,6 +43,7 @@ def parse():
     ap.add_argument("--workload", default="mix_l2_1m")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--fp32-steps", type=int, default=10)
+    ap.add_argument("--bins", default="contiguous", choices=["contiguous", "mod"])
     return ap.parse_args()
 
 
@@ -106,9 +107,10 @@ class OracleRunner:
     """The FP64 oracle running the same method (PartialReduce, top-2K, re-rank)
     on a bounded sample of the workload's queries."""
 
-    def __init__(self, w, L, K):
+    def __init__(self, w, L, K, bins="mod"):
         import oracle
         self.o = oracle
+        self.bins = bins
         self.X, self.Q, self.L, self.K, self.metric = w["X"], w["Q"], L, K, w["metric"]
         self.lowp = w["dtype"] == "bf16"
         self.Xs = oracle.bf16_round(self.X) if self.lowp else self.X.astype(np.float64)
@@ -120,7 +122,7 @@ class OracleRunner:
         self.cursor = (self.cursor + n) % self.Q.shape[0]
         Qs = o.bf16_round(q) if self.lowp else q.astype(np.float64)
         t0 = time.perf_counter()
-        V, A = o.partial_reduce(Qs, self.Xs, self.L, self.metric)
+        V, A = o.partial_reduce(Qs, self.Xs, self.L, self.metric, bins=self.bins)
         _, cand = o.topk_pairs(V, A, 2 * self.K)
         o.rerank(q, self.X, cand, self.K, self.metric)
         return time.perf_counter() - t0
@@ -150,7 +152,7 @@ def main():
         w = synth.workload(args.workload)
         K = w["K"]
         L = min(w["X"].shape[0], -(-R.min_bins(K, w["recall"]) // 128) * 128)
-        runner = OracleRunner(w, L, K)
+        runner = OracleRunner(w, L, K, args.bins)
         n = runner.size_for(max(0.5, 120.0 / max(1, args.steps + args.warmup)), 256)
         per = []
         nq = 0
@@ -166,7 +168,7 @@ def main():
                 "unit": "queries/s", "n_gpus": args.gpus, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": 1e3 * tot / len(per),
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-                "data": "synthetic", "config": config_of(w, L),
+                "data": "synthetic", "config": config_of(w, L, bins=args.bins),
                 "cpu_baseline": {"value": value, "unit": "queries/s", "cores": cores,
                                  "kind": "oracle",
                                  "sample": "%d queries per step of the %d-query batch, full %d-row database"
@@ -198,8 +200,10 @@ def main():
     val = torch.empty((M, K), dtype=torch.float32, device="cuda")
     idx = torch.empty((M, K), dtype=torch.int32, device="cuda")
 
+    bins = args.bins
+
     def step():
-        db.search(Qd, K, L=L, rerank=rerank, out=(val, idx))
+        db.search(Qd, K, L=L, rerank=rerank, out=(val, idx), bins=bins)
 
     for _ in range(max(3, args.warmup)):
         step()
@@ -244,7 +248,22 @@ def main():
     ei = ei.cpu().numpy()
     recall = float(np.mean([len(set(gi[i]) & set(ei[i])) / K for i in range(M)]))
 
-    # the plain FP32 path on the same workload
+    # the same BF16 search with the other bin map (j mod L), same workload
+    other = "mod" if bins == "contiguous" else "contiguous"
+    for _ in range(2):
+        db.search(Qd, K, L=L, rerank=rerank, bins=other)
+    torch.cuda.synchronize()
+    ao, bo = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ao.record()
+    for _ in range(args.steps):
+        db.search(Qd, K, L=L, rerank=rerank, bins=other, out=(val, idx))
+    bo.record()
+    torch.cuda.synchronize()
+    ms_other = ao.elapsed_time(bo) / args.steps
+    io = idx.cpu().numpy()
+    recall_other = float(np.mean([len(set(io[i]) & set(ei[i])) / K for i in range(M)]))
+
+    # the plain FP32 path on the same workload (j mod L bins)
     def step32():
         dbx.search(Qd, K, L=L, rerank=rerank)
     for _ in range(2):
@@ -267,11 +286,11 @@ def main():
     vh = torch.empty((M, K), dtype=torch.float32, pin_memory=True)
     ih = torch.empty((M, K), dtype=torch.int32, pin_memory=True)
     for _ in range(3):
-        db.search_host(qh, K, L=L, rerank=rerank, out=(vh, ih))
+        db.search_host(qh, K, L=L, rerank=rerank, out=(vh, ih), bins=bins)
     e2e_steps = max(5, args.steps)
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
-        db.search_host(qh, K, L=L, rerank=rerank, out=(vh, ih))
+        db.search_host(qh, K, L=L, rerank=rerank, out=(vh, ih), bins=bins)
     e2e_s = time.perf_counter() - t0
     e2e = {"value": world * M * e2e_steps / e2e_s, "unit": "queries/s",
            "h2d_bytes_per_step": int(M * D * 4), "d2h_bytes_per_step": int(M * K * 8)}
@@ -283,11 +302,13 @@ def main():
     achieved = flops / (k1_ms / 1e3) / 1e12
     peak = pk["bf16_tflops"]
     k1_bytes = N * D * 2 + (N * 4 if metric == "l2" else 0) + M * D * 2
-    traffic = k1_traffic(M, N, D)
+    traffic = k1_traffic(M, N, D, bins)
     roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
             "frac": achieved / peak, "traffic": traffic,
             "peak_source": "%s bf16 dense burst (MEASURED_PEAKS.json)" % pk_kind,
-            "kernel": "k1_tc_kernel (fused BF16 contraction + PartialReduce)",
+            "kernel": ("k1_tcq_kernel (fused BF16 contraction + PartialReduce, contiguous bins)"
+                       if bins == "contiguous" else
+                       "k1_tc_kernel (fused BF16 contraction + PartialReduce, j mod L bins)"),
             "algorithmic": "2*M*N*D = %.4g FLOP per launch" % flops,
             "hbm_context": {"algorithmic_bytes": k1_bytes,
                             "achieved_gbs": k1_bytes / (k1_ms / 1e3) / 1e9,
@@ -297,7 +318,7 @@ def main():
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import oracle
         oracle.build()
-        runner = OracleRunner(w, L, K)
+        runner = OracleRunner(w, L, K, bins)
         n = runner.size_for(12.0, M)
         tt = runner.run(n)
         rate = n / tt
@@ -311,8 +332,11 @@ def main():
                 "value": value, "unit": "queries/s", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-                "dtype": "bf16", "data": "synthetic", "config": config_of(w, L, L_min),
+                "dtype": "bf16", "data": "synthetic", "config": config_of(w, L, L_min, bins),
                 "recall_at_10": recall,
+                "other_bins": {"bins": other, "value": world * M / (ms_other / 1e3),
+                               "unit": "queries/s", "ms_per_step": ms_other,
+                               "recall_at_10": recall_other},
                 "p50_ms": sm[len(sm) // 2], "p99_ms": sm[min(len(sm) - 1, int(0.99 * len(sm)))],
                 "fp32_path": {"value": world * M / (ms32 / 1e3), "unit": "queries/s",
                               "ms_per_step": ms32, "recall_at_10": recall32},
@@ -324,27 +348,27 @@ def main():
     return 0
 
 
-def config_of(w, L, L_min=None):
+def config_of(w, L, L_min=None, bins="mod"):
     X, Q = w["X"], w["Q"]
     return {"workload": "gaussian-mixture-256c L2 N=%d D=%d M=%d K=%d" % (X.shape[0], X.shape[1],
                                                                           Q.shape[0], w["K"]),
             "N": X.shape[0], "D": X.shape[1], "global_batch": Q.shape[0], "K": w["K"],
-            "L": L, "L_min_eq14": L_min, "metric": w["metric"], "rerank": "FP32 top-%dK" % w.get("rerank", 2),
+            "L": L, "L_min_eq14": L_min, "bins": bins, "metric": w["metric"], "rerank": "FP32 top-%dK" % w.get("rerank", 2),
             "l2_flush": "inputs larger than L2 (database %d MB in BF16 streamed every step)"
                         % (X.shape[0] * X.shape[1] * 2 // 2 ** 20),
             "parallelism": "replicas"}
 
 
-def k1_traffic(M, N, D):
+def k1_traffic(M, N, D, bins="contiguous"):
     """DRAM bytes per K1 launch from the committed ncu summary, if it was taken
     on the current kernel source (else None)."""
     p = os.path.join(ROOT, "profiles", "k1_tc_traffic.json")
-    src = os.path.join(ROOT, "paper_2206_14286_gb300", "csrc", "k1_tc.cu")
     if not os.path.exists(p):
         return None
     d = json.load(open(p))
+    src = os.path.join(ROOT, "paper_2206_14286_gb300", "csrc", d.get("source", "k1_tc.cu"))
     h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
-    if d.get("k1_tc_sha") != h:
+    if d.get("sha") != h or d.get("bins") != bins:
         return None
     if d.get("M") != M or d.get("D") != D:
         return None

@@ -54,6 +54,15 @@ typedef enum { KNN_IP = 0, KNN_L2 = 1, KNN_COS = 2 } knn_metric;
  * row: value = code * scale. */
 typedef enum { KNN_F32 = 0, KNN_BF16 = 1, KNN_E4M3 = 2 } knn_dtype;
 
+/* Map from database row j to its bin l (Alg. 1, Sec. 5):
+ *   KNN_BINS_MOD        l = j mod L;
+ *   KNN_BINS_CONTIGUOUS runs of consecutive rows (Alg. 1's l = ShiftRight(j, W)),
+ *                       balanced for any L: with q = N / L and r = N mod L, bin l
+ *                       holds rows [l*q + min(l, r), (l+1)*q + min(l+1, r)).
+ * Both give every bin N/L rows (up to one), so the recall law of Sec. 5.1 is the
+ * same for exchangeable rows. KNN_BINS_CONTIGUOUS is implemented for KNN_BF16. */
+typedef enum { KNN_BINS_MOD = 0, KNN_BINS_CONTIGUOUS = 1 } knn_bin_map;
+
 const char* knn_status_string(int status);
 /* The last CUDA error code seen by the library on this thread (0 = none). */
 int knn_last_cuda_error(void);
@@ -108,8 +117,9 @@ knn_status knn_prepare(const float* x, int64_t rows, int32_t D, int32_t metric, 
  *               candidates from db_lp (dequantised).
  *   q         : M x D FP32 queries (device); prepared inside the call.
  *   K         : neighbours per query, 1 <= K <= min(L, 4096).
- *   L         : number of bins (bin of row j = j mod L), 1 <= L <= N; if
- *               L <= 0, L = knn_plan_bins(N, K, recall_target, 1).
+ *   L         : number of bins, 1 <= L <= N; if L <= 0,
+ *               L = knn_plan_bins(N, K, recall_target, 1).
+ *   bin_map   : knn_bin_map (which rows share a bin).
  *   rerank_mult: K' = max(1, rerank_mult) * K candidates (capped at L) leave
  *               ExactRescoring and are scored in FP32; the best K are kept.
  *   out_val   : M x K FP32 values (reported form), best first.
@@ -121,12 +131,13 @@ knn_status knn_prepare(const float* x, int64_t rows, int32_t D, int32_t metric, 
  */
 knn_status knn_search(const void* db_lp, const float* db_scale, const float* db_hnorm,
                       const float* db_f32, int64_t N, int32_t D, int32_t dtype, int32_t metric,
-                      const float* q, int64_t M, int32_t K, int64_t L, double recall_target,
-                      int32_t rerank_mult, float* out_val, int32_t* out_idx,
-                      void* workspace, size_t ws_bytes, void* stream);
+                      const float* q, int64_t M, int32_t K, int64_t L, int32_t bin_map,
+                      double recall_target, int32_t rerank_mult, float* out_val,
+                      int32_t* out_idx, void* workspace, size_t ws_bytes, void* stream);
 
 size_t knn_search_workspace(int64_t N, int32_t D, int32_t dtype, int32_t metric, int64_t M,
-                            int32_t K, int64_t L, double recall_target, int32_t rerank_mult);
+                            int32_t K, int64_t L, int32_t bin_map, double recall_target,
+                            int32_t rerank_mult);
 
 /*
  * The same search with HOST queries and HOST outputs: copies q (M x D FP32)
@@ -139,30 +150,34 @@ size_t knn_search_workspace(int64_t N, int32_t D, int32_t dtype, int32_t metric,
 knn_status knn_search_host(const void* db_lp, const float* db_scale, const float* db_hnorm,
                            const float* db_f32, int64_t N, int32_t D, int32_t dtype,
                            int32_t metric, const float* q_host, int64_t M, int32_t K, int64_t L,
-                           double recall_target, int32_t rerank_mult, float* out_val_host,
-                           int32_t* out_idx_host, void* workspace, size_t ws_bytes, void* stream);
+                           int32_t bin_map, double recall_target, int32_t rerank_mult,
+                           float* out_val_host, int32_t* out_idx_host, void* workspace,
+                           size_t ws_bytes, void* stream);
 
 size_t knn_search_host_workspace(int64_t N, int32_t D, int32_t dtype, int32_t metric, int64_t M,
-                                 int32_t K, int64_t L, double recall_target, int32_t rerank_mult);
+                                 int32_t K, int64_t L, int32_t bin_map, double recall_target,
+                                 int32_t rerank_mult);
 
 /*
  * PartialReduce alone (Alg. 1; the paper's aggregate_to_topk = False,
  * App. A.1): for every query i and bin l the best internal score and its
  * index, out_v[i*L + l], out_a[i*L + l]. Scores are in the internal
  * orientation (see the conventions above; L2 is the relaxed score).
- * For KNN_BF16 / KNN_E4M3 the values carry the contraction's rounding: the
- * kernel keeps only the top 32 - c bits of each FP32 score, c <= 13, while
- * it reduces (the low bits hold the row's position in its bin); for E4M3 the
- * per-query scale is left out of the value (it does not change the order
- * within a query).
+ * With KNN_BINS_MOD and KNN_BF16 / KNN_E4M3 the values carry the
+ * contraction's rounding: the kernel keeps only the top 32 - c bits of each
+ * FP32 score, c <= 13, while it reduces (the low bits hold the row's position
+ * in its bin); for E4M3 the per-query scale is left out of the value (it does
+ * not change the order within a query). With KNN_BINS_CONTIGUOUS (BF16) the
+ * values are the FP32 accumulator, the L2 half norm entering the contraction
+ * as a three-part BF16 split (error below 2^-24 of the norm).
  */
 knn_status knn_partial_reduce(const void* db_lp, const float* db_scale, const float* db_hnorm,
                               int64_t N, int32_t D, int32_t dtype, int32_t metric, const float* q,
-                              int64_t M, int64_t L, float* out_v, int32_t* out_a,
+                              int64_t M, int64_t L, int32_t bin_map, float* out_v, int32_t* out_a,
                               void* workspace, size_t ws_bytes, void* stream);
 
 size_t knn_partial_reduce_workspace(int64_t N, int32_t D, int32_t dtype, int32_t metric,
-                                    int64_t M, int64_t L);
+                                    int64_t M, int64_t L, int32_t bin_map);
 
 /*
  * Exact K-NN (Eq. 1-2): the top K over all N rows, scored in `dtype` with

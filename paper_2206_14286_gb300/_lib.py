@@ -12,6 +12,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "libtpuknn.so")
 KNN_OK, KNN_EINVAL, KNN_ENOMEM, KNN_ECUDA, KNN_ETIMEOUT, KNN_EUNSUPPORTED = range(6)
 METRIC = {"ip": 0, "l2": 1, "cos": 2}
 DTYPE = {"f32": 0, "bf16": 1, "e4m3": 2}
+BINS = {"mod": 0, "contiguous": 1}
 
 # every function the header declares, with (restype, argtypes)
 P, I32, I64, SZ, DBL = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_size_t, ctypes.c_double
@@ -22,15 +23,15 @@ SIGNATURES = {
     "knn_row_pitch": (I32, [I32]),
     "knn_plan_bins": (I64, [I64, I32, DBL, I32]),
     "knn_prepare": (ctypes.c_int, [P, I64, I32, I32, I32, P, P, P, P, P]),
-    "knn_search": (ctypes.c_int, [P, P, P, P, I64, I32, I32, I32, P, I64, I32, I64, DBL, I32,
-                                  P, P, P, SZ, P]),
-    "knn_search_workspace": (SZ, [I64, I32, I32, I32, I64, I32, I64, DBL, I32]),
-    "knn_search_host": (ctypes.c_int, [P, P, P, P, I64, I32, I32, I32, P, I64, I32, I64, DBL,
-                                       I32, P, P, P, SZ, P]),
-    "knn_search_host_workspace": (SZ, [I64, I32, I32, I32, I64, I32, I64, DBL, I32]),
-    "knn_partial_reduce": (ctypes.c_int, [P, P, P, I64, I32, I32, I32, P, I64, I64, P, P, P, SZ,
-                                          P]),
-    "knn_partial_reduce_workspace": (SZ, [I64, I32, I32, I32, I64, I64]),
+    "knn_search": (ctypes.c_int, [P, P, P, P, I64, I32, I32, I32, P, I64, I32, I64, I32, DBL,
+                                  I32, P, P, P, SZ, P]),
+    "knn_search_workspace": (SZ, [I64, I32, I32, I32, I64, I32, I64, I32, DBL, I32]),
+    "knn_search_host": (ctypes.c_int, [P, P, P, P, I64, I32, I32, I32, P, I64, I32, I64, I32,
+                                       DBL, I32, P, P, P, SZ, P]),
+    "knn_search_host_workspace": (SZ, [I64, I32, I32, I32, I64, I32, I64, I32, DBL, I32]),
+    "knn_partial_reduce": (ctypes.c_int, [P, P, P, I64, I32, I32, I32, P, I64, I64, I32, P, P, P,
+                                          SZ, P]),
+    "knn_partial_reduce_workspace": (SZ, [I64, I32, I32, I32, I64, I64, I32]),
     "knn_search_exact": (ctypes.c_int, [P, P, P, P, I64, I32, I32, I32, P, I64, I32, P, P, P, SZ,
                                         P]),
     "knn_search_exact_workspace": (SZ, [I64, I32, I32, I32, I64, I32]),

@@ -182,6 +182,7 @@ struct SearchArgs {
   int64_t L;
   double recall;
   int rerank;
+  int bin_map;
 };
 
 // Checks that do not need the data pointers.
@@ -219,8 +220,41 @@ struct SearchLayout {
 knn_status layout_search(const SearchArgs& a, SearchLayout* s) {
   knn_status st = check_sizes(a.N, a.D, a.dtype, a.metric, a.M, a.K);
   if (st != KNN_OK) return st;
+  if (a.bin_map != KNN_BINS_MOD && a.bin_map != KNN_BINS_CONTIGUOUS) return KNN_EINVAL;
   int64_t L;
   if ((st = resolve_L(a, &L)) != KNN_OK) return st;
+  if (a.bin_map == KNN_BINS_CONTIGUOUS) {
+    if (!k1_tcq_supported(a.dtype, a.D, a.metric)) return KNN_EUNSUPPORTED;
+    // K2 reads the merged [M][L] keys directly: a plan with one bin per L
+    K1Plan p{};
+    p.N = a.N;
+    p.M = a.M;
+    p.L = L;
+    p.Lk = L;
+    p.g = 1;
+    p.D = a.D;
+    p.pitch = (int)round_up(a.D, 16);
+    p.metric = a.metric;
+    p.dtype = a.dtype;
+    p.nsplits = 1;
+    s->plan = p;
+    s->Kp = kprime(a.K, a.rerank, L);
+    s->qb = query_bytes(a.M, a.D, a.dtype, a.metric);
+    size_t o = 0;
+    s->off_qlp = o;
+    o += s->qb.lp;
+    s->off_qscale = o;
+    o += s->qb.scale;
+    s->off_qf32 = o;
+    o += s->qb.f32;
+    s->off_part_v = o;
+    o += al((size_t)a.M * L * 8);
+    s->off_part_a = o;
+    s->off_cand = o;
+    o += al((size_t)a.M * s->Kp * 8);
+    s->total = o > kAlign ? o : kAlign;
+    return KNN_OK;
+  }
   s->plan = make_plan(a.N, a.M, L, a.D, a.metric, a.dtype, 0);
   if (s->plan.BQ == 0) return KNN_EUNSUPPORTED;
   s->Kp = kprime(a.K, a.rerank, L);
@@ -260,9 +294,12 @@ cudaError_t prep_queries(const SearchArgs& a, const SearchLayout& s, char* ws, c
   void* qlp = ws + s.off_qlp;
   float* qscale = s.qb.scale ? reinterpret_cast<float*>(ws + s.off_qscale) : nullptr;
   float* qf = s.qb.f32 ? reinterpret_cast<float*>(ws + s.off_qf32) : nullptr;
-  // the merged partials start at zero: the same launch clears them
-  uint32_t* zbuf = s.plan.atomic_merge ? reinterpret_cast<uint32_t*>(ws + s.off_part_v) : nullptr;
-  const int64_t zn = s.plan.atomic_merge ? s.plan.M * s.plan.Lk : 0;
+  // merged partials start at zero: the same launch clears them
+  const bool keys64 = a.bin_map == KNN_BINS_CONTIGUOUS;
+  uint32_t* zbuf = (s.plan.atomic_merge || keys64) ? reinterpret_cast<uint32_t*>(ws + s.off_part_v)
+                                                   : nullptr;
+  const int64_t zn = keys64 ? 2 * s.plan.M * s.plan.L
+                            : (s.plan.atomic_merge ? s.plan.M * s.plan.Lk : 0);
   cudaError_t e = launch_prep(a.q, a.M, a.D, s.plan.pitch, a.metric, a.dtype, qlp, qscale, nullptr,
                               qf, st, zbuf, zn);
   if (a.dtype == KNN_F32) {
@@ -281,6 +318,9 @@ cudaError_t prep_queries(const SearchArgs& a, const SearchLayout& s, char* ws, c
 cudaError_t run_k1(const K1Plan& p, const SearchArgs& a, const void* xlp, const float* xscale,
                    const float* hnorm, const void* qlp, const float* qscale, Partials parts,
                    cudaStream_t st) {
+  if (parts.keys64)
+    return launch_k1_tcq(p.N, p.M, p.L, p.D, p.metric, xlp, hnorm, qlp,
+                         reinterpret_cast<unsigned long long*>(parts.v), st);
   if (a.dtype == KNN_F32)
     return launch_k1_simt(p, reinterpret_cast<const float*>(xlp), hnorm,
                           reinterpret_cast<const float*>(qlp), parts, st);
@@ -305,9 +345,11 @@ knn_status search_impl(const SearchArgs& a, float* out_val, int32_t* out_idx, vo
     e = prep_queries(a, s, ws, &qf32, &q_stride, st);
   }
   if (e != cudaSuccess) return cuda_status(e);
+  const bool k64 = a.bin_map == KNN_BINS_CONTIGUOUS;
   Partials parts{reinterpret_cast<float*>(ws + s.off_part_v),
-                 a.dtype == KNN_F32 ? reinterpret_cast<int32_t*>(ws + s.off_part_a) : nullptr, 0,
-                 s.plan.atomic_merge};
+                 (a.dtype == KNN_F32 && !k64) ? reinterpret_cast<int32_t*>(ws + s.off_part_a)
+                                              : nullptr,
+                 0, s.plan.atomic_merge, k64};
   const float* qscale = s.qb.scale ? reinterpret_cast<const float*>(ws + s.off_qscale) : nullptr;
   {
     ProfScope ps(1, st);
@@ -402,7 +444,7 @@ knn_status exact_impl(const SearchArgs& a, float* out_val, int32_t* out_idx, voi
     K1Plan p = make_plan(nc, a.M, nc, a.D, a.metric, a.dtype, 1);
     Partials parts{reinterpret_cast<float*>(ws + s.off_part_v),
                    a.dtype == KNN_F32 ? reinterpret_cast<int32_t*>(ws + s.off_part_a) : nullptr,
-                   n0, false};
+                   n0, false, false};
     const char* xlp = reinterpret_cast<const char*>(a.db_lp) + (size_t)n0 * p.pitch * esz;
     const float* xs = a.db_scale ? a.db_scale + n0 : nullptr;
     const float* hn = a.db_hnorm ? a.db_hnorm + n0 : nullptr;
@@ -468,9 +510,10 @@ knn_status knn_prepare(const float* x, int64_t rows, int32_t D, int32_t metric, 
 }
 
 size_t knn_search_workspace(int64_t N, int32_t D, int32_t dtype, int32_t metric, int64_t M,
-                            int32_t K, int64_t L, double recall_target, int32_t rerank_mult) {
+                            int32_t K, int64_t L, int32_t bin_map, double recall_target,
+                            int32_t rerank_mult) {
   SearchArgs a{nullptr, nullptr, nullptr, nullptr, N, D, dtype, metric, nullptr, M, K, L,
-               recall_target, rerank_mult};
+               recall_target, rerank_mult, bin_map};
   SearchLayout s;
   if (layout_search(a, &s) != KNN_OK) return 0;
   return s.total;
@@ -478,17 +521,19 @@ size_t knn_search_workspace(int64_t N, int32_t D, int32_t dtype, int32_t metric,
 
 knn_status knn_search(const void* db_lp, const float* db_scale, const float* db_hnorm,
                       const float* db_f32, int64_t N, int32_t D, int32_t dtype, int32_t metric,
-                      const float* q, int64_t M, int32_t K, int64_t L, double recall_target,
-                      int32_t rerank_mult, float* out_val, int32_t* out_idx, void* workspace,
-                      size_t ws_bytes, void* stream) {
+                      const float* q, int64_t M, int32_t K, int64_t L, int32_t bin_map,
+                      double recall_target, int32_t rerank_mult, float* out_val,
+                      int32_t* out_idx, void* workspace, size_t ws_bytes, void* stream) {
   SearchArgs a{db_lp, db_scale, db_hnorm, db_f32, N, D, dtype, metric, q, M, K, L,
-               recall_target, rerank_mult};
+               recall_target, rerank_mult, bin_map};
   return search_impl(a, out_val, out_idx, workspace, ws_bytes, (cudaStream_t)stream);
 }
 
 size_t knn_search_host_workspace(int64_t N, int32_t D, int32_t dtype, int32_t metric, int64_t M,
-                                 int32_t K, int64_t L, double recall_target, int32_t rerank_mult) {
-  size_t base = knn_search_workspace(N, D, dtype, metric, M, K, L, recall_target, rerank_mult);
+                                 int32_t K, int64_t L, int32_t bin_map, double recall_target,
+                                 int32_t rerank_mult) {
+  size_t base = knn_search_workspace(N, D, dtype, metric, M, K, L, bin_map, recall_target,
+                                     rerank_mult);
   if (base == 0) return 0;
   return al(base) + al((size_t)M * D * 4) + al((size_t)M * K * 4) * 2;
 }
@@ -496,15 +541,16 @@ size_t knn_search_host_workspace(int64_t N, int32_t D, int32_t dtype, int32_t me
 knn_status knn_search_host(const void* db_lp, const float* db_scale, const float* db_hnorm,
                            const float* db_f32, int64_t N, int32_t D, int32_t dtype,
                            int32_t metric, const float* q_host, int64_t M, int32_t K, int64_t L,
-                           double recall_target, int32_t rerank_mult, float* out_val_host,
-                           int32_t* out_idx_host, void* workspace, size_t ws_bytes,
-                           void* stream) {
-  size_t base = knn_search_workspace(N, D, dtype, metric, M, K, L, recall_target, rerank_mult);
+                           int32_t bin_map, double recall_target, int32_t rerank_mult,
+                           float* out_val_host, int32_t* out_idx_host, void* workspace,
+                           size_t ws_bytes, void* stream) {
+  size_t base = knn_search_workspace(N, D, dtype, metric, M, K, L, bin_map, recall_target,
+                                     rerank_mult);
   if (base == 0) return KNN_EINVAL;
   if (M == 0) return KNN_OK;
   if (!q_host || !out_val_host || !out_idx_host) return KNN_EINVAL;
   if (!workspace || !aligned(workspace, kAlign)) return KNN_EINVAL;
-  size_t need = knn_search_host_workspace(N, D, dtype, metric, M, K, L, recall_target,
+  size_t need = knn_search_host_workspace(N, D, dtype, metric, M, K, L, bin_map, recall_target,
                                           rerank_mult);
   if (ws_bytes < need) return KNN_ENOMEM;
   char* ws = reinterpret_cast<char*>(workspace);
@@ -516,7 +562,7 @@ knn_status knn_search_host(const void* db_lp, const float* db_scale, const float
   cudaError_t e = cudaMemcpyAsync(qd, q_host, (size_t)M * D * 4, cudaMemcpyHostToDevice, st);
   if (e != cudaSuccess) return cuda_status(e);
   knn_status rc = knn_search(db_lp, db_scale, db_hnorm, db_f32, N, D, dtype, metric, qd, M, K, L,
-                             recall_target, rerank_mult, vd, id, ws, base, stream);
+                             bin_map, recall_target, rerank_mult, vd, id, ws, base, stream);
   if (rc != KNN_OK) return rc;
   e = cudaMemcpyAsync(out_val_host, vd, (size_t)M * K * 4, cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess)
@@ -526,9 +572,10 @@ knn_status knn_search_host(const void* db_lp, const float* db_scale, const float
 }
 
 size_t knn_partial_reduce_workspace(int64_t N, int32_t D, int32_t dtype, int32_t metric,
-                                    int64_t M, int64_t L) {
+                                    int64_t M, int64_t L, int32_t bin_map) {
   if (L < 1 || L > N) return 0;
-  SearchArgs a{nullptr, nullptr, nullptr, nullptr, N, D, dtype, metric, nullptr, M, 1, L, 0.5, 1};
+  SearchArgs a{nullptr, nullptr, nullptr, nullptr, N, D, dtype, metric, nullptr, M, 1, L, 0.5, 1,
+               bin_map};
   SearchLayout s;
   if (layout_search(a, &s) != KNN_OK) return 0;
   return s.total;
@@ -536,10 +583,11 @@ size_t knn_partial_reduce_workspace(int64_t N, int32_t D, int32_t dtype, int32_t
 
 knn_status knn_partial_reduce(const void* db_lp, const float* db_scale, const float* db_hnorm,
                               int64_t N, int32_t D, int32_t dtype, int32_t metric, const float* q,
-                              int64_t M, int64_t L, float* out_v, int32_t* out_a,
+                              int64_t M, int64_t L, int32_t bin_map, float* out_v, int32_t* out_a,
                               void* workspace, size_t ws_bytes, void* stream) {
   if (L < 1 || L > N) return KNN_EINVAL;
-  SearchArgs a{db_lp, db_scale, db_hnorm, nullptr, N, D, dtype, metric, q, M, 1, L, 0.5, 1};
+  SearchArgs a{db_lp, db_scale, db_hnorm, nullptr, N, D, dtype, metric, q, M, 1, L, 0.5, 1,
+               bin_map};
   SearchLayout s;
   knn_status rc = layout_search(a, &s);
   if (rc != KNN_OK) return rc;
@@ -553,9 +601,11 @@ knn_status knn_partial_reduce(const void* db_lp, const float* db_scale, const fl
   int64_t q_stride;
   cudaError_t e = prep_queries(a, s, ws, &qf32, &q_stride, st);
   if (e != cudaSuccess) return cuda_status(e);
+  const bool k64 = bin_map == KNN_BINS_CONTIGUOUS;
   Partials parts{reinterpret_cast<float*>(ws + s.off_part_v),
-                 dtype == KNN_F32 ? reinterpret_cast<int32_t*>(ws + s.off_part_a) : nullptr, 0,
-                 s.plan.atomic_merge};
+                 (dtype == KNN_F32 && !k64) ? reinterpret_cast<int32_t*>(ws + s.off_part_a)
+                                            : nullptr,
+                 0, s.plan.atomic_merge, k64};
   const float* qscale = s.qb.scale ? reinterpret_cast<const float*>(ws + s.off_qscale) : nullptr;
   e = run_k1(s.plan, a, db_lp, db_scale, db_hnorm, ws + s.off_qlp, qscale, parts, st);
   if (e == cudaErrorNotSupported) return KNN_EUNSUPPORTED;
@@ -565,7 +615,8 @@ knn_status knn_partial_reduce(const void* db_lp, const float* db_scale, const fl
 
 size_t knn_search_exact_workspace(int64_t N, int32_t D, int32_t dtype, int32_t metric, int64_t M,
                                   int32_t K) {
-  SearchArgs a{nullptr, nullptr, nullptr, nullptr, N, D, dtype, metric, nullptr, M, K, N, 0.5, 1};
+  SearchArgs a{nullptr, nullptr, nullptr, nullptr, N, D, dtype, metric, nullptr, M, K, N, 0.5, 1,
+               KNN_BINS_MOD};
   ExactLayout s;
   if (layout_exact(a, &s) != KNN_OK) return 0;
   return s.total;
@@ -576,7 +627,8 @@ knn_status knn_search_exact(const void* db_lp, const float* db_scale, const floa
                             int32_t metric, const float* q, int64_t M, int32_t K,
                             float* out_val, int32_t* out_idx, void* workspace, size_t ws_bytes,
                             void* stream) {
-  SearchArgs a{db_lp, db_scale, db_hnorm, db_f32, N, D, dtype, metric, q, M, K, N, 0.5, 1};
+  SearchArgs a{db_lp, db_scale, db_hnorm, db_f32, N, D, dtype, metric, q, M, K, N, 0.5, 1,
+               KNN_BINS_MOD};
   return exact_impl(a, out_val, out_idx, workspace, ws_bytes, (cudaStream_t)stream);
 }
 
@@ -649,7 +701,9 @@ knn_status knn_profile_read(int32_t kernel_class, double* total_ms, int64_t* lau
 knn_status knn_sync_status(void) {
   cudaError_t e = cudaDeviceSynchronize();
   if (e != cudaSuccess) return cuda_status(e);
-  if (k1_tc_take_timeout()) return KNN_ETIMEOUT;
+  const bool t1 = k1_tc_take_timeout();
+  const bool t2 = k1_tcq_take_timeout();
+  if (t1 || t2) return KNN_ETIMEOUT;
   return KNN_OK;
 }
 

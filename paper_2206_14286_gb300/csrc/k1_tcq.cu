@@ -1,0 +1,414 @@
+// k1_tcq.cu -- PartialReduce with contiguous bins (Alg. 1: l = ShiftRight(j, W),
+// generalised to L balanced runs of rows) fused with a tcgen05 BF16
+// contraction, queries on the tensor-memory lanes.
+//
+// One CTA (384 threads, one per SM) owns 128 queries and a contiguous range
+// of database rows:
+//   warp 0      : TMA producer. The query tile stays in shared memory; tiles of
+//                 128 database rows stream through an S-stage ring. For L2 the
+//                 warp also writes each tile's half norms as an extra K block
+//                 (-h split into three BF16 parts), so the contraction itself
+//                 yields the relaxed score <q,x> - |x|^2/2 (App. A.2, Eq. 19).
+//   warp 1      : TMEM allocation and tcgen05.mma issue (one thread):
+//                 D[128 queries x 128 rows], four accumulator buffers.
+//   warps 4..11 : epilogue. A thread owns one query (its TMEM lane) and half
+//                 of each tile's columns. Columns are consecutive database rows,
+//                 so a run of 32 columns inside one bin is reduced by a single
+//                 tcgen05.ld.red.max (the load returns the 32 scores and their
+//                 maximum). Only when that maximum beats the bin's best so far
+//                 does the thread look for its column; a bin boundary inside a
+//                 run is handled column by column. Each thread keeps just the
+//                 current bin's best score and row; when the bin ends it merges
+//                 them into G[query][bin] with a 64-bit atomicMax on the
+//                 ordered key (score, ~row), so ties keep the smaller row and
+//                 bins split between CTAs merge exactly.
+//   warps 2, 3  : idle.
+// All waits are bounded (see tc_ptx.cuh).
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_bf16.h>
+
+#include "common.cuh"
+#include "kernels.h"
+#include "tc_ptx.cuh"
+
+namespace tpuknn {
+
+namespace {
+
+constexpr int kThreadsQ = 384;
+constexpr int kQ = 128;          // queries per CTA: MMA M, TMEM lanes
+constexpr int kBN = 128;         // database rows per tile: MMA N
+constexpr int kNumAcc = 4;       // accumulator buffers of kBN columns
+constexpr int kSpan = 128;       // bytes of one 128-byte swizzle span
+constexpr int kExtBytes = kBN * 32;  // one K = 16 BF16 block of 128 rows
+
+struct TcqArgs {
+  int64_t N, M, L;
+  int64_t bq, br;                  // bins: q = N / L, r = N % L
+  int64_t rows_per_cta, nranges, nqtiles;
+  int nkb, nksteps, stages;
+  uint32_t a_bytes, tile_bytes, stage_stride;
+  int ext;
+  uint32_t idesc;
+  const float* hnorm;
+  unsigned long long* G;
+};
+
+__device__ __forceinline__ int64_t bin_of(int64_t p, int64_t q, int64_t r) {
+  const int64_t big = r * (q + 1);
+  return p < big ? p / (q + 1) : r + (p - big) / q;
+}
+__device__ __forceinline__ int64_t bin_end(int64_t b, int64_t q, int64_t r) {
+  return (b + 1) * q + min(b + 1, r);
+}
+
+// 32 columns of this thread's lane and their maximum, waited for.
+__device__ __forceinline__ void tmem_ld32_max(uint32_t taddr, float (&r)[32], float& m) {
+  asm volatile(
+      "tcgen05.ld.red.sync.aligned.32x32b.x32.max.f32 "
+      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+      "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, %32, [%33];\n\t"
+      "tcgen05.wait::ld.sync.aligned;"
+      : "=f"(r[0]), "=f"(r[1]), "=f"(r[2]), "=f"(r[3]), "=f"(r[4]), "=f"(r[5]), "=f"(r[6]),
+        "=f"(r[7]), "=f"(r[8]), "=f"(r[9]), "=f"(r[10]), "=f"(r[11]), "=f"(r[12]), "=f"(r[13]),
+        "=f"(r[14]), "=f"(r[15]), "=f"(r[16]), "=f"(r[17]), "=f"(r[18]), "=f"(r[19]),
+        "=f"(r[20]), "=f"(r[21]), "=f"(r[22]), "=f"(r[23]), "=f"(r[24]), "=f"(r[25]),
+        "=f"(r[26]), "=f"(r[27]), "=f"(r[28]), "=f"(r[29]), "=f"(r[30]), "=f"(r[31]), "=f"(m)
+      : "r"(taddr)
+      : "memory");
+}
+
+// byte offset of (row r, 16-byte piece kc) in a K = 16 BF16 block without swizzle
+__device__ __forceinline__ uint32_t ext_off(int r, int kc) {
+  return (uint32_t)((r >> 3) * 256 + kc * 128 + (r & 7) * 16);
+}
+
+__global__ void __launch_bounds__(kThreadsQ, 1)
+k1_tcq_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmQ,
+              const TcqArgs a) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
+                                             ~(uintptr_t)1023);
+  const int S = a.stages;
+  uint8_t* sA = smem;                                   // queries, SW128
+  uint8_t* sAext = sA + a.a_bytes;                      // ones block (L2)
+  uint8_t* sB = sAext + (a.ext ? kExtBytes : 0);        // stages: tile (+ ext block)
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sB + (size_t)S * a.stage_stride);
+  const uint32_t b_full = smem_u32(bars), b_empty = smem_u32(bars + S);
+  const uint32_t b_accf = smem_u32(bars + 2 * S), b_acce = smem_u32(bars + 2 * S + kNumAcc);
+  const uint32_t b_q = smem_u32(bars + 2 * S + 2 * kNumAcc);
+  const uint32_t b_done = smem_u32(bars + 2 * S + 2 * kNumAcc + 1);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * S + 2 * kNumAcc + 2);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t qtile = blockIdx.x % a.nqtiles;
+  const int64_t range = blockIdx.x / a.nqtiles;
+  const int64_t P0 = range * a.rows_per_cta;
+  const int64_t P1 = min(a.N, P0 + a.rows_per_cta);
+  const int nt = (int)cdiv(P1 - P0, kBN);
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < S; ++s) {
+      mbar_init(b_full + 8 * s, a.ext ? 2 : 1);
+      mbar_init(b_empty + 8 * s, 1);
+    }
+    for (int b = 0; b < kNumAcc; ++b) {
+      mbar_init(b_accf + 8 * b, 1);
+      mbar_init(b_acce + 8 * b, 8);
+    }
+    mbar_init(b_q, 1);
+    mbar_init(b_done, 1);
+    *abort_flag = 0;
+    fence_barrier_init();
+  }
+  if (a.ext) {
+    // the queries' ones block: K index 0..2 = 1, the rest 0; and the second
+    // 16-byte piece of every stage's block is always zero
+    const __nv_bfloat16 one = __float2bfloat16_rn(1.0f), zero = __float2bfloat16_rn(0.0f);
+    for (int r = threadIdx.x; r < kQ; r += kThreadsQ) {
+      __nv_bfloat16 v[8] = {one, one, one, zero, zero, zero, zero, zero};
+      *reinterpret_cast<uint4*>(sAext + ext_off(r, 0)) = *reinterpret_cast<uint4*>(v);
+      *reinterpret_cast<uint4*>(sAext + ext_off(r, 1)) = make_uint4(0, 0, 0, 0);
+    }
+    for (int t = threadIdx.x; t < S * kBN; t += kThreadsQ) {
+      uint8_t* ext = sB + (size_t)(t / kBN) * a.stage_stride + a.tile_bytes;
+      *reinterpret_cast<uint4*>(ext + ext_off(t % kBN, 1)) = make_uint4(0, 0, 0, 0);
+    }
+    fence_proxy_async_smem();
+  }
+  if (warp == 1) tmem_alloc(smem_u32(tmem_slot), kNumAcc * kBN);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_base = *tmem_slot;
+
+  if (warp == 0) {
+    // -------------------------------------------------------------- producer
+    if (lane == 0) {
+      mbar_expect_tx(b_q, a.a_bytes);
+      for (int kb = 0; kb < a.nkb; ++kb)
+        tma_load_2d(smem_u32(sA + (size_t)kb * kQ * kSpan), &tmQ, b_q, kb * (kSpan / 2),
+                    (int)(qtile * kQ));
+    }
+    int issued = 0;
+    for (int it = 0; it < nt; ++it) {
+      const int s = it % S;
+      const uint32_t ph = (uint32_t)((it / S) & 1);
+      int ok = 1;
+      if (lane == 0 && it >= S) ok = mbar_wait(b_empty + 8 * s, ph ^ 1u, abort_flag) ? 1 : 0;
+      ok = __shfl_sync(0xffffffffu, ok, 0);
+      if (!ok) break;
+      const int64_t p0 = P0 + (int64_t)it * kBN;
+      uint8_t* st = sB + (size_t)s * a.stage_stride;
+      if (lane == 0) {
+        mbar_expect_tx(b_full + 8 * s, a.tile_bytes);
+        for (int kb = 0; kb < a.nkb; ++kb)
+          tma_load_2d(smem_u32(st + (size_t)kb * kBN * kSpan), &tmX, b_full + 8 * s,
+                      kb * (kSpan / 2), (int)p0);
+      }
+      if (a.ext) {
+        uint8_t* ext = st + a.tile_bytes;
+#pragma unroll
+        for (int u = 0; u < kBN / 32; ++u) {
+          const int r = lane + 32 * u;
+          const int64_t p = p0 + r;
+          const float h = p < a.N ? a.hnorm[p] : 0.0f;
+          const __nv_bfloat16 hi = __float2bfloat16_rn(h);
+          const float rem1 = h - __bfloat162float(hi);
+          const __nv_bfloat16 mid = __float2bfloat16_rn(rem1);
+          const __nv_bfloat16 lo = __float2bfloat16_rn(rem1 - __bfloat162float(mid));
+          const __nv_bfloat16 z = __float2bfloat16_rn(0.0f);
+          __nv_bfloat16 v[8] = {__hneg(hi), __hneg(mid), __hneg(lo), z, z, z, z, z};
+          *reinterpret_cast<uint4*>(ext + ext_off(r, 0)) = *reinterpret_cast<uint4*>(v);
+        }
+        fence_proxy_async_smem();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(b_full + 8 * s);
+      }
+      issued = it + 1;
+    }
+    if (lane == 0) {
+      for (int it = (issued > S ? issued - S : 0); it < issued; ++it)
+        mbar_wait(b_full + 8 * (it % S), (uint32_t)((it / S) & 1), abort_flag);
+      mbar_wait(b_q, 0, abort_flag);
+    }
+    return;
+  }
+  if (warp == 1) {
+    // -------------------------------------------------------------- MMA issuer
+    if (lane == 0) {
+      if (mbar_wait(b_q, 0, abort_flag)) {
+        const uint32_t a_base = smem_u32(sA);
+        for (int it = 0; it < nt; ++it) {
+          const int s = it % S;
+          const uint32_t ph = (uint32_t)((it / S) & 1);
+          const int ab = it % kNumAcc;
+          const uint32_t aph = (uint32_t)((it / kNumAcc) & 1);
+          if (!mbar_wait(b_full + 8 * s, ph, abort_flag)) break;
+          if (it >= kNumAcc && !mbar_wait(b_acce + 8 * ab, aph ^ 1u, abort_flag)) break;
+          tc_fence_after();
+          const uint32_t b_base = smem_u32(sB + (size_t)s * a.stage_stride);
+          const uint32_t d_tmem = tmem_base + (uint32_t)(ab * kBN);
+          for (int ks = 0; ks < a.nksteps; ++ks) {
+            const int kb = ks >> 2, kk = ks & 3;
+            const uint64_t ad = smem_desc_sw128(a_base + kb * kQ * kSpan + kk * 32);
+            const uint64_t bd = smem_desc_sw128(b_base + kb * kBN * kSpan + kk * 32);
+            tc_mma<KNN_BF16>(d_tmem, ad, bd, a.idesc, ks > 0 ? 1u : 0u);
+          }
+          if (a.ext) {
+            const uint64_t ad = smem_desc_noswz(smem_u32(sAext), 128, 256);
+            const uint64_t bd = smem_desc_noswz(b_base + a.tile_bytes, 128, 256);
+            tc_mma<KNN_BF16>(d_tmem, ad, bd, a.idesc, 1u);
+          }
+          tc_commit(b_empty + 8 * s);
+          tc_commit(b_accf + 8 * ab);
+        }
+      }
+      tc_commit(b_done);
+      mbar_wait(b_done, 0, abort_flag);
+    }
+    __syncwarp();
+    asm volatile("bar.sync 1, %0;" ::"n"(32 + 256) : "memory");
+    tc_fence_after();
+    tmem_dealloc(tmem_base, kNumAcc * kBN);
+    return;
+  }
+  if (warp < 4) return;
+
+  // ---------------------------------------------------------------- epilogue
+  const int quad = warp & 3;
+  const int half = (warp - 4) >> 2;
+  const int64_t qi = qtile * kQ + quad * 32 + lane;
+  const bool q_ok = qi < a.M;
+  unsigned long long* gq = a.G + (q_ok ? qi : 0) * a.L;
+  int64_t cur_bin = bin_of(P0, a.bq, a.br);
+  int64_t seg_end = bin_end(cur_bin, a.bq, a.br);
+  float best = __uint_as_float(kNegInfBits);
+  int64_t best_row = -1;
+  auto flush = [&]() {
+    if (q_ok && best_row >= 0) atomicMax(&gq[cur_bin], (unsigned long long)make_key(best, (int32_t)best_row));
+  };
+  for (int it = 0; it < nt; ++it) {
+    const int ab = it % kNumAcc;
+    const uint32_t aph = (uint32_t)((it / kNumAcc) & 1);
+    if (!mbar_wait(b_accf + 8 * ab, aph, abort_flag)) break;
+    tc_fence_after();
+    const int64_t p0 = P0 + (int64_t)it * kBN;
+    const uint32_t tcol =
+        tmem_base + ((uint32_t)(quad * 32) << 16) + (uint32_t)(ab * kBN + half * (kBN / 2));
+#pragma unroll
+    for (int ch = 0; ch < kBN / 64; ++ch) {
+      const int64_t prow = p0 + half * (kBN / 2) + ch * 32;
+      float r[32], m;
+      __syncwarp();
+      tmem_ld32_max(tcol + ch * 32, r, m);
+      if (prow + 32 <= seg_end && prow + 32 <= P1) {
+        // the run lies inside the current bin: one compare per 32 scores
+        if (m > best) {
+          int pos = 0;
+#pragma unroll
+          for (int k = 31; k >= 0; --k) pos = (r[k] == m) ? k : pos;
+          best = m;
+          best_row = prow + pos;
+        }
+      } else {
+#pragma unroll
+        for (int k = 0; k < 32; ++k) {
+          const int64_t p = prow + k;
+          if (p < P1) {
+            while (p >= seg_end) {
+              flush();
+              ++cur_bin;
+              seg_end = bin_end(cur_bin, a.bq, a.br);
+              best = __uint_as_float(kNegInfBits);
+              best_row = -1;
+            }
+            if (r[k] > best) {
+              best = r[k];
+              best_row = p;
+            }
+          }
+        }
+      }
+    }
+    tc_fence_before();
+    __syncwarp();
+    if (lane == 0) mbar_arrive(b_acce + 8 * ab);
+  }
+  tc_fence_before();
+  asm volatile("bar.arrive 1, %0;" ::"n"(32 + 256) : "memory");
+  flush();
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 get_encode_q() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      return nullptr;
+    fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }
+  return fn;
+}
+
+bool make_map_bf16(CUtensorMap* m, const void* base, int64_t rows, int pitch, int box_rows) {
+  auto enc = get_encode_q();
+  if (!enc) return false;
+  cuuint64_t dims[2] = {(cuuint64_t)pitch, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)pitch * 2};
+  cuuint32_t box[2] = {(cuuint32_t)(kSpan / 2), (cuuint32_t)box_rows};
+  cuuint32_t estr[2] = {1, 1};
+  return enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box,
+             estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+struct TcqShape {
+  int nkb, nksteps, stages;
+  uint32_t a_bytes, tile_bytes, stage_stride;
+  size_t smem;
+};
+
+bool tcq_shape(int D, int metric, TcqShape* sh) {
+  const int pitch = (int)round_up(D, 16);
+  sh->nkb = (int)cdiv((int64_t)pitch * 2, kSpan);
+  sh->nksteps = (int)cdiv((int64_t)pitch * 2, 32);
+  sh->a_bytes = (uint32_t)(sh->nkb * kQ * kSpan);
+  sh->tile_bytes = (uint32_t)(sh->nkb * kBN * kSpan);
+  const int ext = metric == KNN_L2;
+  sh->stage_stride = sh->tile_bytes + (ext ? kExtBytes : 0);
+  const size_t fixed = 1024 + sh->a_bytes + (ext ? kExtBytes : 0) + 512;
+  const size_t budget = 227 * 1024;
+  if (fixed + 2 * (size_t)sh->stage_stride > budget) return false;
+  int stages = (int)((budget - fixed) / sh->stage_stride);
+  sh->stages = stages > 8 ? 8 : stages;
+  sh->smem = fixed + (size_t)sh->stages * sh->stage_stride;
+  return true;
+}
+
+}  // namespace
+
+bool k1_tcq_supported(int dtype, int D, int metric) {
+  TcqShape sh;
+  return dtype == KNN_BF16 && metric >= KNN_IP && metric <= KNN_COS && tcq_shape(D, metric, &sh);
+}
+
+void k1_tcq_grid(int64_t N, int64_t M, int64_t* nqtiles, int64_t* nranges, int64_t* rows_per_cta) {
+  const int64_t sms = device_sm_count();
+  *nqtiles = cdiv(M, kQ);
+  int64_t nr = *nqtiles >= sms ? 1 : (sms + *nqtiles / 2) / *nqtiles;
+  const int64_t ntile = cdiv(N, kBN);
+  if (nr > ntile) nr = ntile;
+  if (nr < 1) nr = 1;
+  *rows_per_cta = cdiv(ntile, nr) * kBN;
+  *nranges = cdiv(N, *rows_per_cta);
+}
+
+cudaError_t launch_k1_tcq(int64_t N, int64_t M, int64_t L, int D, int metric, const void* X,
+                          const float* hnorm, const void* Qp, unsigned long long* G,
+                          cudaStream_t st) {
+  TcqShape sh;
+  if (!tcq_shape(D, metric, &sh)) return cudaErrorNotSupported;
+  if (metric == KNN_L2 && !hnorm) return cudaErrorInvalidValue;
+  if ((reinterpret_cast<uintptr_t>(X) & 15) || (reinterpret_cast<uintptr_t>(Qp) & 15))
+    return cudaErrorInvalidValue;
+  if (M <= 0) return cudaSuccess;
+  TcqArgs a{};
+  a.N = N;
+  a.M = M;
+  a.L = L;
+  a.bq = N / L;
+  a.br = N % L;
+  k1_tcq_grid(N, M, &a.nqtiles, &a.nranges, &a.rows_per_cta);
+  a.nkb = sh.nkb;
+  a.nksteps = sh.nksteps;
+  a.stages = sh.stages;
+  a.a_bytes = sh.a_bytes;
+  a.tile_bytes = sh.tile_bytes;
+  a.stage_stride = sh.stage_stride;
+  a.ext = metric == KNN_L2 ? 1 : 0;
+  // D = F32, A = B = BF16, both K-major, N = 128, M = 128
+  a.idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kBN >> 3) << 17) |
+            ((uint32_t)(kQ >> 4) << 24);
+  a.hnorm = hnorm;
+  a.G = G;
+  const int pitch = (int)round_up(D, 16);
+  CUtensorMap mx, mq;
+  if (!make_map_bf16(&mx, X, N, pitch, kBN)) return cudaErrorInvalidValue;
+  if (!make_map_bf16(&mq, Qp, M, pitch, kQ)) return cudaErrorInvalidValue;
+  const int64_t blocks = a.nqtiles * a.nranges;
+  cudaError_t e = cudaFuncSetAttribute(k1_tcq_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)sh.smem);
+  if (e != cudaSuccess) return e;
+  k1_tcq_kernel<<<(unsigned)blocks, kThreadsQ, sh.smem, st>>>(mx, mq, a);
+  return cudaGetLastError();
+}
+
+bool k1_tcq_take_timeout() { return tc_take_timeout_local(); }
+
+}  // namespace tpuknn

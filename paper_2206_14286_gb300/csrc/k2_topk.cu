@@ -88,6 +88,13 @@ struct MergedSource {
   }
 };
 
+// 64-bit keys already merged per (query, bin).
+struct KeySource {
+  const uint64_t* G;
+  int64_t L;
+  __device__ __forceinline__ uint64_t key(int64_t i, int64_t b) const { return G[i * L + b]; }
+};
+
 // Descending sort of KPL keys held in registers (bitonic network).
 template <int KPL>
 __device__ __forceinline__ void reg_sort_desc(uint64_t (&k)[KPL]) {
@@ -239,7 +246,10 @@ cudaError_t launch_merge_bins(const K1Plan& p, Partials parts, float* out_v, int
   const int64_t n = p.M * p.L;
   if (n <= 0) return cudaSuccess;
   const unsigned blocks = (unsigned)cdiv(n, 256);
-  if (parts.a) {
+  if (parts.keys64) {
+    KeySource s{reinterpret_cast<const uint64_t*>(parts.v), p.L};
+    merge_bins_kernel<<<blocks, 256, 0, st>>>(s, p.M, p.L, out_v, out_a);
+  } else if (parts.a) {
     PairSource s{parts.v, parts.a, p.M, p.Lk, p.L, p.nsplits, parts.index_offset, p.g};
     merge_bins_kernel<<<blocks, 256, 0, st>>>(s, p.M, p.L, out_v, out_a);
   } else if (parts.merged) {
@@ -264,6 +274,11 @@ cudaError_t launch_k2(const K1Plan& p, Partials parts, int Kp, const uint64_t* r
                       uint64_t* out_keys, cudaStream_t st) {
   if (p.M <= 0) return cudaSuccess;
   const bool warp = use_warp(p.L, Kp, run_in);
+  if (parts.keys64) {
+    KeySource s{reinterpret_cast<const uint64_t*>(parts.v), p.L};
+    return warp ? run_k2_warp(s, p.M, p.L, Kp, out_keys, st)
+                : run_k2(s, p.M, p.L, Kp, run_in, out_keys, st);
+  }
   if (parts.a) {
     PairSource s{parts.v, parts.a, p.M, p.Lk, p.L, p.nsplits, parts.index_offset, p.g};
     return warp ? run_k2_warp(s, p.M, p.L, Kp, out_keys, st)

@@ -75,24 +75,39 @@ k3_warp_kernel(int64_t M, const uint64_t* __restrict__ cand, int Kp, int K, int 
   const float* q = qf32 + i * q_stride;
   const uint64_t mykey_in = lane < Kp ? cand[i * Kp + lane] : 0;
   uint64_t mine = 0;
-  for (int c = 0; c < Kp; ++c) {
-    const uint64_t key = __shfl_sync(0xffffffffu, mykey_in, c);
-    const int32_t j = key ? key_index(key) : -1;
-    if (j < 0 || j >= N) continue;  // warp-uniform
-    float acc = 0.0f;
+  // 8 candidates at a time: their row loads are independent, so they overlap
+  for (int c0 = 0; c0 < Kp; c0 += 8) {
+    int32_t js[8];
+    float acc[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const uint64_t key = __shfl_sync(0xffffffffu, mykey_in, (c0 + u) & 31);
+      const int32_t j = (c0 + u < Kp && key) ? key_index(key) : -1;
+      js[u] = (j >= 0 && j < N) ? j : -1;
+      acc[u] = 0.0f;
+    }
     for (int d = lane; d < D; d += 32) {
-      const float x = xf32 ? xf32[(int64_t)j * D + d] : load_stored(xlp, dtype, j, pitch, d, xscale);
       const float qq = q[d];
-      if (metric == KNN_L2) {
-        const float t = qq - x;
-        acc = fmaf(t, t, acc);
-      } else {
-        acc = fmaf(qq, x, acc);
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        if (js[u] < 0) continue;  // warp-uniform
+        const float x = xf32 ? xf32[(int64_t)js[u] * D + d]
+                             : load_stored(xlp, dtype, js[u], pitch, d, xscale);
+        if (metric == KNN_L2) {
+          const float t = qq - x;
+          acc[u] = fmaf(t, t, acc[u]);
+        } else {
+          acc[u] = fmaf(qq, x, acc[u]);
+        }
       }
     }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    if (lane == c) mine = make_key(metric == KNN_L2 ? -acc : acc, j);
+    for (int u = 0; u < 8; ++u) {
+      float v = acc[u];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      if (lane == c0 + u && js[u] >= 0) mine = make_key(metric == KNN_L2 ? -v : v, js[u]);
+    }
   }
   // descending bitonic sort across the 32 lanes
 #pragma unroll

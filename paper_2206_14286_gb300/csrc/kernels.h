@@ -42,6 +42,7 @@ struct Partials {
   int32_t* a;       // pair form indices (nullptr otherwise)
   int64_t index_offset;  // added to every decoded index (chunked exact search)
   bool merged;
+  bool keys64;      // v holds [M][L] 64-bit (score, ~index) keys, 0 = empty
 };
 
 // Row preparation; optionally also zeroes zero_n 32-bit words of zero_buf.
@@ -56,6 +57,15 @@ cudaError_t launch_k1_simt(const K1Plan& p, const float* X, const float* hnorm, 
 // outside what the kernel handles.
 cudaError_t launch_k1_tc(const K1Plan& p, const void* X, const float* xscale, const float* hnorm,
                          const void* Qp, const float* qscale, Partials out, cudaStream_t st);
+
+// Tensor-core K1 with contiguous bins, queries on TMEM lanes (BF16):
+// G[M][L] receives ordered 64-bit (score, ~index) keys by atomicMax and must
+// be zero on entry.
+bool k1_tcq_supported(int dtype, int D, int metric);
+cudaError_t launch_k1_tcq(int64_t N, int64_t M, int64_t L, int D, int metric, const void* X,
+                          const float* hnorm, const void* Qp, unsigned long long* G,
+                          cudaStream_t st);
+bool k1_tcq_take_timeout();
 
 // K2: per query, merge the partials of every split and fold and select the
 // best Kp (score, index) keys, sorted. If run_in is given its Kp keys per

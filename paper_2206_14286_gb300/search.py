@@ -6,7 +6,7 @@ and streams. See include/tpuknn.h for the semantics of each call.
 import torch
 
 from . import _lib
-from ._lib import METRIC, DTYPE, check
+from ._lib import METRIC, DTYPE, BINS, check
 
 _ESIZE = {"f32": 4, "bf16": 2, "e4m3": 1}
 
@@ -84,47 +84,53 @@ class Database:
         return int(L) if L else plan_bins(self.N, K, recall_target)
 
     # -- calls -----------------------------------------------------------------
-    def search(self, q, K, L=None, recall_target=0.95, rerank=2, stream=None, out=None):
-        """Approximate search; returns (values M x K float32, indices M x K int32)."""
+    def search(self, q, K, L=None, recall_target=0.95, rerank=2, stream=None, out=None,
+               bins="mod"):
+        """Approximate search; returns (values M x K float32, indices M x K int32).
+
+        bins: "mod" (row j in bin j mod L) or "contiguous" (runs of rows)."""
         q = q.contiguous()
         M = q.shape[0]
         L = self.resolve_L(K, L, recall_target)
         lib = _lib.get()
         nb = lib.knn_search_workspace(self.N, self.D, DTYPE[self.dtype], METRIC[self.metric], M, K,
-                                      L, recall_target, rerank)
+                                      L, BINS[bins], recall_target, rerank)
         if nb == 0:
             raise ValueError("invalid search arguments (N=%d D=%d M=%d K=%d L=%d)"
                              % (self.N, self.D, M, K, L))
-        ws = self._get_ws(("search", M, K, L, rerank), nb)
+        ws = self._get_ws(("search", M, K, L, rerank, bins), nb)
         if out is None:
             val = torch.empty((M, K), dtype=torch.float32, device=self.device)
             idx = torch.empty((M, K), dtype=torch.int32, device=self.device)
         else:
             val, idx = out
         with torch.cuda.device(self.device):
-            check(lib.knn_search(*self._args(), q.data_ptr(), M, K, L, recall_target, rerank,
-                                 val.data_ptr(), idx.data_ptr(), ws.data_ptr(), ws.numel(),
-                                 _stream(stream)), "knn_search")
+            check(lib.knn_search(*self._args(), q.data_ptr(), M, K, L, BINS[bins], recall_target,
+                                 rerank, val.data_ptr(), idx.data_ptr(), ws.data_ptr(),
+                                 ws.numel(), _stream(stream)), "knn_search")
         return val, idx
 
     def search_host(self, q_host, K, L=None, recall_target=0.95, rerank=2, stream=None,
-                    out=None):
+                    out=None, bins="mod"):
         """Search with host queries and host outputs (copies inside the call)."""
         M = q_host.shape[0]
         L = self.resolve_L(K, L, recall_target)
         lib = _lib.get()
         nb = lib.knn_search_host_workspace(self.N, self.D, DTYPE[self.dtype], METRIC[self.metric],
-                                           M, K, L, recall_target, rerank)
-        ws = self._get_ws(("host", M, K, L, rerank), nb)
+                                           M, K, L, BINS[bins], recall_target, rerank)
+        if nb == 0:
+            raise ValueError("invalid search arguments")
+        ws = self._get_ws(("host", M, K, L, rerank, bins), nb)
         if out is None:
             val = torch.empty((M, K), dtype=torch.float32, pin_memory=True)
             idx = torch.empty((M, K), dtype=torch.int32, pin_memory=True)
         else:
             val, idx = out
         with torch.cuda.device(self.device):
-            check(lib.knn_search_host(*self._args(), q_host.data_ptr(), M, K, L, recall_target,
-                                      rerank, val.data_ptr(), idx.data_ptr(), ws.data_ptr(),
-                                      ws.numel(), _stream(stream)), "knn_search_host")
+            check(lib.knn_search_host(*self._args(), q_host.data_ptr(), M, K, L, BINS[bins],
+                                      recall_target, rerank, val.data_ptr(), idx.data_ptr(),
+                                      ws.data_ptr(), ws.numel(), _stream(stream)),
+                  "knn_search_host")
         return val, idx
 
     def search_exact(self, q, K, stream=None):
@@ -144,24 +150,24 @@ class Database:
                                        _stream(stream)), "knn_search_exact")
         return val, idx
 
-    def partial_reduce(self, q, L, stream=None):
+    def partial_reduce(self, q, L, stream=None, bins="mod"):
         """Alg. 1 alone: (V, A), each M x L (internal scores, indices)."""
         q = q.contiguous()
         M = q.shape[0]
         lib = _lib.get()
         nb = lib.knn_partial_reduce_workspace(self.N, self.D, DTYPE[self.dtype],
-                                              METRIC[self.metric], M, L)
+                                              METRIC[self.metric], M, L, BINS[bins])
         if nb == 0:
             raise ValueError("invalid partial-reduce arguments")
-        ws = self._get_ws(("pr", M, L), nb)
+        ws = self._get_ws(("pr", M, L, bins), nb)
         V = torch.empty((M, L), dtype=torch.float32, device=self.device)
         A = torch.empty((M, L), dtype=torch.int32, device=self.device)
         a = self._args()
         with torch.cuda.device(self.device):
             check(lib.knn_partial_reduce(a[0], a[1], a[2], self.N, self.D, a[6], a[7],
-                                         q.data_ptr(), M, L, V.data_ptr(), A.data_ptr(),
-                                         ws.data_ptr(), ws.numel(), _stream(stream)),
-                  "knn_partial_reduce")
+                                         q.data_ptr(), M, L, BINS[bins], V.data_ptr(),
+                                         A.data_ptr(), ws.data_ptr(), ws.numel(),
+                                         _stream(stream)), "knn_partial_reduce")
         return V, A
 
     def backward(self, q, idx, grad_val, want_dq=True, want_dx=True, deterministic=False,

@@ -62,8 +62,19 @@ def reported(S, metric):
     return -S if metric == "l2" else S
 
 
-def bin_best_second(S, L):
+def bin_best_second(S, L, bins="mod"):
     M, N = S.shape
+    if bins == "contiguous":
+        best = np.empty((M, L))
+        second = np.full((M, L), -np.inf)
+        for b, rows in enumerate(np.array_split(np.arange(N), L)):
+            blk = S[:, rows]
+            if rows.size >= 2:
+                part = -np.partition(-blk, 1, axis=1)
+                best[:, b], second[:, b] = part[:, 0], part[:, 1]
+            else:
+                best[:, b] = blk[:, 0]
+        return best, second
     nb = -(-N // L)
     P = np.full((M, nb * L), -np.inf)
     P[:, :N] = S
@@ -74,14 +85,14 @@ def bin_best_second(S, L):
     return P[:, 0, :], np.full((M, L), -np.inf)
 
 
-def decided_mask(S_lp, L, Kp, S_f32, cand, K, tol, tol_final=None):
+def decided_mask(S_lp, L, Kp, S_f32, cand, K, tol, tol_final=None, bins="mod"):
     """Boolean per query; cand = the oracle's Kp candidates (M x Kp).
     tol applies to the bin step, tol_final (default tol) to the FP32 order."""
     if tol_final is None:
         tol_final = tol
     M = S_lp.shape[0]
     ok = np.ones(M, bool)
-    best, second = bin_best_second(S_lp, L)
+    best, second = bin_best_second(S_lp, L, bins)
     w = -np.sort(-best, axis=1)
     if L > Kp:
         ok &= (w[:, Kp - 1] - w[:, Kp]) > 2 * tol
@@ -98,12 +109,21 @@ def decided_mask(S_lp, L, Kp, S_f32, cand, K, tol, tol_final=None):
     return ok
 
 
-def check_search(gpu_val, gpu_idx, orc_val, orc_idx, S_lp, S_f32, L, metric, tol, decided):
+def bin_of_rows(N, L, bins):
+    if bins == "contiguous":
+        return np.concatenate([np.full(len(r), b) for b, r in
+                               enumerate(np.array_split(np.arange(N), L))])
+    return np.arange(N) % L
+
+
+def check_search(gpu_val, gpu_idx, orc_val, orc_idx, S_lp, S_f32, L, metric, tol, decided,
+                 bins="mod"):
     """Asserts the rules above; returns the fraction of decided queries."""
     gpu_val = np.asarray(gpu_val, np.float64)
     gpu_idx = np.asarray(gpu_idx, np.int64)
     M, K = gpu_idx.shape
-    best, _ = bin_best_second(S_lp, L)
+    best, _ = bin_best_second(S_lp, L, bins)
+    owner = bin_of_rows(S_lp.shape[1], L, bins)
     bad = []
     for i in range(M):
         if decided[i]:
@@ -121,7 +141,7 @@ def check_search(gpu_val, gpu_idx, orc_val, orc_idx, S_lp, S_f32, L, metric, tol
         if np.any(np.abs(own - gpu_val[i]) > tol[i]):
             bad.append((i, "own value", own[:6], gpu_val[i][:6]))
             continue
-        if np.any(S_lp[i, j] < best[i, j % L] - tol[i]):
+        if np.any(S_lp[i, j] < best[i, owner[j]] - tol[i]):
             bad.append((i, "not a bin maximum", j[:8]))
     assert not bad, "%d of %d queries disagree, e.g. %s" % (len(bad), M, bad[:3])
     return float(np.mean(decided))

@@ -70,13 +70,13 @@ def test_invalid_arguments_rejected_before_any_launch(lib):
     f = lib.knn_search
     # N = 0, K > N, bad metric, bad dtype, K > L: all EINVAL without touching a device
     base = dict(db=None, sc=None, hn=None, f32=None, N=100, D=8, dt=0, me=0, q=None, M=4, K=3,
-                L=10, r=0.9, rr=1, ov=None, oi=None, ws=None, wsb=0, st=None)
+                L=10, bm=0, r=0.9, rr=1, ov=None, oi=None, ws=None, wsb=0, st=None)
 
     def call(**kw):
         a = dict(base, **kw)
         return f(a["db"], a["sc"], a["hn"], a["f32"], a["N"], a["D"], a["dt"], a["me"], a["q"],
-                 a["M"], a["K"], a["L"], a["r"], a["rr"], a["ov"], a["oi"], a["ws"], a["wsb"],
-                 a["st"])
+                 a["M"], a["K"], a["L"], a["bm"], a["r"], a["rr"], a["ov"], a["oi"], a["ws"],
+                 a["wsb"], a["st"])
 
     assert call(N=0) == _lib.KNN_EINVAL
     assert call(K=101) == _lib.KNN_EINVAL
@@ -87,14 +87,17 @@ def test_invalid_arguments_rejected_before_any_launch(lib):
     assert call(D=5000) == _lib.KNN_EUNSUPPORTED
     assert call() == _lib.KNN_EINVAL           # null pointers
     assert call(M=0) == _lib.KNN_OK            # empty query set is a no-op
+    assert call(bm=7) == _lib.KNN_EINVAL       # unknown bin map
+    assert call(bm=1) == _lib.KNN_EUNSUPPORTED  # contiguous bins: BF16 only
     # workspace queries return 0 for invalid requests
-    assert lib.knn_search_workspace(0, 8, 0, 0, 4, 3, 10, 0.9, 1) == 0
+    assert lib.knn_search_workspace(0, 8, 0, 0, 4, 3, 10, 0, 0.9, 1) == 0
     assert lib.knn_search_exact_workspace(100, 8, 0, 0, 4, 101) == 0
-    assert lib.knn_partial_reduce_workspace(100, 8, 0, 0, 4, 101) == 0
+    assert lib.knn_partial_reduce_workspace(100, 8, 0, 0, 4, 101, 0) == 0
 
 
 def test_workspace_grows_with_queries(lib):
-    a = lib.knn_search_workspace(10 ** 6, 128, 1, 1, 1024, 10, 256, 0.95, 2)
-    b = lib.knn_search_workspace(10 ** 6, 128, 1, 1, 2048, 10, 256, 0.95, 2)
-    assert 0 < a < b
-    assert lib.knn_search_host_workspace(10 ** 6, 128, 1, 1, 1024, 10, 256, 0.95, 2) > a
+    for bm in (0, 1):
+        a = lib.knn_search_workspace(10 ** 6, 128, 1, 1, 1024, 10, 256, bm, 0.95, 2)
+        b = lib.knn_search_workspace(10 ** 6, 128, 1, 1, 2048, 10, 256, bm, 0.95, 2)
+        assert 0 < a < b
+        assert lib.knn_search_host_workspace(10 ** 6, 128, 1, 1, 1024, 10, 256, bm, 0.95, 2) > a
