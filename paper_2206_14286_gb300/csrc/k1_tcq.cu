@@ -5,10 +5,11 @@
 // One CTA (384 threads, one per SM) owns 128 queries and a contiguous range
 // of database rows:
 //   warp 0      : TMA producer. The query tile stays in shared memory; tiles of
-//                 128 database rows stream through an S-stage ring. For L2 the
-//                 warp also writes each tile's half norms as an extra K block
+//                 128 database rows stream through an S-stage ring.
+//   warp 2      : (L2 only) writes each tile's half norms as an extra K block
 //                 (-h split into three BF16 parts), so the contraction itself
-//                 yields the relaxed score <q,x> - |x|^2/2 (App. A.2, Eq. 19).
+//                 yields the relaxed score <q,x> - |x|^2/2 (App. A.2, Eq. 19);
+//                 its global loads run four tiles ahead of the ring.
 //   warp 1      : TMEM allocation and tcgen05.mma issue (one thread):
 //                 D[128 queries x 128 rows], four accumulator buffers.
 //   warps 4..11 : epilogue. A thread owns one query (its TMEM lane) and half
@@ -22,7 +23,7 @@
 //                 them into G[query][bin] with a 64-bit atomicMax on the
 //                 ordered key (score, ~row), so ties keep the smaller row and
 //                 bins split between CTAs merge exactly.
-//   warps 2, 3  : idle.
+//   warp 3      : idle.
 // All waits are bounded (see tc_ptx.cuh).
 #include <cuda.h>
 #include <cudaTypedefs.h>
@@ -63,19 +64,29 @@ __device__ __forceinline__ int64_t bin_end(int64_t b, int64_t q, int64_t r) {
   return (b + 1) * q + min(b + 1, r);
 }
 
-// 32 columns of this thread's lane and their maximum, waited for.
-__device__ __forceinline__ void tmem_ld32_max(uint32_t taddr, float (&r)[32], float& m) {
+// Two runs of 32 columns of this thread's lane and their maxima, waited for.
+__device__ __forceinline__ void tmem_ld2x32_max(uint32_t taddr, float (&r)[32], float& m,
+                                                float (&r2)[32], float& m2) {
   asm volatile(
       "tcgen05.ld.red.sync.aligned.32x32b.x32.max.f32 "
       "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
-      "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, %32, [%33];\n\t"
+      "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, %32, [%66];\n\t"
+      "tcgen05.ld.red.sync.aligned.32x32b.x32.max.f32 "
+      "{%33, %34, %35, %36, %37, %38, %39, %40, %41, %42, %43, %44, %45, %46, %47, %48, "
+      "%49, %50, %51, %52, %53, %54, %55, %56, %57, %58, %59, %60, %61, %62, %63, %64}, %65, [%67];\n\t"
       "tcgen05.wait::ld.sync.aligned;"
       : "=f"(r[0]), "=f"(r[1]), "=f"(r[2]), "=f"(r[3]), "=f"(r[4]), "=f"(r[5]), "=f"(r[6]),
         "=f"(r[7]), "=f"(r[8]), "=f"(r[9]), "=f"(r[10]), "=f"(r[11]), "=f"(r[12]), "=f"(r[13]),
         "=f"(r[14]), "=f"(r[15]), "=f"(r[16]), "=f"(r[17]), "=f"(r[18]), "=f"(r[19]),
         "=f"(r[20]), "=f"(r[21]), "=f"(r[22]), "=f"(r[23]), "=f"(r[24]), "=f"(r[25]),
-        "=f"(r[26]), "=f"(r[27]), "=f"(r[28]), "=f"(r[29]), "=f"(r[30]), "=f"(r[31]), "=f"(m)
-      : "r"(taddr)
+        "=f"(r[26]), "=f"(r[27]), "=f"(r[28]), "=f"(r[29]), "=f"(r[30]), "=f"(r[31]), "=f"(m),
+        "=f"(r2[0]), "=f"(r2[1]), "=f"(r2[2]), "=f"(r2[3]), "=f"(r2[4]), "=f"(r2[5]),
+        "=f"(r2[6]), "=f"(r2[7]), "=f"(r2[8]), "=f"(r2[9]), "=f"(r2[10]), "=f"(r2[11]),
+        "=f"(r2[12]), "=f"(r2[13]), "=f"(r2[14]), "=f"(r2[15]), "=f"(r2[16]), "=f"(r2[17]),
+        "=f"(r2[18]), "=f"(r2[19]), "=f"(r2[20]), "=f"(r2[21]), "=f"(r2[22]), "=f"(r2[23]),
+        "=f"(r2[24]), "=f"(r2[25]), "=f"(r2[26]), "=f"(r2[27]), "=f"(r2[28]), "=f"(r2[29]),
+        "=f"(r2[30]), "=f"(r2[31]), "=f"(m2)
+      : "r"(taddr), "r"(taddr + 32u)
       : "memory");
 }
 
@@ -168,25 +179,6 @@ k1_tcq_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
           tma_load_2d(smem_u32(st + (size_t)kb * kBN * kSpan), &tmX, b_full + 8 * s,
                       kb * (kSpan / 2), (int)p0);
       }
-      if (a.ext) {
-        uint8_t* ext = st + a.tile_bytes;
-#pragma unroll
-        for (int u = 0; u < kBN / 32; ++u) {
-          const int r = lane + 32 * u;
-          const int64_t p = p0 + r;
-          const float h = p < a.N ? a.hnorm[p] : 0.0f;
-          const __nv_bfloat16 hi = __float2bfloat16_rn(h);
-          const float rem1 = h - __bfloat162float(hi);
-          const __nv_bfloat16 mid = __float2bfloat16_rn(rem1);
-          const __nv_bfloat16 lo = __float2bfloat16_rn(rem1 - __bfloat162float(mid));
-          const __nv_bfloat16 z = __float2bfloat16_rn(0.0f);
-          __nv_bfloat16 v[8] = {__hneg(hi), __hneg(mid), __hneg(lo), z, z, z, z, z};
-          *reinterpret_cast<uint4*>(ext + ext_off(r, 0)) = *reinterpret_cast<uint4*>(v);
-        }
-        fence_proxy_async_smem();
-        __syncwarp();
-        if (lane == 0) mbar_arrive(b_full + 8 * s);
-      }
       issued = it + 1;
     }
     if (lane == 0) {
@@ -235,6 +227,55 @@ k1_tcq_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
     tmem_dealloc(tmem_base, kNumAcc * kBN);
     return;
   }
+  if (warp == 2) {
+    // ---------------------------------------------------------- L2 half norms
+    if (!a.ext) return;
+    // each lane owns rows lane, lane+32, lane+64, lane+96 of every tile; the
+    // loads of four tiles are in flight at a time (h0 = the current tile)
+    float h0[4], h1[4], h2[4], h3[4];
+    auto load = [&](int it, float (&h)[4]) {
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int64_t p = P0 + (int64_t)it * kBN + lane + 32 * u;
+        h[u] = (it < nt && p < a.N) ? a.hnorm[p] : 0.0f;
+      }
+    };
+    load(0, h0);
+    load(1, h1);
+    load(2, h2);
+    load(3, h3);
+    for (int it = 0; it < nt; ++it) {
+      const int s = it % S;
+      const uint32_t ph = (uint32_t)((it / S) & 1);
+      int ok = 1;
+      if (lane == 0 && it >= S) ok = mbar_wait(b_empty + 8 * s, ph ^ 1u, abort_flag) ? 1 : 0;
+      ok = __shfl_sync(0xffffffffu, ok, 0);
+      if (!ok) break;
+      uint8_t* ext = sB + (size_t)s * a.stage_stride + a.tile_bytes;
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const float h = h0[u];
+        const __nv_bfloat16 hi = __float2bfloat16_rn(h);
+        const float rem1 = h - __bfloat162float(hi);
+        const __nv_bfloat16 mid = __float2bfloat16_rn(rem1);
+        const __nv_bfloat16 lo = __float2bfloat16_rn(rem1 - __bfloat162float(mid));
+        const __nv_bfloat16 z = __float2bfloat16_rn(0.0f);
+        __nv_bfloat16 v[8] = {__hneg(hi), __hneg(mid), __hneg(lo), z, z, z, z, z};
+        *reinterpret_cast<uint4*>(ext + ext_off(lane + 32 * u, 0)) = *reinterpret_cast<uint4*>(v);
+      }
+      fence_proxy_async_smem();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(b_full + 8 * s);
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        h0[u] = h1[u];
+        h1[u] = h2[u];
+        h2[u] = h3[u];
+      }
+      load(it + 4, h3);
+    }
+    return;
+  }
   if (warp < 4) return;
 
   // ---------------------------------------------------------------- epilogue
@@ -258,12 +299,14 @@ k1_tcq_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
     const int64_t p0 = P0 + (int64_t)it * kBN;
     const uint32_t tcol =
         tmem_base + ((uint32_t)(quad * 32) << 16) + (uint32_t)(ab * kBN + half * (kBN / 2));
+    float rr[2][32], mm[2];
+    __syncwarp();
+    tmem_ld2x32_max(tcol, rr[0], mm[0], rr[1], mm[1]);
 #pragma unroll
     for (int ch = 0; ch < kBN / 64; ++ch) {
       const int64_t prow = p0 + half * (kBN / 2) + ch * 32;
-      float r[32], m;
-      __syncwarp();
-      tmem_ld32_max(tcol + ch * 32, r, m);
+      float(&r)[32] = rr[ch];
+      const float m = mm[ch];
       if (prow + 32 <= seg_end && prow + 32 <= P1) {
         // the run lies inside the current bin: one compare per 32 scores
         if (m > best) {

