@@ -12,11 +12,11 @@
 //                 its global loads run four tiles ahead of the ring.
 //   warp 1      : TMEM allocation and tcgen05.mma issue (one thread):
 //                 D[128 queries x 128 rows], four accumulator buffers.
-//   warps 4..11 : epilogue. A thread owns one query (its TMEM lane) and half
-//                 of each tile's columns. Columns are consecutive database rows,
-//                 so a run of 32 columns inside one bin is reduced by a single
-//                 tcgen05.ld.red.max (the load returns the 32 scores and their
-//                 maximum). Only when that maximum beats the bin's best so far
+//   warps 4..11 : epilogue, two warpgroups taking alternate tiles. A thread owns
+//                 one query (its TMEM lane). Columns are consecutive database
+//                 rows, so a run of 64 columns inside one bin is reduced by a
+//                 single tcgen05.ld.red.max (the load returns the 64 scores and
+//                 their maximum). Only when that maximum beats the bin's best so far
 //                 does the thread look for its column; a bin boundary inside a
 //                 run is handled column by column. Each thread keeps just the
 //                 current bin's best score and row; when the bin ends it merges
@@ -64,29 +64,17 @@ __device__ __forceinline__ int64_t bin_end(int64_t b, int64_t q, int64_t r) {
   return (b + 1) * q + min(b + 1, r);
 }
 
-// Two runs of 32 columns of this thread's lane and their maxima, waited for.
-__device__ __forceinline__ void tmem_ld2x32_max(uint32_t taddr, float (&r)[32], float& m,
-                                                float (&r2)[32], float& m2) {
+// The 128 columns of this thread's lane as two runs of 64, with the maximum
+// of each run (tcgen05.ld.red), waited for.
+__device__ __forceinline__ void tmem_ld2x64_max(uint32_t taddr, float (&r)[64], float& m,
+                                                float (&r2)[64], float& m2) {
   asm volatile(
-      "tcgen05.ld.red.sync.aligned.32x32b.x32.max.f32 "
-      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
-      "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, %32, [%66];\n\t"
-      "tcgen05.ld.red.sync.aligned.32x32b.x32.max.f32 "
-      "{%33, %34, %35, %36, %37, %38, %39, %40, %41, %42, %43, %44, %45, %46, %47, %48, "
-      "%49, %50, %51, %52, %53, %54, %55, %56, %57, %58, %59, %60, %61, %62, %63, %64}, %65, [%67];\n\t"
+      "tcgen05.ld.red.sync.aligned.32x32b.x64.max.f32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32,%33,%34,%35,%36,%37,%38,%39,%40,%41,%42,%43,%44,%45,%46,%47,%48,%49,%50,%51,%52,%53,%54,%55,%56,%57,%58,%59,%60,%61,%62,%63}, %64, [%130];\n\t"
+      "tcgen05.ld.red.sync.aligned.32x32b.x64.max.f32 {%65,%66,%67,%68,%69,%70,%71,%72,%73,%74,%75,%76,%77,%78,%79,%80,%81,%82,%83,%84,%85,%86,%87,%88,%89,%90,%91,%92,%93,%94,%95,%96,%97,%98,%99,%100,%101,%102,%103,%104,%105,%106,%107,%108,%109,%110,%111,%112,%113,%114,%115,%116,%117,%118,%119,%120,%121,%122,%123,%124,%125,%126,%127,%128}, %129, [%131];\n\t"
       "tcgen05.wait::ld.sync.aligned;"
-      : "=f"(r[0]), "=f"(r[1]), "=f"(r[2]), "=f"(r[3]), "=f"(r[4]), "=f"(r[5]), "=f"(r[6]),
-        "=f"(r[7]), "=f"(r[8]), "=f"(r[9]), "=f"(r[10]), "=f"(r[11]), "=f"(r[12]), "=f"(r[13]),
-        "=f"(r[14]), "=f"(r[15]), "=f"(r[16]), "=f"(r[17]), "=f"(r[18]), "=f"(r[19]),
-        "=f"(r[20]), "=f"(r[21]), "=f"(r[22]), "=f"(r[23]), "=f"(r[24]), "=f"(r[25]),
-        "=f"(r[26]), "=f"(r[27]), "=f"(r[28]), "=f"(r[29]), "=f"(r[30]), "=f"(r[31]), "=f"(m),
-        "=f"(r2[0]), "=f"(r2[1]), "=f"(r2[2]), "=f"(r2[3]), "=f"(r2[4]), "=f"(r2[5]),
-        "=f"(r2[6]), "=f"(r2[7]), "=f"(r2[8]), "=f"(r2[9]), "=f"(r2[10]), "=f"(r2[11]),
-        "=f"(r2[12]), "=f"(r2[13]), "=f"(r2[14]), "=f"(r2[15]), "=f"(r2[16]), "=f"(r2[17]),
-        "=f"(r2[18]), "=f"(r2[19]), "=f"(r2[20]), "=f"(r2[21]), "=f"(r2[22]), "=f"(r2[23]),
-        "=f"(r2[24]), "=f"(r2[25]), "=f"(r2[26]), "=f"(r2[27]), "=f"(r2[28]), "=f"(r2[29]),
-        "=f"(r2[30]), "=f"(r2[31]), "=f"(m2)
-      : "r"(taddr), "r"(taddr + 32u)
+      : "=f"(r[0]), "=f"(r[1]), "=f"(r[2]), "=f"(r[3]), "=f"(r[4]), "=f"(r[5]), "=f"(r[6]), "=f"(r[7]), "=f"(r[8]), "=f"(r[9]), "=f"(r[10]), "=f"(r[11]), "=f"(r[12]), "=f"(r[13]), "=f"(r[14]), "=f"(r[15]), "=f"(r[16]), "=f"(r[17]), "=f"(r[18]), "=f"(r[19]), "=f"(r[20]), "=f"(r[21]), "=f"(r[22]), "=f"(r[23]), "=f"(r[24]), "=f"(r[25]), "=f"(r[26]), "=f"(r[27]), "=f"(r[28]), "=f"(r[29]), "=f"(r[30]), "=f"(r[31]), "=f"(r[32]), "=f"(r[33]), "=f"(r[34]), "=f"(r[35]), "=f"(r[36]), "=f"(r[37]), "=f"(r[38]), "=f"(r[39]), "=f"(r[40]), "=f"(r[41]), "=f"(r[42]), "=f"(r[43]), "=f"(r[44]), "=f"(r[45]), "=f"(r[46]), "=f"(r[47]), "=f"(r[48]), "=f"(r[49]), "=f"(r[50]), "=f"(r[51]), "=f"(r[52]), "=f"(r[53]), "=f"(r[54]), "=f"(r[55]), "=f"(r[56]), "=f"(r[57]), "=f"(r[58]), "=f"(r[59]), "=f"(r[60]), "=f"(r[61]), "=f"(r[62]), "=f"(r[63]), "=f"(m),
+        "=f"(r2[0]), "=f"(r2[1]), "=f"(r2[2]), "=f"(r2[3]), "=f"(r2[4]), "=f"(r2[5]), "=f"(r2[6]), "=f"(r2[7]), "=f"(r2[8]), "=f"(r2[9]), "=f"(r2[10]), "=f"(r2[11]), "=f"(r2[12]), "=f"(r2[13]), "=f"(r2[14]), "=f"(r2[15]), "=f"(r2[16]), "=f"(r2[17]), "=f"(r2[18]), "=f"(r2[19]), "=f"(r2[20]), "=f"(r2[21]), "=f"(r2[22]), "=f"(r2[23]), "=f"(r2[24]), "=f"(r2[25]), "=f"(r2[26]), "=f"(r2[27]), "=f"(r2[28]), "=f"(r2[29]), "=f"(r2[30]), "=f"(r2[31]), "=f"(r2[32]), "=f"(r2[33]), "=f"(r2[34]), "=f"(r2[35]), "=f"(r2[36]), "=f"(r2[37]), "=f"(r2[38]), "=f"(r2[39]), "=f"(r2[40]), "=f"(r2[41]), "=f"(r2[42]), "=f"(r2[43]), "=f"(r2[44]), "=f"(r2[45]), "=f"(r2[46]), "=f"(r2[47]), "=f"(r2[48]), "=f"(r2[49]), "=f"(r2[50]), "=f"(r2[51]), "=f"(r2[52]), "=f"(r2[53]), "=f"(r2[54]), "=f"(r2[55]), "=f"(r2[56]), "=f"(r2[57]), "=f"(r2[58]), "=f"(r2[59]), "=f"(r2[60]), "=f"(r2[61]), "=f"(r2[62]), "=f"(r2[63]), "=f"(m2)
+      : "r"(taddr), "r"(taddr + 64u)
       : "memory");
 }
 
@@ -127,7 +115,7 @@ k1_tcq_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
     }
     for (int b = 0; b < kNumAcc; ++b) {
       mbar_init(b_accf + 8 * b, 1);
-      mbar_init(b_acce + 8 * b, 8);
+      mbar_init(b_acce + 8 * b, 4);
     }
     mbar_init(b_q, 1);
     mbar_init(b_done, 1);
@@ -231,8 +219,8 @@ k1_tcq_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
     // ---------------------------------------------------------- L2 half norms
     if (!a.ext) return;
     // each lane owns rows lane, lane+32, lane+64, lane+96 of every tile; the
-    // loads of four tiles are in flight at a time (h0 = the current tile)
-    float h0[4], h1[4], h2[4], h3[4];
+    // loads of the next four tiles are in flight while a tile is written
+    float hb[4][4];
     auto load = [&](int it, float (&h)[4]) {
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
@@ -240,39 +228,41 @@ k1_tcq_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
         h[u] = (it < nt && p < a.N) ? a.hnorm[p] : 0.0f;
       }
     };
-    load(0, h0);
-    load(1, h1);
-    load(2, h2);
-    load(3, h3);
-    for (int it = 0; it < nt; ++it) {
-      const int s = it % S;
-      const uint32_t ph = (uint32_t)((it / S) & 1);
-      int ok = 1;
-      if (lane == 0 && it >= S) ok = mbar_wait(b_empty + 8 * s, ph ^ 1u, abort_flag) ? 1 : 0;
-      ok = __shfl_sync(0xffffffffu, ok, 0);
-      if (!ok) break;
-      uint8_t* ext = sB + (size_t)s * a.stage_stride + a.tile_bytes;
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const float h = h0[u];
-        const __nv_bfloat16 hi = __float2bfloat16_rn(h);
-        const float rem1 = h - __bfloat162float(hi);
-        const __nv_bfloat16 mid = __float2bfloat16_rn(rem1);
-        const __nv_bfloat16 lo = __float2bfloat16_rn(rem1 - __bfloat162float(mid));
-        const __nv_bfloat16 z = __float2bfloat16_rn(0.0f);
-        __nv_bfloat16 v[8] = {__hneg(hi), __hneg(mid), __hneg(lo), z, z, z, z, z};
-        *reinterpret_cast<uint4*>(ext + ext_off(lane + 32 * u, 0)) = *reinterpret_cast<uint4*>(v);
-      }
-      fence_proxy_async_smem();
-      __syncwarp();
-      if (lane == 0) mbar_arrive(b_full + 8 * s);
+    for (int k = 0; k < 4; ++k) load(k, hb[k]);
+    bool run = true;
+    for (int it0 = 0; it0 < nt && run; it0 += 4) {
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        h0[u] = h1[u];
-        h1[u] = h2[u];
-        h2[u] = h3[u];
+      for (int k = 0; k < 4; ++k) {
+        const int it = it0 + k;
+        if (it >= nt || !run) break;
+        const int s = it % S;
+        const uint32_t ph = (uint32_t)((it / S) & 1);
+        int ok = 1;
+        if (lane == 0 && it >= S) ok = mbar_wait(b_empty + 8 * s, ph ^ 1u, abort_flag) ? 1 : 0;
+        ok = __shfl_sync(0xffffffffu, ok, 0);
+        if (!ok) {
+          run = false;
+          break;
+        }
+        uint8_t* ext = sB + (size_t)s * a.stage_stride + a.tile_bytes;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const float h = hb[k][u];
+          const __nv_bfloat16 hi = __float2bfloat16_rn(h);
+          const float rem1 = h - __bfloat162float(hi);
+          const __nv_bfloat16 mid = __float2bfloat16_rn(rem1);
+          const __nv_bfloat16 lo = __float2bfloat16_rn(rem1 - __bfloat162float(mid));
+          const __nv_bfloat16 z = __float2bfloat16_rn(0.0f);
+          __nv_bfloat16 v[8] = {__hneg(hi), __hneg(mid), __hneg(lo), z, z, z, z, z};
+          *reinterpret_cast<uint4*>(ext + ext_off(lane + 32 * u, 0)) =
+              *reinterpret_cast<uint4*>(v);
+        }
+        fence_proxy_async_smem();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(b_full + 8 * s);
+        load(it + 4, hb[k]);
       }
-      load(it + 4, h3);
     }
     return;
   }
@@ -280,7 +270,7 @@ k1_tcq_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
 
   // ---------------------------------------------------------------- epilogue
   const int quad = warp & 3;
-  const int half = (warp - 4) >> 2;
+  const int wg = (warp - 4) >> 2;  // tiles it with it % 2 == wg
   const int64_t qi = qtile * kQ + quad * 32 + lane;
   const bool q_ok = qi < a.M;
   unsigned long long* gq = a.G + (q_ok ? qi : 0) * a.L;
@@ -289,36 +279,39 @@ k1_tcq_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
   float best = __uint_as_float(kNegInfBits);
   int64_t best_row = -1;
   auto flush = [&]() {
-    if (q_ok && best_row >= 0) atomicMax(&gq[cur_bin], (unsigned long long)make_key(best, (int32_t)best_row));
+    if (q_ok && best_row >= 0)
+      atomicMax(&gq[cur_bin], (unsigned long long)make_key(best, (int32_t)best_row));
   };
-  for (int it = 0; it < nt; ++it) {
+  for (int it = wg; it < nt; it += 2) {
     const int ab = it % kNumAcc;
     const uint32_t aph = (uint32_t)((it / kNumAcc) & 1);
     if (!mbar_wait(b_accf + 8 * ab, aph, abort_flag)) break;
     tc_fence_after();
     const int64_t p0 = P0 + (int64_t)it * kBN;
-    const uint32_t tcol =
-        tmem_base + ((uint32_t)(quad * 32) << 16) + (uint32_t)(ab * kBN + half * (kBN / 2));
-    float rr[2][32], mm[2];
+    const uint32_t tcol = tmem_base + ((uint32_t)(quad * 32) << 16) + (uint32_t)(ab * kBN);
+    float rr[2][64], mm[2];
     __syncwarp();
-    tmem_ld2x32_max(tcol, rr[0], mm[0], rr[1], mm[1]);
+    tmem_ld2x64_max(tcol, rr[0], mm[0], rr[1], mm[1]);
+    tc_fence_before();
+    __syncwarp();
+    if (lane == 0) mbar_arrive(b_acce + 8 * ab);  // the scores are in registers now
 #pragma unroll
-    for (int ch = 0; ch < kBN / 64; ++ch) {
-      const int64_t prow = p0 + half * (kBN / 2) + ch * 32;
-      float(&r)[32] = rr[ch];
+    for (int ch = 0; ch < 2; ++ch) {
+      const int64_t prow = p0 + ch * 64;
+      float(&r)[64] = rr[ch];
       const float m = mm[ch];
-      if (prow + 32 <= seg_end && prow + 32 <= P1) {
-        // the run lies inside the current bin: one compare per 32 scores
+      if (prow + 64 <= seg_end && prow + 64 <= P1) {
+        // the run lies inside the current bin: one compare per 64 scores
         if (m > best) {
           int pos = 0;
 #pragma unroll
-          for (int k = 31; k >= 0; --k) pos = (r[k] == m) ? k : pos;
+          for (int k = 63; k >= 0; --k) pos = (r[k] == m) ? k : pos;
           best = m;
           best_row = prow + pos;
         }
       } else {
 #pragma unroll
-        for (int k = 0; k < 32; ++k) {
+        for (int k = 0; k < 64; ++k) {
           const int64_t p = prow + k;
           if (p < P1) {
             while (p >= seg_end) {
@@ -336,9 +329,6 @@ k1_tcq_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
         }
       }
     }
-    tc_fence_before();
-    __syncwarp();
-    if (lane == 0) mbar_arrive(b_acce + 8 * ab);
   }
   tc_fence_before();
   asm volatile("bar.arrive 1, %0;" ::"n"(32 + 256) : "memory");
