@@ -78,6 +78,18 @@ __device__ __forceinline__ void tmem_ld2x64_max(uint32_t taddr, float (&r)[64], 
       : "memory");
 }
 
+// One column of this thread's lane (runtime column), waited for.
+__device__ __forceinline__ float tmem_ld1(uint32_t taddr) {
+  float v;
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x1.b32 {%0}, [%1];\n\t"
+      "tcgen05.wait::ld.sync.aligned;"
+      : "=f"(v)
+      : "r"(taddr)
+      : "memory");
+  return v;
+}
+
 // byte offset of (row r, 16-byte piece kc) in a K = 16 BF16 block without swizzle
 __device__ __forceinline__ uint32_t ext_off(int r, int kc) {
   return (uint32_t)((r >> 3) * 256 + kc * 128 + (r & 7) * 16);
@@ -292,42 +304,45 @@ k1_tcq_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
     float rr[2][64], mm[2];
     __syncwarp();
     tmem_ld2x64_max(tcol, rr[0], mm[0], rr[1], mm[1]);
-    tc_fence_before();
-    __syncwarp();
-    if (lane == 0) mbar_arrive(b_acce + 8 * ab);  // the scores are in registers now
+    if (p0 + kBN <= seg_end && p0 + kBN <= P1) {
+      // common case: the tile lies inside the current bin (warp-uniform);
+      // release the buffer at once, then one compare per 64 scores
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(b_acce + 8 * ab);
 #pragma unroll
-    for (int ch = 0; ch < 2; ++ch) {
-      const int64_t prow = p0 + ch * 64;
-      float(&r)[64] = rr[ch];
-      const float m = mm[ch];
-      if (prow + 64 <= seg_end && prow + 64 <= P1) {
-        // the run lies inside the current bin: one compare per 64 scores
+      for (int ch = 0; ch < 2; ++ch) {
+        const float m = mm[ch];
         if (m > best) {
           int pos = 0;
 #pragma unroll
-          for (int k = 63; k >= 0; --k) pos = (r[k] == m) ? k : pos;
+          for (int k = 63; k >= 0; --k) pos = (rr[ch][k] == m) ? k : pos;
           best = m;
-          best_row = prow + pos;
-        }
-      } else {
-#pragma unroll
-        for (int k = 0; k < 64; ++k) {
-          const int64_t p = prow + k;
-          if (p < P1) {
-            while (p >= seg_end) {
-              flush();
-              ++cur_bin;
-              seg_end = bin_end(cur_bin, a.bq, a.br);
-              best = __uint_as_float(kNegInfBits);
-              best_row = -1;
-            }
-            if (r[k] > best) {
-              best = r[k];
-              best_row = p;
-            }
-          }
+          best_row = p0 + ch * 64 + pos;
         }
       }
+    } else {
+      // a bin boundary or the end of the range falls in this tile (rare):
+      // walk its columns one by one, re-reading them from tensor memory
+      for (int k = 0; k < kBN; ++k) {
+        const float v = tmem_ld1(tcol + (uint32_t)k);
+        const int64_t p = p0 + k;
+        if (p >= P1) break;  // warp-uniform
+        while (p >= seg_end) {
+          flush();
+          ++cur_bin;
+          seg_end = bin_end(cur_bin, a.bq, a.br);
+          best = __uint_as_float(kNegInfBits);
+          best_row = -1;
+        }
+        if (v > best) {
+          best = v;
+          best_row = p;
+        }
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(b_acce + 8 * ab);
     }
   }
   tc_fence_before();
