@@ -3,20 +3,23 @@
 // contraction, queries on the tensor-memory lanes.
 //
 // One CTA (384 threads, one per SM) owns 128 queries and a contiguous range
-// of database rows:
-//   warp 0      : TMA producer. The query tile stays in shared memory; tiles of
-//                 128 database rows stream through an S-stage ring.
+// of database rows, walked in tiles of 256 rows:
+//   warp 0      : TMA producer. The query tile stays in shared memory; each
+//                 tile's 128-byte K blocks (256 rows x 64 BF16) stream through
+//                 an S-stage ring.
 //   warp 2      : (L2 only) writes each tile's half norms as an extra K block
-//                 (-h split into three BF16 parts), so the contraction itself
-//                 yields the relaxed score <q,x> - |x|^2/2 (App. A.2, Eq. 19);
-//                 its global loads run four tiles ahead of the ring.
+//                 (-h split into three BF16 parts) into a 2-slot ring, so the
+//                 contraction itself yields the relaxed score <q,x> - |x|^2/2
+//                 (App. A.2, Eq. 19); its global loads run four tiles ahead.
 //   warp 1      : TMEM allocation and tcgen05.mma issue (one thread):
-//                 D[128 queries x 128 rows], four accumulator buffers.
-//   warps 4..11 : epilogue, two warpgroups taking alternate tiles. A thread owns
-//                 one query (its TMEM lane). Columns are consecutive database
-//                 rows, so a run of 64 columns inside one bin is reduced by a
-//                 single tcgen05.ld.red.max (the load returns the 64 scores and
-//                 their maximum). Only when that maximum beats the bin's best so far
+//                 D[128 queries x 256 rows] (M = 128, N = 256: 128 cycles of
+//                 tensor work per instruction), two accumulator buffers.
+//   warps 4..11 : epilogue, two warpgroups taking alternate tiles (one
+//                 accumulator buffer each). A thread owns one query (its TMEM
+//                 lane). Columns are consecutive database rows, so a run of 64
+//                 columns inside one bin is reduced by a single
+//                 tcgen05.ld.red.max (the load returns the 64 scores and their
+//                 maximum). Only when that maximum beats the bin's best so far
 //                 does the thread look for its column; a bin boundary inside a
 //                 run is handled column by column. Each thread keeps just the
 //                 current bin's best score and row; when the bin ends it merges
@@ -39,17 +42,20 @@ namespace {
 
 constexpr int kThreadsQ = 384;
 constexpr int kQ = 128;          // queries per CTA: MMA M, TMEM lanes
-constexpr int kBN = 128;         // database rows per tile: MMA N
-constexpr int kNumAcc = 4;       // accumulator buffers of kBN columns
-constexpr int kSpan = 128;       // bytes of one 128-byte swizzle span
-constexpr int kExtBytes = kBN * 32;  // one K = 16 BF16 block of 128 rows
+constexpr int kBN = 256;         // database rows per tile: MMA N
+constexpr int kNumAcc = 2;       // accumulator buffers of kBN columns
+constexpr int kSpan = 128;       // bytes of one 128-byte swizzle span (one K block)
+constexpr int kStageBytes = kBN * kSpan;   // one K block of a tile
+constexpr int kExtA = kQ * 32;   // K = 16 BF16 block of the query tile
+constexpr int kExtB = kBN * 32;  // K = 16 BF16 block of a database tile
+constexpr int kExtSlots = 2;
 
 struct TcqArgs {
   int64_t N, M, L;
   int64_t bq, br;                  // bins: q = N / L, r = N % L
   int64_t rows_per_cta, nranges, nqtiles;
   int nkb, nksteps, stages;
-  uint32_t a_bytes, tile_bytes, stage_stride;
+  uint32_t a_bytes;
   int ext;
   uint32_t idesc;
   const float* hnorm;
@@ -102,15 +108,19 @@ k1_tcq_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                              ~(uintptr_t)1023);
   const int S = a.stages;
-  uint8_t* sA = smem;                                   // queries, SW128
-  uint8_t* sAext = sA + a.a_bytes;                      // ones block (L2)
-  uint8_t* sB = sAext + (a.ext ? kExtBytes : 0);        // stages: tile (+ ext block)
-  uint64_t* bars = reinterpret_cast<uint64_t*>(sB + (size_t)S * a.stage_stride);
+  uint8_t* sA = smem;                                      // queries, SW128
+  uint8_t* sB = sA + a.a_bytes;                            // S stages of one K block
+  uint8_t* sAext = sB + (size_t)S * kStageBytes;           // ones block (L2)
+  uint8_t* sBext = sAext + (a.ext ? kExtA : 0);            // 2 half-norm blocks (L2)
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sBext + (a.ext ? kExtSlots * kExtB : 0));
   const uint32_t b_full = smem_u32(bars), b_empty = smem_u32(bars + S);
   const uint32_t b_accf = smem_u32(bars + 2 * S), b_acce = smem_u32(bars + 2 * S + kNumAcc);
-  const uint32_t b_q = smem_u32(bars + 2 * S + 2 * kNumAcc);
-  const uint32_t b_done = smem_u32(bars + 2 * S + 2 * kNumAcc + 1);
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * S + 2 * kNumAcc + 2);
+  const uint32_t b_xf = smem_u32(bars + 2 * S + 2 * kNumAcc);
+  const uint32_t b_xe = smem_u32(bars + 2 * S + 2 * kNumAcc + kExtSlots);
+  const uint32_t b_q = smem_u32(bars + 2 * S + 2 * kNumAcc + 2 * kExtSlots);
+  const uint32_t b_done = smem_u32(bars + 2 * S + 2 * kNumAcc + 2 * kExtSlots + 1);
+  uint32_t* tmem_slot =
+      reinterpret_cast<uint32_t*>(bars + 2 * S + 2 * kNumAcc + 2 * kExtSlots + 2);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -122,12 +132,16 @@ k1_tcq_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < S; ++s) {
-      mbar_init(b_full + 8 * s, a.ext ? 2 : 1);
+      mbar_init(b_full + 8 * s, 1);
       mbar_init(b_empty + 8 * s, 1);
     }
     for (int b = 0; b < kNumAcc; ++b) {
       mbar_init(b_accf + 8 * b, 1);
       mbar_init(b_acce + 8 * b, 4);
+    }
+    for (int e = 0; e < kExtSlots; ++e) {
+      mbar_init(b_xf + 8 * e, 1);
+      mbar_init(b_xe + 8 * e, 1);
     }
     mbar_init(b_q, 1);
     mbar_init(b_done, 1);
@@ -136,17 +150,16 @@ k1_tcq_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
   }
   if (a.ext) {
     // the queries' ones block: K index 0..2 = 1, the rest 0; and the second
-    // 16-byte piece of every stage's block is always zero
+    // 16-byte piece of every half-norm block is always zero
     const __nv_bfloat16 one = __float2bfloat16_rn(1.0f), zero = __float2bfloat16_rn(0.0f);
     for (int r = threadIdx.x; r < kQ; r += kThreadsQ) {
       __nv_bfloat16 v[8] = {one, one, one, zero, zero, zero, zero, zero};
       *reinterpret_cast<uint4*>(sAext + ext_off(r, 0)) = *reinterpret_cast<uint4*>(v);
       *reinterpret_cast<uint4*>(sAext + ext_off(r, 1)) = make_uint4(0, 0, 0, 0);
     }
-    for (int t = threadIdx.x; t < S * kBN; t += kThreadsQ) {
-      uint8_t* ext = sB + (size_t)(t / kBN) * a.stage_stride + a.tile_bytes;
-      *reinterpret_cast<uint4*>(ext + ext_off(t % kBN, 1)) = make_uint4(0, 0, 0, 0);
-    }
+    for (int t = threadIdx.x; t < kExtSlots * kBN; t += kThreadsQ)
+      *reinterpret_cast<uint4*>(sBext + (size_t)(t / kBN) * kExtB + ext_off(t % kBN, 1)) =
+          make_uint4(0, 0, 0, 0);
     fence_proxy_async_smem();
   }
   if (warp == 1) tmem_alloc(smem_u32(tmem_slot), kNumAcc * kBN);
@@ -162,28 +175,21 @@ k1_tcq_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
       for (int kb = 0; kb < a.nkb; ++kb)
         tma_load_2d(smem_u32(sA + (size_t)kb * kQ * kSpan), &tmQ, b_q, kb * (kSpan / 2),
                     (int)(qtile * kQ));
-    }
-    int issued = 0;
-    for (int it = 0; it < nt; ++it) {
-      const int s = it % S;
-      const uint32_t ph = (uint32_t)((it / S) & 1);
-      int ok = 1;
-      if (lane == 0 && it >= S) ok = mbar_wait(b_empty + 8 * s, ph ^ 1u, abort_flag) ? 1 : 0;
-      ok = __shfl_sync(0xffffffffu, ok, 0);
-      if (!ok) break;
-      const int64_t p0 = P0 + (int64_t)it * kBN;
-      uint8_t* st = sB + (size_t)s * a.stage_stride;
-      if (lane == 0) {
-        mbar_expect_tx(b_full + 8 * s, a.tile_bytes);
-        for (int kb = 0; kb < a.nkb; ++kb)
-          tma_load_2d(smem_u32(st + (size_t)kb * kBN * kSpan), &tmX, b_full + 8 * s,
-                      kb * (kSpan / 2), (int)p0);
+      int64_t issued = 0;
+      const int64_t total = (int64_t)nt * a.nkb;
+      for (int64_t g = 0; g < total; ++g) {
+        const int s = (int)(g % S);
+        const uint32_t ph = (uint32_t)((g / S) & 1);
+        if (g >= S && !mbar_wait(b_empty + 8 * s, ph ^ 1u, abort_flag)) break;
+        const int it = (int)(g / a.nkb), kb = (int)(g % a.nkb);
+        mbar_expect_tx(b_full + 8 * s, kStageBytes);
+        tma_load_2d(smem_u32(sB + (size_t)s * kStageBytes), &tmX, b_full + 8 * s,
+                    kb * (kSpan / 2), (int)(P0 + (int64_t)it * kBN));
+        issued = g + 1;
       }
-      issued = it + 1;
-    }
-    if (lane == 0) {
-      for (int it = (issued > S ? issued - S : 0); it < issued; ++it)
-        mbar_wait(b_full + 8 * (it % S), (uint32_t)((it / S) & 1), abort_flag);
+      // drain: every issued copy lands before the CTA can exit
+      for (int64_t g = (issued > S ? issued - S : 0); g < issued; ++g)
+        mbar_wait(b_full + 8 * (int)(g % S), (uint32_t)((g / S) & 1), abort_flag);
       mbar_wait(b_q, 0, abort_flag);
     }
     return;
@@ -192,29 +198,42 @@ k1_tcq_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
     // -------------------------------------------------------------- MMA issuer
     if (lane == 0) {
       if (mbar_wait(b_q, 0, abort_flag)) {
-        const uint32_t a_base = smem_u32(sA);
-        for (int it = 0; it < nt; ++it) {
-          const int s = it % S;
-          const uint32_t ph = (uint32_t)((it / S) & 1);
-          const int ab = it % kNumAcc;
-          const uint32_t aph = (uint32_t)((it / kNumAcc) & 1);
-          if (!mbar_wait(b_full + 8 * s, ph, abort_flag)) break;
+        const uint64_t a_desc = smem_desc_sw128(smem_u32(sA));
+        const uint64_t b_desc = smem_desc_sw128(smem_u32(sB));
+        const uint64_t ax_desc = smem_desc_noswz(smem_u32(sAext), 128, 256);
+        const uint64_t bx_desc = smem_desc_noswz(smem_u32(sBext), 128, 256);
+        int64_t g = 0;
+        bool run = true;
+        for (int it = 0; it < nt && run; ++it) {
+          const int ab = it & 1;
+          const uint32_t aph = (uint32_t)((it >> 1) & 1);
           if (it >= kNumAcc && !mbar_wait(b_acce + 8 * ab, aph ^ 1u, abort_flag)) break;
           tc_fence_after();
-          const uint32_t b_base = smem_u32(sB + (size_t)s * a.stage_stride);
           const uint32_t d_tmem = tmem_base + (uint32_t)(ab * kBN);
-          for (int ks = 0; ks < a.nksteps; ++ks) {
-            const int kb = ks >> 2, kk = ks & 3;
-            const uint64_t ad = smem_desc_sw128(a_base + kb * kQ * kSpan + kk * 32);
-            const uint64_t bd = smem_desc_sw128(b_base + kb * kBN * kSpan + kk * 32);
-            tc_mma<KNN_BF16>(d_tmem, ad, bd, a.idesc, ks > 0 ? 1u : 0u);
+          for (int kb = 0; kb < a.nkb; ++kb, ++g) {
+            const int s = (int)(g % S);
+            if (!mbar_wait(b_full + 8 * s, (uint32_t)((g / S) & 1), abort_flag)) {
+              run = false;
+              break;
+            }
+            tc_fence_after();
+            // descriptors advance by (bytes >> 4) in their address field
+            const uint64_t ad = a_desc + (uint64_t)((kb * kQ * kSpan) >> 4);
+            const uint64_t bd = b_desc + (uint64_t)((s * kStageBytes) >> 4);
+            const int steps = min(4, a.nksteps - kb * 4);
+            for (int kk = 0; kk < steps; ++kk)
+              tc_mma<KNN_BF16>(d_tmem, ad + (uint64_t)(kk * 2), bd + (uint64_t)(kk * 2), a.idesc,
+                               (kb | kk) ? 1u : 0u);
+            tc_commit(b_empty + 8 * s);
           }
+          if (!run) break;
           if (a.ext) {
-            const uint64_t ad = smem_desc_noswz(smem_u32(sAext), 128, 256);
-            const uint64_t bd = smem_desc_noswz(b_base + a.tile_bytes, 128, 256);
-            tc_mma<KNN_BF16>(d_tmem, ad, bd, a.idesc, 1u);
+            const int e = it % kExtSlots;
+            if (!mbar_wait(b_xf + 8 * e, (uint32_t)((it / kExtSlots) & 1), abort_flag)) break;
+            tc_fence_after();
+            tc_mma<KNN_BF16>(d_tmem, ax_desc, bx_desc + (uint64_t)((e * kExtB) >> 4), a.idesc, 1u);
+            tc_commit(b_xe + 8 * e);
           }
-          tc_commit(b_empty + 8 * s);
           tc_commit(b_accf + 8 * ab);
         }
       }
@@ -230,12 +249,12 @@ k1_tcq_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
   if (warp == 2) {
     // ---------------------------------------------------------- L2 half norms
     if (!a.ext) return;
-    // each lane owns rows lane, lane+32, lane+64, lane+96 of every tile; the
-    // loads of the next four tiles are in flight while a tile is written
-    float hb[4][4];
-    auto load = [&](int it, float (&h)[4]) {
+    // each lane owns rows lane + 32 u (u < 8) of every tile; the loads of the
+    // next four tiles are in flight while a tile is written
+    float hb[4][8];
+    auto load = [&](int it, float (&h)[8]) {
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
+      for (int u = 0; u < 8; ++u) {
         const int64_t p = P0 + (int64_t)it * kBN + lane + 32 * u;
         h[u] = (it < nt && p < a.N) ? a.hnorm[p] : 0.0f;
       }
@@ -248,18 +267,18 @@ k1_tcq_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
       for (int k = 0; k < 4; ++k) {
         const int it = it0 + k;
         if (it >= nt || !run) break;
-        const int s = it % S;
-        const uint32_t ph = (uint32_t)((it / S) & 1);
+        const int e = it % kExtSlots;
         int ok = 1;
-        if (lane == 0 && it >= S) ok = mbar_wait(b_empty + 8 * s, ph ^ 1u, abort_flag) ? 1 : 0;
+        if (lane == 0 && it >= kExtSlots)
+          ok = mbar_wait(b_xe + 8 * e, (uint32_t)(((it / kExtSlots) & 1) ^ 1), abort_flag) ? 1 : 0;
         ok = __shfl_sync(0xffffffffu, ok, 0);
         if (!ok) {
           run = false;
           break;
         }
-        uint8_t* ext = sB + (size_t)s * a.stage_stride + a.tile_bytes;
+        uint8_t* ext = sBext + (size_t)e * kExtB;
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
+        for (int u = 0; u < 8; ++u) {
           const float h = hb[k][u];
           const __nv_bfloat16 hi = __float2bfloat16_rn(h);
           const float rem1 = h - __bfloat162float(hi);
@@ -272,7 +291,7 @@ k1_tcq_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
         }
         fence_proxy_async_smem();
         __syncwarp();
-        if (lane == 0) mbar_arrive(b_full + 8 * s);
+        if (lane == 0) mbar_arrive(b_xf + 8 * e);
         load(it + 4, hb[k]);
       }
     }
@@ -282,7 +301,7 @@ k1_tcq_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
 
   // ---------------------------------------------------------------- epilogue
   const int quad = warp & 3;
-  const int wg = (warp - 4) >> 2;  // tiles it with it % 2 == wg
+  const int wg = (warp - 4) >> 2;  // tiles it with it % 2 == wg, accumulator buffer wg
   const int64_t qi = qtile * kQ + quad * 32 + lane;
   const bool q_ok = qi < a.M;
   unsigned long long* gq = a.G + (q_ok ? qi : 0) * a.L;
@@ -295,55 +314,56 @@ k1_tcq_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
       atomicMax(&gq[cur_bin], (unsigned long long)make_key(best, (int32_t)best_row));
   };
   for (int it = wg; it < nt; it += 2) {
-    const int ab = it % kNumAcc;
-    const uint32_t aph = (uint32_t)((it / kNumAcc) & 1);
-    if (!mbar_wait(b_accf + 8 * ab, aph, abort_flag)) break;
+    const uint32_t aph = (uint32_t)((it >> 1) & 1);
+    if (!mbar_wait(b_accf + 8 * wg, aph, abort_flag)) break;
     tc_fence_after();
-    const int64_t p0 = P0 + (int64_t)it * kBN;
-    const uint32_t tcol = tmem_base + ((uint32_t)(quad * 32) << 16) + (uint32_t)(ab * kBN);
-    float rr[2][64], mm[2];
-    __syncwarp();
-    tmem_ld2x64_max(tcol, rr[0], mm[0], rr[1], mm[1]);
-    if (p0 + kBN <= seg_end && p0 + kBN <= P1) {
-      // common case: the tile lies inside the current bin (warp-uniform);
-      // release the buffer at once, then one compare per 64 scores
-      tc_fence_before();
+    const uint32_t tbase =
+        tmem_base + ((uint32_t)(quad * 32) << 16) + (uint32_t)(wg * kBN);
+#pragma unroll 1
+    for (int hh = 0; hh < kBN / 128; ++hh) {
+      const int64_t p0 = P0 + (int64_t)it * kBN + hh * 128;
+      const uint32_t tcol = tbase + (uint32_t)(hh * 128);
+      float rr[2][64], mm[2];
       __syncwarp();
-      if (lane == 0) mbar_arrive(b_acce + 8 * ab);
+      tmem_ld2x64_max(tcol, rr[0], mm[0], rr[1], mm[1]);
+      if (p0 + 128 <= seg_end && p0 + 128 <= P1) {
+        // common case: these 128 rows lie inside the current bin (warp-uniform):
+        // one compare per 64 scores
 #pragma unroll
-      for (int ch = 0; ch < 2; ++ch) {
-        const float m = mm[ch];
-        if (m > best) {
-          int pos = 0;
+        for (int ch = 0; ch < 2; ++ch) {
+          const float m = mm[ch];
+          if (m > best) {
+            int pos = 0;
 #pragma unroll
-          for (int k = 63; k >= 0; --k) pos = (rr[ch][k] == m) ? k : pos;
-          best = m;
-          best_row = p0 + ch * 64 + pos;
+            for (int k = 63; k >= 0; --k) pos = (rr[ch][k] == m) ? k : pos;
+            best = m;
+            best_row = p0 + ch * 64 + pos;
+          }
+        }
+      } else if (p0 < P1) {
+        // a bin boundary or the end of the range falls in these rows (rare):
+        // walk the columns one by one, re-reading them from tensor memory
+        for (int k = 0; k < 128; ++k) {
+          const int64_t p = p0 + k;
+          if (p >= P1) break;  // warp-uniform
+          const float v = tmem_ld1(tcol + (uint32_t)k);
+          while (p >= seg_end) {
+            flush();
+            ++cur_bin;
+            seg_end = bin_end(cur_bin, a.bq, a.br);
+            best = __uint_as_float(kNegInfBits);
+            best_row = -1;
+          }
+          if (v > best) {
+            best = v;
+            best_row = p;
+          }
         }
       }
-    } else {
-      // a bin boundary or the end of the range falls in this tile (rare):
-      // walk its columns one by one, re-reading them from tensor memory
-      for (int k = 0; k < kBN; ++k) {
-        const float v = tmem_ld1(tcol + (uint32_t)k);
-        const int64_t p = p0 + k;
-        if (p >= P1) break;  // warp-uniform
-        while (p >= seg_end) {
-          flush();
-          ++cur_bin;
-          seg_end = bin_end(cur_bin, a.bq, a.br);
-          best = __uint_as_float(kNegInfBits);
-          best_row = -1;
-        }
-        if (v > best) {
-          best = v;
-          best_row = p;
-        }
-      }
-      tc_fence_before();
-      __syncwarp();
-      if (lane == 0) mbar_arrive(b_acce + 8 * ab);
     }
+    tc_fence_before();
+    __syncwarp();
+    if (lane == 0) mbar_arrive(b_acce + 8 * wg);
   }
   tc_fence_before();
   asm volatile("bar.arrive 1, %0;" ::"n"(32 + 256) : "memory");
@@ -378,7 +398,7 @@ bool make_map_bf16(CUtensorMap* m, const void* base, int64_t rows, int pitch, in
 
 struct TcqShape {
   int nkb, nksteps, stages;
-  uint32_t a_bytes, tile_bytes, stage_stride;
+  uint32_t a_bytes;
   size_t smem;
 };
 
@@ -387,15 +407,13 @@ bool tcq_shape(int D, int metric, TcqShape* sh) {
   sh->nkb = (int)cdiv((int64_t)pitch * 2, kSpan);
   sh->nksteps = (int)cdiv((int64_t)pitch * 2, 32);
   sh->a_bytes = (uint32_t)(sh->nkb * kQ * kSpan);
-  sh->tile_bytes = (uint32_t)(sh->nkb * kBN * kSpan);
   const int ext = metric == KNN_L2;
-  sh->stage_stride = sh->tile_bytes + (ext ? kExtBytes : 0);
-  const size_t fixed = 1024 + sh->a_bytes + (ext ? kExtBytes : 0) + 512;
+  const size_t fixed = 1024 + sh->a_bytes + (ext ? kExtA + kExtSlots * kExtB : 0) + 512;
   const size_t budget = 227 * 1024;
-  if (fixed + 2 * (size_t)sh->stage_stride > budget) return false;
-  int stages = (int)((budget - fixed) / sh->stage_stride);
+  if (fixed + 3 * (size_t)kStageBytes > budget) return false;
+  int stages = (int)((budget - fixed) / kStageBytes);
   sh->stages = stages > 8 ? 8 : stages;
-  sh->smem = fixed + (size_t)sh->stages * sh->stage_stride;
+  sh->smem = fixed + (size_t)sh->stages * kStageBytes;
   return true;
 }
 
@@ -437,8 +455,6 @@ cudaError_t launch_k1_tcq(int64_t N, int64_t M, int64_t L, int D, int metric, co
   a.nksteps = sh.nksteps;
   a.stages = sh.stages;
   a.a_bytes = sh.a_bytes;
-  a.tile_bytes = sh.tile_bytes;
-  a.stage_stride = sh.stage_stride;
   a.ext = metric == KNN_L2 ? 1 : 0;
   // D = F32, A = B = BF16, both K-major, N = 128, M = 128
   a.idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kBN >> 3) << 17) |
