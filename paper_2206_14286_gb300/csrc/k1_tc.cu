@@ -130,10 +130,9 @@ k1_tc_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CU
       for (int kb = 0; kb < a.nkb; ++kb)
         tma_load_2d(smem_u32(sQ + (size_t)kb * BQ * kKBlockBytes), &tmQ, b_q,
                     kb * (kKBlockBytes / (DT == KNN_BF16 ? 2 : 1)), qrow);
-      int issued = 0;
+      int issued = 0, s = 0;
+      uint32_t ph = 0;
       for (int it = 0; it < nt; ++it) {
-        const int s = it % S;
-        const uint32_t ph = (uint32_t)((it / S) & 1);
         if (it >= S && !mbar_wait(b_empty + 8 * s, ph ^ 1u, abort_flag)) break;
         mbar_expect_tx(b_full + 8 * s, a.stage_bytes);
         const int row0 = (int)((t_begin + it) * a.Lk + strip * kRows);
@@ -142,19 +141,28 @@ k1_tc_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CU
           tma_load_2d(smem_u32(dst + (size_t)kb * kRows * kKBlockBytes), &tmX, b_full + 8 * s,
                       kb * (kKBlockBytes / (DT == KNN_BF16 ? 2 : 1)), row0);
         issued = it + 1;
+        if (++s == S) {
+          s = 0;
+          ph ^= 1u;
+        }
       }
-      // drain: every issued copy lands before the CTA can exit
-      for (int it = (issued > S ? issued - S : 0); it < issued; ++it)
-        mbar_wait(b_full + 8 * (it % S), (uint32_t)((it / S) & 1), abort_flag);
+      // drain: the last min(issued, S) copies land before the CTA can exit
+      for (int k = 0; k < S && k < issued; ++k) {
+        if (--s < 0) {
+          s = S - 1;
+          ph ^= 1u;
+        }
+        mbar_wait(b_full + 8 * s, ph, abort_flag);
+      }
       mbar_wait(b_q, 0, abort_flag);
     } else if (warp == 1) {
       // ---------------------------------------------------------- MMA issuer
       if (lane == 0) {
         if (mbar_wait(b_q, 0, abort_flag)) {
           const uint32_t q_base = smem_u32(sQ);
+          int s = 0;
+          uint32_t ph = 0;
           for (int it = 0; it < nt; ++it) {
-            const int s = it % S;
-            const uint32_t ph = (uint32_t)((it / S) & 1);
             const int ab = it & 1;
             const uint32_t aph = (uint32_t)((it >> 1) & 1);
             if (!mbar_wait(b_full + 8 * s, ph, abort_flag)) break;
@@ -170,6 +178,10 @@ k1_tc_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CU
             }
             tc_commit(b_empty + 8 * s);
             tc_commit(b_accf + 8 * ab);
+            if (++s == S) {
+              s = 0;
+              ph ^= 1u;
+            }
           }
         }
         // all MMAs have completed before tensor memory is released

@@ -175,21 +175,34 @@ k1_tcq_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
       for (int kb = 0; kb < a.nkb; ++kb)
         tma_load_2d(smem_u32(sA + (size_t)kb * kQ * kSpan), &tmQ, b_q, kb * (kSpan / 2),
                     (int)(qtile * kQ));
-      int64_t issued = 0;
-      const int64_t total = (int64_t)nt * a.nkb;
-      for (int64_t g = 0; g < total; ++g) {
-        const int s = (int)(g % S);
-        const uint32_t ph = (uint32_t)((g / S) & 1);
+      // ring position (stage s, phase ph) is kept incrementally: no division
+      int s = 0, it = 0, kb = 0, issued = 0;
+      uint32_t ph = 0;
+      const int total = nt * a.nkb;
+      for (int g = 0; g < total; ++g) {
         if (g >= S && !mbar_wait(b_empty + 8 * s, ph ^ 1u, abort_flag)) break;
-        const int it = (int)(g / a.nkb), kb = (int)(g % a.nkb);
         mbar_expect_tx(b_full + 8 * s, kStageBytes);
         tma_load_2d(smem_u32(sB + (size_t)s * kStageBytes), &tmX, b_full + 8 * s,
                     kb * (kSpan / 2), (int)(P0 + (int64_t)it * kBN));
         issued = g + 1;
+        if (++kb == a.nkb) {
+          kb = 0;
+          ++it;
+        }
+        if (++s == S) {
+          s = 0;
+          ph ^= 1u;
+        }
       }
-      // drain: every issued copy lands before the CTA can exit
-      for (int64_t g = (issued > S ? issued - S : 0); g < issued; ++g)
-        mbar_wait(b_full + 8 * (int)(g % S), (uint32_t)((g / S) & 1), abort_flag);
+      // drain: the last min(issued, S) copies land before the CTA can exit
+      // (walk the ring backwards from the next position)
+      for (int k = 0; k < S && k < issued; ++k) {
+        if (--s < 0) {
+          s = S - 1;
+          ph ^= 1u;
+        }
+        mbar_wait(b_full + 8 * s, ph, abort_flag);
+      }
       mbar_wait(b_q, 0, abort_flag);
     }
     return;
@@ -202,7 +215,8 @@ k1_tcq_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
         const uint64_t b_desc = smem_desc_sw128(smem_u32(sB));
         const uint64_t ax_desc = smem_desc_noswz(smem_u32(sAext), 128, 256);
         const uint64_t bx_desc = smem_desc_noswz(smem_u32(sBext), 128, 256);
-        int64_t g = 0;
+        int s = 0;
+        uint32_t ph = 0;
         bool run = true;
         for (int it = 0; it < nt && run; ++it) {
           const int ab = it & 1;
@@ -210,9 +224,8 @@ k1_tcq_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
           if (it >= kNumAcc && !mbar_wait(b_acce + 8 * ab, aph ^ 1u, abort_flag)) break;
           tc_fence_after();
           const uint32_t d_tmem = tmem_base + (uint32_t)(ab * kBN);
-          for (int kb = 0; kb < a.nkb; ++kb, ++g) {
-            const int s = (int)(g % S);
-            if (!mbar_wait(b_full + 8 * s, (uint32_t)((g / S) & 1), abort_flag)) {
+          for (int kb = 0; kb < a.nkb; ++kb) {
+            if (!mbar_wait(b_full + 8 * s, ph, abort_flag)) {
               run = false;
               break;
             }
@@ -225,11 +238,15 @@ k1_tcq_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
               tc_mma<KNN_BF16>(d_tmem, ad + (uint64_t)(kk * 2), bd + (uint64_t)(kk * 2), a.idesc,
                                (kb | kk) ? 1u : 0u);
             tc_commit(b_empty + 8 * s);
+            if (++s == S) {
+              s = 0;
+              ph ^= 1u;
+            }
           }
           if (!run) break;
           if (a.ext) {
-            const int e = it % kExtSlots;
-            if (!mbar_wait(b_xf + 8 * e, (uint32_t)((it / kExtSlots) & 1), abort_flag)) break;
+            const int e = it & 1;
+            if (!mbar_wait(b_xf + 8 * e, (uint32_t)((it >> 1) & 1), abort_flag)) break;
             tc_fence_after();
             tc_mma<KNN_BF16>(d_tmem, ax_desc, bx_desc + (uint64_t)((e * kExtB) >> 4), a.idesc, 1u);
             tc_commit(b_xe + 8 * e);
@@ -267,10 +284,10 @@ k1_tcq_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
       for (int k = 0; k < 4; ++k) {
         const int it = it0 + k;
         if (it >= nt || !run) break;
-        const int e = it % kExtSlots;
+        const int e = it & 1;
         int ok = 1;
         if (lane == 0 && it >= kExtSlots)
-          ok = mbar_wait(b_xe + 8 * e, (uint32_t)(((it / kExtSlots) & 1) ^ 1), abort_flag) ? 1 : 0;
+          ok = mbar_wait(b_xe + 8 * e, (uint32_t)(((it >> 1) & 1) ^ 1), abort_flag) ? 1 : 0;
         ok = __shfl_sync(0xffffffffu, ok, 0);
         if (!ok) {
           run = false;
