@@ -2,7 +2,7 @@
 // generalised to L balanced runs of rows) fused with a tcgen05 BF16
 // contraction, queries on the tensor-memory lanes.
 //
-// One CTA (384 threads, one per SM) owns 128 queries and a contiguous range
+// One CTA (640 threads, one per SM) owns 128 queries and a contiguous range
 // of database rows, walked in tiles of 256 rows:
 //   warp 0      : TMA producer. The query tile stays in shared memory; each
 //                 tile's 128-byte K blocks (256 rows x 64 BF16) stream through
@@ -14,12 +14,12 @@
 //   warp 1      : TMEM allocation and tcgen05.mma issue (one thread):
 //                 D[128 queries x 256 rows] (M = 128, N = 256: 128 cycles of
 //                 tensor work per instruction), two accumulator buffers.
-//   warps 4..11 : epilogue, two warpgroups taking alternate tiles (one
-//                 accumulator buffer each). A thread owns one query (its TMEM
-//                 lane). Columns are consecutive database rows, so a run of 64
-//                 columns inside one bin is reduced by a single
-//                 tcgen05.ld.red.max (the load returns the 64 scores and their
-//                 maximum). Only when that maximum beats the bin's best so far
+//   warps 4..19 : epilogue, four warpgroups: two per accumulator buffer (even
+//                 and odd tiles), each owning 128 of the tile's 256 columns. A
+//                 thread owns one query (its TMEM lane). Columns are consecutive
+//                 database rows, so each run of 16 columns inside one bin is
+//                 reduced by tcgen05.ld.red.max (the load returns the 16 scores
+//                 and their maximum) and compared once. Only when that maximum beats the bin's best so far
 //                 does the thread look for its column; a bin boundary inside a
 //                 run is handled column by column. Each thread keeps just the
 //                 current bin's best score and row; when the bin ends it merges
@@ -40,7 +40,7 @@ namespace tpuknn {
 
 namespace {
 
-constexpr int kThreadsQ = 384;
+constexpr int kThreadsQ = 640;  // 4 control warps + 4 epilogue warpgroups
 constexpr int kQ = 128;          // queries per CTA: MMA M, TMEM lanes
 constexpr int kBN = 256;         // database rows per tile: MMA N
 constexpr int kNumAcc = 2;       // accumulator buffers of kBN columns
@@ -70,30 +70,32 @@ __device__ __forceinline__ int64_t bin_end(int64_t b, int64_t q, int64_t r) {
   return (b + 1) * q + min(b + 1, r);
 }
 
-// The 128 columns of this thread's lane as two runs of 64, with the maximum
-// of each run (tcgen05.ld.red), waited for.
-__device__ __forceinline__ void tmem_ld2x64_max(uint32_t taddr, float (&r)[64], float& m,
-                                                float (&r2)[64], float& m2) {
+// 64 columns of this thread's lane as four runs of 16, with the maximum of
+// each run (tcgen05.ld.red), waited for.
+__device__ __forceinline__ void tmem_ld4x16_max(uint32_t taddr, float (&r)[4][16], float (&m)[4]) {
   asm volatile(
-      "tcgen05.ld.red.sync.aligned.32x32b.x64.max.f32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32,%33,%34,%35,%36,%37,%38,%39,%40,%41,%42,%43,%44,%45,%46,%47,%48,%49,%50,%51,%52,%53,%54,%55,%56,%57,%58,%59,%60,%61,%62,%63}, %64, [%130];\n\t"
-      "tcgen05.ld.red.sync.aligned.32x32b.x64.max.f32 {%65,%66,%67,%68,%69,%70,%71,%72,%73,%74,%75,%76,%77,%78,%79,%80,%81,%82,%83,%84,%85,%86,%87,%88,%89,%90,%91,%92,%93,%94,%95,%96,%97,%98,%99,%100,%101,%102,%103,%104,%105,%106,%107,%108,%109,%110,%111,%112,%113,%114,%115,%116,%117,%118,%119,%120,%121,%122,%123,%124,%125,%126,%127,%128}, %129, [%131];\n\t"
+      "tcgen05.ld.red.sync.aligned.32x32b.x16.max.f32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, %16, [%68];\n\t"
+      "tcgen05.ld.red.sync.aligned.32x32b.x16.max.f32 {%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32}, %33, [%69];\n\t"
+      "tcgen05.ld.red.sync.aligned.32x32b.x16.max.f32 {%34,%35,%36,%37,%38,%39,%40,%41,%42,%43,%44,%45,%46,%47,%48,%49}, %50, [%70];\n\t"
+      "tcgen05.ld.red.sync.aligned.32x32b.x16.max.f32 {%51,%52,%53,%54,%55,%56,%57,%58,%59,%60,%61,%62,%63,%64,%65,%66}, %67, [%71];\n\t"
       "tcgen05.wait::ld.sync.aligned;"
-      : "=f"(r[0]), "=f"(r[1]), "=f"(r[2]), "=f"(r[3]), "=f"(r[4]), "=f"(r[5]), "=f"(r[6]), "=f"(r[7]), "=f"(r[8]), "=f"(r[9]), "=f"(r[10]), "=f"(r[11]), "=f"(r[12]), "=f"(r[13]), "=f"(r[14]), "=f"(r[15]), "=f"(r[16]), "=f"(r[17]), "=f"(r[18]), "=f"(r[19]), "=f"(r[20]), "=f"(r[21]), "=f"(r[22]), "=f"(r[23]), "=f"(r[24]), "=f"(r[25]), "=f"(r[26]), "=f"(r[27]), "=f"(r[28]), "=f"(r[29]), "=f"(r[30]), "=f"(r[31]), "=f"(r[32]), "=f"(r[33]), "=f"(r[34]), "=f"(r[35]), "=f"(r[36]), "=f"(r[37]), "=f"(r[38]), "=f"(r[39]), "=f"(r[40]), "=f"(r[41]), "=f"(r[42]), "=f"(r[43]), "=f"(r[44]), "=f"(r[45]), "=f"(r[46]), "=f"(r[47]), "=f"(r[48]), "=f"(r[49]), "=f"(r[50]), "=f"(r[51]), "=f"(r[52]), "=f"(r[53]), "=f"(r[54]), "=f"(r[55]), "=f"(r[56]), "=f"(r[57]), "=f"(r[58]), "=f"(r[59]), "=f"(r[60]), "=f"(r[61]), "=f"(r[62]), "=f"(r[63]), "=f"(m),
-        "=f"(r2[0]), "=f"(r2[1]), "=f"(r2[2]), "=f"(r2[3]), "=f"(r2[4]), "=f"(r2[5]), "=f"(r2[6]), "=f"(r2[7]), "=f"(r2[8]), "=f"(r2[9]), "=f"(r2[10]), "=f"(r2[11]), "=f"(r2[12]), "=f"(r2[13]), "=f"(r2[14]), "=f"(r2[15]), "=f"(r2[16]), "=f"(r2[17]), "=f"(r2[18]), "=f"(r2[19]), "=f"(r2[20]), "=f"(r2[21]), "=f"(r2[22]), "=f"(r2[23]), "=f"(r2[24]), "=f"(r2[25]), "=f"(r2[26]), "=f"(r2[27]), "=f"(r2[28]), "=f"(r2[29]), "=f"(r2[30]), "=f"(r2[31]), "=f"(r2[32]), "=f"(r2[33]), "=f"(r2[34]), "=f"(r2[35]), "=f"(r2[36]), "=f"(r2[37]), "=f"(r2[38]), "=f"(r2[39]), "=f"(r2[40]), "=f"(r2[41]), "=f"(r2[42]), "=f"(r2[43]), "=f"(r2[44]), "=f"(r2[45]), "=f"(r2[46]), "=f"(r2[47]), "=f"(r2[48]), "=f"(r2[49]), "=f"(r2[50]), "=f"(r2[51]), "=f"(r2[52]), "=f"(r2[53]), "=f"(r2[54]), "=f"(r2[55]), "=f"(r2[56]), "=f"(r2[57]), "=f"(r2[58]), "=f"(r2[59]), "=f"(r2[60]), "=f"(r2[61]), "=f"(r2[62]), "=f"(r2[63]), "=f"(m2)
-      : "r"(taddr), "r"(taddr + 64u)
+      : "=f"(r[0][0]), "=f"(r[0][1]), "=f"(r[0][2]), "=f"(r[0][3]), "=f"(r[0][4]), "=f"(r[0][5]), "=f"(r[0][6]), "=f"(r[0][7]), "=f"(r[0][8]), "=f"(r[0][9]), "=f"(r[0][10]), "=f"(r[0][11]), "=f"(r[0][12]), "=f"(r[0][13]), "=f"(r[0][14]), "=f"(r[0][15]), "=f"(m[0]),
+        "=f"(r[1][0]), "=f"(r[1][1]), "=f"(r[1][2]), "=f"(r[1][3]), "=f"(r[1][4]), "=f"(r[1][5]), "=f"(r[1][6]), "=f"(r[1][7]), "=f"(r[1][8]), "=f"(r[1][9]), "=f"(r[1][10]), "=f"(r[1][11]), "=f"(r[1][12]), "=f"(r[1][13]), "=f"(r[1][14]), "=f"(r[1][15]), "=f"(m[1]),
+        "=f"(r[2][0]), "=f"(r[2][1]), "=f"(r[2][2]), "=f"(r[2][3]), "=f"(r[2][4]), "=f"(r[2][5]), "=f"(r[2][6]), "=f"(r[2][7]), "=f"(r[2][8]), "=f"(r[2][9]), "=f"(r[2][10]), "=f"(r[2][11]), "=f"(r[2][12]), "=f"(r[2][13]), "=f"(r[2][14]), "=f"(r[2][15]), "=f"(m[2]),
+        "=f"(r[3][0]), "=f"(r[3][1]), "=f"(r[3][2]), "=f"(r[3][3]), "=f"(r[3][4]), "=f"(r[3][5]), "=f"(r[3][6]), "=f"(r[3][7]), "=f"(r[3][8]), "=f"(r[3][9]), "=f"(r[3][10]), "=f"(r[3][11]), "=f"(r[3][12]), "=f"(r[3][13]), "=f"(r[3][14]), "=f"(r[3][15]), "=f"(m[3])
+      : "r"(taddr), "r"(taddr + 16u), "r"(taddr + 32u), "r"(taddr + 48u)
       : "memory");
 }
 
-// One column of this thread's lane (runtime column), waited for.
-__device__ __forceinline__ float tmem_ld1(uint32_t taddr) {
-  float v;
+// 16 columns of this thread's lane (runtime column), waited for.
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&r)[16]) {
   asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x1.b32 {%0}, [%1];\n\t"
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];\n\t"
       "tcgen05.wait::ld.sync.aligned;"
-      : "=f"(v)
+      : "=f"(r[0]), "=f"(r[1]), "=f"(r[2]), "=f"(r[3]), "=f"(r[4]), "=f"(r[5]), "=f"(r[6]), "=f"(r[7]), "=f"(r[8]), "=f"(r[9]), "=f"(r[10]), "=f"(r[11]), "=f"(r[12]), "=f"(r[13]), "=f"(r[14]), "=f"(r[15])
       : "r"(taddr)
       : "memory");
-  return v;
 }
 
 // byte offset of (row r, 16-byte piece kc) in a K = 16 BF16 block without swizzle
@@ -137,7 +139,7 @@ k1_tcq_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
     }
     for (int b = 0; b < kNumAcc; ++b) {
       mbar_init(b_accf + 8 * b, 1);
-      mbar_init(b_acce + 8 * b, 4);
+      mbar_init(b_acce + 8 * b, 8);
     }
     for (int e = 0; e < kExtSlots; ++e) {
       mbar_init(b_xf + 8 * e, 1);
@@ -258,7 +260,7 @@ k1_tcq_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
       mbar_wait(b_done, 0, abort_flag);
     }
     __syncwarp();
-    asm volatile("bar.sync 1, %0;" ::"n"(32 + 256) : "memory");
+    asm volatile("bar.sync 1, %0;" ::"n"(32 + 512) : "memory");
     tc_fence_after();
     tmem_dealloc(tmem_base, kNumAcc * kBN);
     return;
@@ -318,7 +320,9 @@ k1_tcq_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
 
   // ---------------------------------------------------------------- epilogue
   const int quad = warp & 3;
-  const int wg = (warp - 4) >> 2;  // tiles it with it % 2 == wg, accumulator buffer wg
+  const int egrp = (warp - 4) >> 2;  // 0..3
+  const int ab = egrp & 1;           // accumulator buffer = tile parity
+  const int chalf = egrp >> 1;       // columns chalf*128 .. +127 of each tile
   const int64_t qi = qtile * kQ + quad * 32 + lane;
   const bool q_ok = qi < a.M;
   unsigned long long* gq = a.G + (q_ok ? qi : 0) * a.L;
@@ -330,60 +334,70 @@ k1_tcq_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
     if (q_ok && best_row >= 0)
       atomicMax(&gq[cur_bin], (unsigned long long)make_key(best, (int32_t)best_row));
   };
-  for (int it = wg; it < nt; it += 2) {
+  for (int it = ab; it < nt; it += 2) {
     const uint32_t aph = (uint32_t)((it >> 1) & 1);
-    if (!mbar_wait(b_accf + 8 * wg, aph, abort_flag)) break;
+    if (!mbar_wait(b_accf + 8 * ab, aph, abort_flag)) break;
     tc_fence_after();
-    const uint32_t tbase =
-        tmem_base + ((uint32_t)(quad * 32) << 16) + (uint32_t)(wg * kBN);
+    const uint32_t tbase = tmem_base + ((uint32_t)(quad * 32) << 16) +
+                           (uint32_t)(ab * kBN + chalf * 128);
+    const int64_t pbase = P0 + (int64_t)it * kBN + chalf * 128;
 #pragma unroll 1
-    for (int hh = 0; hh < kBN / 128; ++hh) {
-      const int64_t p0 = P0 + (int64_t)it * kBN + hh * 128;
-      const uint32_t tcol = tbase + (uint32_t)(hh * 128);
-      float rr[2][64], mm[2];
-      __syncwarp();
-      tmem_ld2x64_max(tcol, rr[0], mm[0], rr[1], mm[1]);
-      if (p0 + 128 <= seg_end && p0 + 128 <= P1) {
-        // common case: these 128 rows lie inside the current bin (warp-uniform):
-        // one compare per 64 scores
+    for (int rd = 0; rd < 2; ++rd) {
+      const int64_t p0 = pbase + rd * 64;
+      const uint32_t tcol = tbase + (uint32_t)(rd * 64);
+      if (p0 >= P1) break;  // warp-uniform
+      if (p0 + 64 <= seg_end && p0 + 64 <= P1) {
+        // common case: the 64 rows lie inside the current bin (warp-uniform):
+        // one compare per 16 scores
+        float r[4][16], m[4];
+        __syncwarp();
+        tmem_ld4x16_max(tcol, r, m);
 #pragma unroll
-        for (int ch = 0; ch < 2; ++ch) {
-          const float m = mm[ch];
-          if (m > best) {
+        for (int g = 0; g < 4; ++g) {
+          if (m[g] > best) {
             int pos = 0;
 #pragma unroll
-            for (int k = 63; k >= 0; --k) pos = (rr[ch][k] == m) ? k : pos;
-            best = m;
-            best_row = p0 + ch * 64 + pos;
+            for (int k = 15; k >= 0; --k) pos = (r[g][k] == m[g]) ? k : pos;
+            best = m[g];
+            best_row = p0 + g * 16 + pos;
           }
         }
-      } else if (p0 < P1) {
+      } else {
         // a bin boundary or the end of the range falls in these rows (rare):
-        // walk the columns one by one, re-reading them from tensor memory
-        for (int k = 0; k < 128; ++k) {
-          const int64_t p = p0 + k;
-          if (p >= P1) break;  // warp-uniform
-          const float v = tmem_ld1(tcol + (uint32_t)k);
-          while (p >= seg_end) {
-            flush();
-            ++cur_bin;
-            seg_end = bin_end(cur_bin, a.bq, a.br);
-            best = __uint_as_float(kNegInfBits);
-            best_row = -1;
-          }
-          if (v > best) {
-            best = v;
-            best_row = p;
+        // walk them column by column, 16 at a time
+#pragma unroll 1
+        for (int g = 0; g < 4; ++g) {
+          const int64_t pg = p0 + g * 16;
+          if (pg >= P1) break;  // warp-uniform
+          float r[16];
+          __syncwarp();
+          tmem_ld16(tcol + (uint32_t)(g * 16), r);
+#pragma unroll
+          for (int k = 0; k < 16; ++k) {
+            const int64_t p = pg + k;
+            if (p < P1) {
+              while (p >= seg_end) {
+                flush();
+                ++cur_bin;
+                seg_end = bin_end(cur_bin, a.bq, a.br);
+                best = __uint_as_float(kNegInfBits);
+                best_row = -1;
+              }
+              if (r[k] > best) {
+                best = r[k];
+                best_row = p;
+              }
+            }
           }
         }
       }
     }
     tc_fence_before();
     __syncwarp();
-    if (lane == 0) mbar_arrive(b_acce + 8 * wg);
+    if (lane == 0) mbar_arrive(b_acce + 8 * ab);
   }
   tc_fence_before();
-  asm volatile("bar.arrive 1, %0;" ::"n"(32 + 256) : "memory");
+  asm volatile("bar.arrive 1, %0;" ::"n"(32 + 512) : "memory");
   flush();
 }
 
