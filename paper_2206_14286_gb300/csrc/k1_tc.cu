@@ -133,7 +133,7 @@ k1_tc_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CU
       int issued = 0, s = 0;
       uint32_t ph = 0;
       for (int it = 0; it < nt; ++it) {
-        if (it >= S && !mbar_wait(b_empty + 8 * s, ph ^ 1u, abort_flag)) break;
+        if (it >= S && !mbar_wait_sleep(b_empty + 8 * s, ph ^ 1u, abort_flag, 64)) break;
         mbar_expect_tx(b_full + 8 * s, a.stage_bytes);
         const int row0 = (int)((t_begin + it) * a.Lk + strip * kRows);
         uint8_t* dst = sA + (size_t)s * a.stage_bytes;
@@ -152,9 +152,9 @@ k1_tc_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CU
           s = S - 1;
           ph ^= 1u;
         }
-        mbar_wait(b_full + 8 * s, ph, abort_flag);
+        mbar_wait_sleep(b_full + 8 * s, ph, abort_flag, 64);
       }
-      mbar_wait(b_q, 0, abort_flag);
+      mbar_wait_sleep(b_q, 0, abort_flag, 64);
     } else if (warp == 1) {
       // ---------------------------------------------------------- MMA issuer
       if (lane == 0) {
@@ -234,7 +234,7 @@ k1_tc_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CU
         if (DT == KNN_E4M3) mul_n = a.xscale[jn];
       }
     }
-    if (!mbar_wait(b_accf + 8 * ab, aph, abort_flag)) break;
+    if (!mbar_wait_sleep(b_accf + 8 * ab, aph, abort_flag, 128)) break;
     tc_fence_after();
     // invalid lanes turn every key into -inf: no divergence, no extra select
     const uint32_t km = valid ? nmask : 0u;

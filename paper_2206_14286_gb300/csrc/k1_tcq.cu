@@ -182,7 +182,7 @@ k1_tcq_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
       uint32_t ph = 0;
       const int total = nt * a.nkb;
       for (int g = 0; g < total; ++g) {
-        if (g >= S && !mbar_wait(b_empty + 8 * s, ph ^ 1u, abort_flag)) break;
+        if (g >= S && !mbar_wait_sleep(b_empty + 8 * s, ph ^ 1u, abort_flag, 64)) break;
         mbar_expect_tx(b_full + 8 * s, kStageBytes);
         tma_load_2d(smem_u32(sB + (size_t)s * kStageBytes), &tmX, b_full + 8 * s,
                     kb * (kSpan / 2), (int)(P0 + (int64_t)it * kBN));
@@ -203,9 +203,9 @@ k1_tcq_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
           s = S - 1;
           ph ^= 1u;
         }
-        mbar_wait(b_full + 8 * s, ph, abort_flag);
+        mbar_wait_sleep(b_full + 8 * s, ph, abort_flag, 64);
       }
-      mbar_wait(b_q, 0, abort_flag);
+      mbar_wait_sleep(b_q, 0, abort_flag, 64);
     }
     return;
   }
@@ -289,7 +289,7 @@ k1_tcq_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
         const int e = it & 1;
         int ok = 1;
         if (lane == 0 && it >= kExtSlots)
-          ok = mbar_wait(b_xe + 8 * e, (uint32_t)(((it >> 1) & 1) ^ 1), abort_flag) ? 1 : 0;
+          ok = mbar_wait_sleep(b_xe + 8 * e, (uint32_t)(((it >> 1) & 1) ^ 1), abort_flag, 64) ? 1 : 0;
         ok = __shfl_sync(0xffffffffu, ok, 0);
         if (!ok) {
           run = false;
@@ -336,7 +336,7 @@ k1_tcq_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
   };
   for (int it = ab; it < nt; it += 2) {
     const uint32_t aph = (uint32_t)((it >> 1) & 1);
-    if (!mbar_wait(b_accf + 8 * ab, aph, abort_flag)) break;
+    if (!mbar_wait_sleep(b_accf + 8 * ab, aph, abort_flag, 128)) break;
     tc_fence_after();
     const uint32_t tbase = tmem_base + ((uint32_t)(quad * 32) << 16) +
                            (uint32_t)(ab * kBN + chalf * 128);

@@ -72,6 +72,26 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatil
     }
   }
 }
+// Bounded wait for roles with slack (producer, epilogue, ...): between polls
+// the warp sleeps for about `ns` nanoseconds, so that its polling does not
+// compete with the tensor core for shared-memory bandwidth.
+__device__ __forceinline__ bool mbar_wait_sleep(uint32_t bar, uint32_t parity,
+                                                volatile int* abort_flag, uint32_t ns) {
+  if (mbar_test_wait(bar, parity)) return true;
+  const uint64_t t0 = global_ns();
+  for (uint32_t n = 1;; ++n) {
+    __nanosleep(ns);
+    if (mbar_test_wait(bar, parity)) return true;
+    if ((n & 15) == 0) {
+      if (*abort_flag) return false;
+      if (global_ns() - t0 > kTimeoutNs) {
+        *abort_flag = 1;
+        atomicExch(&g_tc_timeout, 1u);
+        return false;
+      }
+    }
+  }
+}
 __device__ __forceinline__ void fence_barrier_init() {
   asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
 }
