@@ -172,94 +172,107 @@ k1_tcq_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
 
   if (warp == 0) {
     // -------------------------------------------------------------- producer
+    // The whole warp runs the loop (waits included) and stays converged; one
+    // lane issues the copies.
     if (lane == 0) {
       mbar_expect_tx(b_q, a.a_bytes);
       for (int kb = 0; kb < a.nkb; ++kb)
         tma_load_2d(smem_u32(sA + (size_t)kb * kQ * kSpan), &tmQ, b_q, kb * (kSpan / 2),
                     (int)(qtile * kQ));
-      // ring position (stage s, phase ph) is kept incrementally: no division
-      int s = 0, it = 0, kb = 0, issued = 0;
-      uint32_t ph = 0;
-      const int total = nt * a.nkb;
-      for (int g = 0; g < total; ++g) {
-        if (g >= S && !mbar_wait_sleep(b_empty + 8 * s, ph ^ 1u, abort_flag, 64)) break;
+    }
+    __syncwarp();
+    // ring position (stage s, phase ph) is kept incrementally: no division
+    int s = 0, it = 0, kb = 0, issued = 0;
+    uint32_t ph = 0;
+    const int total = nt * a.nkb;
+    for (int g = 0; g < total; ++g) {
+      if (g >= S && !mbar_wait_sleep(b_empty + 8 * s, ph ^ 1u, abort_flag, 64)) break;
+      if (lane == 0) {
         mbar_expect_tx(b_full + 8 * s, kStageBytes);
         tma_load_2d(smem_u32(sB + (size_t)s * kStageBytes), &tmX, b_full + 8 * s,
                     kb * (kSpan / 2), (int)(P0 + (int64_t)it * kBN));
-        issued = g + 1;
-        if (++kb == a.nkb) {
-          kb = 0;
-          ++it;
-        }
-        if (++s == S) {
-          s = 0;
-          ph ^= 1u;
-        }
       }
-      // drain: the last min(issued, S) copies land before the CTA can exit
-      // (walk the ring backwards from the next position)
-      for (int k = 0; k < S && k < issued; ++k) {
-        if (--s < 0) {
-          s = S - 1;
-          ph ^= 1u;
-        }
-        mbar_wait_sleep(b_full + 8 * s, ph, abort_flag, 64);
+      __syncwarp();
+      issued = g + 1;
+      if (++kb == a.nkb) {
+        kb = 0;
+        ++it;
       }
-      mbar_wait_sleep(b_q, 0, abort_flag, 64);
+      if (++s == S) {
+        s = 0;
+        ph ^= 1u;
+      }
     }
+    // drain: the last min(issued, S) copies land before the CTA can exit
+    // (walk the ring backwards from the next position)
+    for (int k = 0; k < S && k < issued; ++k) {
+      if (--s < 0) {
+        s = S - 1;
+        ph ^= 1u;
+      }
+      mbar_wait_sleep(b_full + 8 * s, ph, abort_flag, 64);
+    }
+    mbar_wait_sleep(b_q, 0, abort_flag, 64);
     return;
   }
   if (warp == 1) {
     // -------------------------------------------------------------- MMA issuer
-    if (lane == 0) {
-      if (mbar_wait(b_q, 0, abort_flag)) {
-        const uint64_t a_desc = smem_desc_sw128(smem_u32(sA));
-        const uint64_t b_desc = smem_desc_sw128(smem_u32(sB));
-        const uint64_t ax_desc = smem_desc_noswz(smem_u32(sAext), 128, 256);
-        const uint64_t bx_desc = smem_desc_noswz(smem_u32(sBext), 128, 256);
-        int s = 0;
-        uint32_t ph = 0;
-        bool run = true;
-        for (int it = 0; it < nt && run; ++it) {
-          const int ab = it & 1;
-          const uint32_t aph = (uint32_t)((it >> 1) & 1);
-          if (it >= kNumAcc && !mbar_wait(b_acce + 8 * ab, aph ^ 1u, abort_flag)) break;
-          tc_fence_after();
-          const uint32_t d_tmem = tmem_base + (uint32_t)(ab * kBN);
-          for (int kb = 0; kb < a.nkb; ++kb) {
-            if (!mbar_wait(b_full + 8 * s, ph, abort_flag)) {
-              run = false;
-              break;
-            }
-            tc_fence_after();
+    // The whole warp runs the loop and the waits; one lane issues the MMAs and
+    // the commits.
+    if (mbar_wait(b_q, 0, abort_flag)) {
+      const uint64_t a_desc = smem_desc_sw128(smem_u32(sA));
+      const uint64_t b_desc = smem_desc_sw128(smem_u32(sB));
+      const uint64_t ax_desc = smem_desc_noswz(smem_u32(sAext), 128, 256);
+      const uint64_t bx_desc = smem_desc_noswz(smem_u32(sBext), 128, 256);
+      int s = 0;
+      uint32_t ph = 0;
+      bool run = true;
+      for (int it = 0; it < nt && run; ++it) {
+        const int ab = it & 1;
+        const uint32_t aph = (uint32_t)((it >> 1) & 1);
+        if (it >= kNumAcc && !mbar_wait(b_acce + 8 * ab, aph ^ 1u, abort_flag)) break;
+        tc_fence_after();
+        const uint32_t d_tmem = tmem_base + (uint32_t)(ab * kBN);
+        for (int kb = 0; kb < a.nkb; ++kb) {
+          if (!mbar_wait(b_full + 8 * s, ph, abort_flag)) {
+            run = false;
+            break;
+          }
+          if (lane == 0) {
             // descriptors advance by (bytes >> 4) in their address field
             const uint64_t ad = a_desc + (uint64_t)((kb * kQ * kSpan) >> 4);
             const uint64_t bd = b_desc + (uint64_t)((s * kStageBytes) >> 4);
             const int steps = min(4, a.nksteps - kb * 4);
             for (int kk = 0; kk < steps; ++kk)
-              tc_mma<KNN_BF16>(d_tmem, ad + (uint64_t)(kk * 2), bd + (uint64_t)(kk * 2), a.idesc,
-                               (kb | kk) ? 1u : 0u);
+              tc_mma<KNN_BF16>(d_tmem, ad + (uint64_t)(kk * 2), bd + (uint64_t)(kk * 2),
+                               a.idesc, (kb | kk) ? 1u : 0u);
             tc_commit(b_empty + 8 * s);
-            if (++s == S) {
-              s = 0;
-              ph ^= 1u;
-            }
           }
-          if (!run) break;
-          if (a.ext) {
-            const int e = it & 1;
-            if (!mbar_wait(b_xf + 8 * e, (uint32_t)((it >> 1) & 1), abort_flag)) break;
-            tc_fence_after();
-            tc_mma<KNN_BF16>(d_tmem, ax_desc, bx_desc + (uint64_t)((e * kExtB) >> 4), a.idesc, 1u);
+          __syncwarp();
+          if (++s == S) {
+            s = 0;
+            ph ^= 1u;
+          }
+        }
+        if (!run) break;
+        if (a.ext) {
+          const int e = it & 1;
+          if (!mbar_wait(b_xf + 8 * e, (uint32_t)((it >> 1) & 1), abort_flag)) break;
+          if (lane == 0) {
+            tc_mma<KNN_BF16>(d_tmem, ax_desc, bx_desc + (uint64_t)((e * kExtB) >> 4), a.idesc,
+                             1u);
             tc_commit(b_xe + 8 * e);
           }
-          tc_commit(b_accf + 8 * ab);
+          __syncwarp();
         }
+        if (lane == 0) tc_commit(b_accf + 8 * ab);
+        __syncwarp();
       }
-      tc_commit(b_done);
-      mbar_wait(b_done, 0, abort_flag);
     }
+    // all MMAs have completed before tensor memory is released
+    if (lane == 0) tc_commit(b_done);
     __syncwarp();
+    mbar_wait(b_done, 0, abort_flag);
     asm volatile("bar.sync 1, %0;" ::"n"(32 + 512) : "memory");
     tc_fence_after();
     tmem_dealloc(tmem_base, kNumAcc * kBN);
