@@ -43,7 +43,7 @@ def parse():
     ap.add_argument("--workload", default="mix_l2_1m")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--fp32-steps", type=int, default=10)
-    ap.add_argument("--bins", default="contiguous", choices=["contiguous", "mod"])
+    ap.add_argument("--bins", default="mod", choices=["mod", "contiguous"])
     return ap.parse_args()
 
 
