@@ -159,6 +159,43 @@ size_t knn_search_host_workspace(int64_t N, int32_t D, int32_t dtype, int32_t me
                                  int32_t rerank_mult);
 
 /*
+ * knn_search without a caller workspace: the search runs in a scratch buffer
+ * of KNN_STATIC_WORKSPACE_BYTES that the library reserves in device memory
+ * when the module loads (a file-scope __device__ array, one per device). The
+ * paper has no counterpart; this is a library convenience.
+ *
+ * Who needs it: callers that cannot allocate device memory at the moment
+ * they search -- code running inside an allocator's own callbacks or
+ * out-of-memory handler, a serving thread that must not take the caching
+ * allocator's lock or grow its pool, or a plugin whose host framework hands
+ * it no scratch. This call allocates nothing: no cudaMalloc, no cudaFree, no
+ * allocating library routine.
+ *
+ * Arguments, results and errors are those of knn_search, minus workspace and
+ * ws_bytes. In addition:
+ *   - KNN_ENOMEM when knn_search_workspace(...) for the same arguments
+ *     exceeds KNN_STATIC_WORKSPACE_BYTES (checked before any CUDA call);
+ *     use knn_search with a workspace of your own for larger batches.
+ *   - The first call on each device looks up the buffer's address
+ *     (cudaGetSymbolAddress with that device current, which can load the
+ *     module); later calls reuse it. Make that first call before any stream
+ *     capture begins. A failed lookup returns KNN_ECUDA.
+ *   - Nothing in the buffer has to start at zero: each call clears what it
+ *     accumulates into (the merged bin winners) in its first kernel.
+ *   - One buffer serves every call on a device. Calls that overlap in time
+ *     (on different streams, or from several host threads without ordering)
+ *     race on it and give wrong results; calls on one stream are ordered and
+ *     safe.
+ */
+#define KNN_STATIC_WORKSPACE_BYTES (16u << 20)
+
+knn_status knn_search_static(const void* db_lp, const float* db_scale, const float* db_hnorm,
+                             const float* db_f32, int64_t N, int32_t D, int32_t dtype,
+                             int32_t metric, const float* q, int64_t M, int32_t K, int64_t L,
+                             int32_t bin_map, double recall_target, int32_t rerank_mult,
+                             float* out_val, int32_t* out_idx, void* stream);
+
+/*
  * PartialReduce alone (Alg. 1; the paper's aggregate_to_topk = False,
  * App. A.1): for every query i and bin l the best internal score and its
  * index, out_v[i*L + l], out_a[i*L + l]. Scores are in the internal

@@ -13,6 +13,7 @@ KNN_OK, KNN_EINVAL, KNN_ENOMEM, KNN_ECUDA, KNN_ETIMEOUT, KNN_EUNSUPPORTED = rang
 METRIC = {"ip": 0, "l2": 1, "cos": 2}
 DTYPE = {"f32": 0, "bf16": 1, "e4m3": 2}
 BINS = {"mod": 0, "contiguous": 1}
+STATIC_WORKSPACE_BYTES = 16 << 20  # KNN_STATIC_WORKSPACE_BYTES
 
 # every function the header declares, with (restype, argtypes)
 P, I32, I64, SZ, DBL = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_size_t, ctypes.c_double
@@ -29,6 +30,8 @@ SIGNATURES = {
     "knn_search_host": (ctypes.c_int, [P, P, P, P, I64, I32, I32, I32, P, I64, I32, I64, I32,
                                        DBL, I32, P, P, P, SZ, P]),
     "knn_search_host_workspace": (SZ, [I64, I32, I32, I32, I64, I32, I64, I32, DBL, I32]),
+    "knn_search_static": (ctypes.c_int, [P, P, P, P, I64, I32, I32, I32, P, I64, I32, I64, I32,
+                                         DBL, I32, P, P, P]),
     "knn_partial_reduce": (ctypes.c_int, [P, P, P, I64, I32, I32, I32, P, I64, I64, I32, P, P, P,
                                           SZ, P]),
     "knn_partial_reduce_workspace": (SZ, [I64, I32, I32, I32, I64, I64, I32]),

@@ -1,5 +1,6 @@
 // api.cu -- the extern "C" boundary: argument checks, the bin planner
 // (Eq. 13-14), work decomposition, workspace layout and kernel launches.
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -459,6 +460,33 @@ knn_status exact_impl(const SearchArgs& a, float* out_val, int32_t* out_idx, voi
   return cuda_status(e);
 }
 
+// ---------------------------------------------------------------------------
+// The library's own search scratch (knn_search_static). A file-scope device
+// array is reserved when the module is loaded, so a search through it needs
+// no allocation at call time. Its device address is looked up once per device
+// with that device current and kept; two threads racing on the first lookup
+// store the same address.
+// ---------------------------------------------------------------------------
+constexpr int kMaxDevices = 64;
+static __device__ __align__(256) unsigned char g_static_ws[KNN_STATIC_WORKSPACE_BYTES];
+std::atomic<void*> g_static_ws_addr[kMaxDevices];
+
+knn_status static_workspace(void** out) {
+  int dev = -1;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_status(e);
+  if (dev < 0 || dev >= kMaxDevices) return KNN_EUNSUPPORTED;
+  void* p = g_static_ws_addr[dev].load(std::memory_order_acquire);
+  if (!p) {
+    e = cudaGetSymbolAddress(&p, g_static_ws);
+    if (e != cudaSuccess) return cuda_status(e);
+    if (!p || !aligned(p, kAlign)) return KNN_ECUDA;
+    g_static_ws_addr[dev].store(p, std::memory_order_release);
+  }
+  *out = p;
+  return KNN_OK;
+}
+
 }  // namespace
 
 // ===========================================================================
@@ -569,6 +597,26 @@ knn_status knn_search_host(const void* db_lp, const float* db_scale, const float
     e = cudaMemcpyAsync(out_idx_host, id, (size_t)M * K * 4, cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   return cuda_status(e);
+}
+
+knn_status knn_search_static(const void* db_lp, const float* db_scale, const float* db_hnorm,
+                             const float* db_f32, int64_t N, int32_t D, int32_t dtype,
+                             int32_t metric, const float* q, int64_t M, int32_t K, int64_t L,
+                             int32_t bin_map, double recall_target, int32_t rerank_mult,
+                             float* out_val, int32_t* out_idx, void* stream) {
+  SearchArgs a{db_lp, db_scale, db_hnorm, db_f32, N, D, dtype, metric, q, M, K, L,
+               recall_target, rerank_mult, bin_map};
+  // every size check comes before the device is touched
+  SearchLayout s;
+  knn_status rc = layout_search(a, &s);
+  if (rc != KNN_OK) return rc;
+  if (s.total > (size_t)KNN_STATIC_WORKSPACE_BYTES) return KNN_ENOMEM;
+  if (a.M == 0) return KNN_OK;
+  if ((rc = check_pointers(a, out_val, out_idx)) != KNN_OK) return rc;
+  void* ws = nullptr;
+  if ((rc = static_workspace(&ws)) != KNN_OK) return rc;
+  return search_impl(a, out_val, out_idx, ws, (size_t)KNN_STATIC_WORKSPACE_BYTES,
+                     (cudaStream_t)stream);
 }
 
 size_t knn_partial_reduce_workspace(int64_t N, int32_t D, int32_t dtype, int32_t metric,

@@ -133,6 +133,26 @@ class Database:
                   "knn_search_host")
         return val, idx
 
+    def search_static(self, q, K, L=None, recall_target=0.95, rerank=2, stream=None, out=None,
+                      bins="mod"):
+        """search() in the library's own scratch buffer (knn_search_static): no
+        workspace is allocated; out= preallocated outputs make the call
+        allocation-free on the Python side too."""
+        q = q.contiguous()
+        M = q.shape[0]
+        L = self.resolve_L(K, L, recall_target)
+        if out is None:
+            val = torch.empty((M, K), dtype=torch.float32, device=self.device)
+            idx = torch.empty((M, K), dtype=torch.int32, device=self.device)
+        else:
+            val, idx = out
+        with torch.cuda.device(self.device):
+            check(_lib.get().knn_search_static(*self._args(), q.data_ptr(), M, K, L, BINS[bins],
+                                               recall_target, rerank, val.data_ptr(),
+                                               idx.data_ptr(), _stream(stream)),
+                  "knn_search_static")
+        return val, idx
+
     def search_exact(self, q, K, stream=None):
         q = q.contiguous()
         M = q.shape[0]
