@@ -13,6 +13,10 @@ Recipe (NumPy PCG64 generators, float32 output):
     same mixture as the database.
   * ``unit_rows``: rows scaled to unit l2 norm in float64 and stored as
     float32 (the cosine workload's "rows normalised after sampling").
+  * ``serving_trace``: Poisson arrivals (exponential gaps at a given rate)
+    from the arrival seed; per request a database picked uniformly, a query
+    count log-uniform in [1, m_max] and K uniform over the given choices;
+    queries drawn from that database's mixture with a per-request seed.
 Generation is chunked so that peak host memory stays near the output size.
 """
 import numpy as np
@@ -63,6 +67,27 @@ def targets(m, k, seed=TARGET_SEED):
     """Seeded N(0,1) weights t[m, k] for the softmax-over-top-K loss."""
     rng = np.random.Generator(np.random.PCG64(seed))
     return rng.standard_normal((m, k)).astype(np.float32)
+
+
+def serving_trace(n_requests, rate, dbs, k_choices=(10, 100), m_max=512, seed=ARRIVAL_SEED):
+    """[(t_seconds, db_name, q float32 m x D, K)] for a Poisson stream.
+
+    dbs: {name: (D, n_centres)} -- queries come from that mixture (centres of
+    the data seed, as the database rows)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    names = sorted(dbs)
+    t = 0.0
+    out = []
+    for r in range(n_requests):
+        t += float(rng.exponential(1.0 / rate))
+        name = names[int(rng.integers(0, len(names)))]
+        m = int(np.floor(np.exp(rng.uniform(0.0, np.log(m_max + 1)))))
+        m = min(max(m, 1), m_max)
+        K = int(k_choices[int(rng.integers(0, len(k_choices)))])
+        D, nc = dbs[name]
+        q = mixture(m, D, nc, seed=(seed << 32) + 1 + r)
+        out.append((t, name, q, K))
+    return out
 
 
 # Named workloads. Each returns (X, Q) as float32 numpy arrays plus the
