@@ -215,6 +215,8 @@ struct SearchLayout {
   K1Plan plan;
   int Kp;
   QueryBufs qb;
+  bool keys64;      // K1 merges 64-bit (score, ~index) keys into one [M][L] array
+  bool contiguous;  // bins are runs of consecutive rows
   size_t off_qlp, off_qscale, off_qf32, off_part_v, off_part_a, off_cand, total;
 };
 
@@ -224,8 +226,10 @@ knn_status layout_search(const SearchArgs& a, SearchLayout* s) {
   if (a.bin_map != KNN_BINS_MOD && a.bin_map != KNN_BINS_CONTIGUOUS) return KNN_EINVAL;
   int64_t L;
   if ((st = resolve_L(a, &L)) != KNN_OK) return st;
-  if (a.bin_map == KNN_BINS_CONTIGUOUS) {
-    if (!k1_tcq_supported(a.dtype, a.D, a.metric)) return KNN_EUNSUPPORTED;
+  s->contiguous = a.bin_map == KNN_BINS_CONTIGUOUS;
+  s->keys64 = s->contiguous ? true : k1_tcs_supported(a.dtype, a.D, a.metric, a.N, L);
+  if (s->contiguous && !k1_tcq_supported(a.dtype, a.D, a.metric)) return KNN_EUNSUPPORTED;
+  if (s->keys64) {
     // K2 reads the merged [M][L] keys directly: a plan with one bin per L
     K1Plan p{};
     p.N = a.N;
@@ -296,7 +300,7 @@ cudaError_t prep_queries(const SearchArgs& a, const SearchLayout& s, char* ws, c
   float* qscale = s.qb.scale ? reinterpret_cast<float*>(ws + s.off_qscale) : nullptr;
   float* qf = s.qb.f32 ? reinterpret_cast<float*>(ws + s.off_qf32) : nullptr;
   // merged partials start at zero: the same launch clears them
-  const bool keys64 = a.bin_map == KNN_BINS_CONTIGUOUS;
+  const bool keys64 = s.keys64;
   uint32_t* zbuf = (s.plan.atomic_merge || keys64) ? reinterpret_cast<uint32_t*>(ws + s.off_part_v)
                                                    : nullptr;
   const int64_t zn = keys64 ? 2 * s.plan.M * s.plan.L
@@ -319,8 +323,11 @@ cudaError_t prep_queries(const SearchArgs& a, const SearchLayout& s, char* ws, c
 cudaError_t run_k1(const K1Plan& p, const SearchArgs& a, const void* xlp, const float* xscale,
                    const float* hnorm, const void* qlp, const float* qscale, Partials parts,
                    cudaStream_t st) {
-  if (parts.keys64)
+  if (parts.keys64 && a.bin_map == KNN_BINS_CONTIGUOUS)
     return launch_k1_tcq(p.N, p.M, p.L, p.D, p.metric, xlp, hnorm, qlp,
+                         reinterpret_cast<unsigned long long*>(parts.v), st);
+  if (parts.keys64)
+    return launch_k1_tcs(p.N, p.M, p.L, p.D, p.metric, xlp, hnorm, qlp,
                          reinterpret_cast<unsigned long long*>(parts.v), st);
   if (a.dtype == KNN_F32)
     return launch_k1_simt(p, reinterpret_cast<const float*>(xlp), hnorm,
@@ -346,7 +353,7 @@ knn_status search_impl(const SearchArgs& a, float* out_val, int32_t* out_idx, vo
     e = prep_queries(a, s, ws, &qf32, &q_stride, st);
   }
   if (e != cudaSuccess) return cuda_status(e);
-  const bool k64 = a.bin_map == KNN_BINS_CONTIGUOUS;
+  const bool k64 = s.keys64;
   Partials parts{reinterpret_cast<float*>(ws + s.off_part_v),
                  (a.dtype == KNN_F32 && !k64) ? reinterpret_cast<int32_t*>(ws + s.off_part_a)
                                               : nullptr,
@@ -427,7 +434,7 @@ knn_status exact_impl(const SearchArgs& a, float* out_val, int32_t* out_idx, voi
   if (!workspace || !aligned(workspace, kAlign)) return KNN_EINVAL;
   if (ws_bytes < s.total) return KNN_ENOMEM;
   char* ws = reinterpret_cast<char*>(workspace);
-  SearchLayout sl;
+  SearchLayout sl{};
   sl.plan = s.plan;
   sl.qb = s.qb;
   sl.off_qlp = s.off_qlp;
@@ -649,7 +656,7 @@ knn_status knn_partial_reduce(const void* db_lp, const float* db_scale, const fl
   int64_t q_stride;
   cudaError_t e = prep_queries(a, s, ws, &qf32, &q_stride, st);
   if (e != cudaSuccess) return cuda_status(e);
-  const bool k64 = bin_map == KNN_BINS_CONTIGUOUS;
+  const bool k64 = s.keys64;
   Partials parts{reinterpret_cast<float*>(ws + s.off_part_v),
                  (dtype == KNN_F32 && !k64) ? reinterpret_cast<int32_t*>(ws + s.off_part_a)
                                             : nullptr,
@@ -751,7 +758,8 @@ knn_status knn_sync_status(void) {
   if (e != cudaSuccess) return cuda_status(e);
   const bool t1 = k1_tc_take_timeout();
   const bool t2 = k1_tcq_take_timeout();
-  if (t1 || t2) return KNN_ETIMEOUT;
+  const bool t3 = k1_tcs_take_timeout();
+  if (t1 || t2 || t3) return KNN_ETIMEOUT;
   return KNN_OK;
 }
 

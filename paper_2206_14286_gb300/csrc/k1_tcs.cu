@@ -1,0 +1,651 @@
+// k1_tcs.cu -- PartialReduce with bins j mod L (Alg. 1) fused with a tcgen05
+// BF16 contraction, queries on the tensor-memory lanes and each bin's rows
+// side by side in the accumulator.
+//
+// Row j = t*L + b lies in bin b; the database is read as a [T x L*pitch] grid
+// (grid row t holds rows t*L .. t*L + L - 1). One pipeline step covers 16 bins
+// b0..b0+15 and 16 grid rows t0..t0+15: 256 database rows, loaded by one
+// 16-row TMA box per bin, so accumulator column n = (b - b0)*16 + (t - t0)
+// and every run of 16 consecutive columns holds 16 rows of ONE bin. The
+// epilogue reduces such a run with a single tcgen05.ld.red.max (the load
+// returns the 16 scores and their maximum) and compares the maximum once with
+// the bin's best so far; only on a new best does it look for the column. That
+// is about one compare per 16 scores instead of a compare (and a key pack)
+// per score, which keeps the CUDA-core work well below the tensor-core time.
+//
+// One CTA (640 threads, one per SM) owns 256 queries (two M = 128 halves,
+// A operand resident in shared memory) and a contiguous run of steps:
+//   warp 0      : TMA producer (query tile once; per step and 128-byte K block
+//                 16 boxes of 16 rows into a 32 KB stage of an S-stage ring).
+//   warp 1      : TMEM allocation (512 columns: one 128 x 256 FP32 accumulator
+//                 per query half) and tcgen05.mma issue. Half 0 of a step is
+//                 computed and handed to its epilogue while half 1 is
+//                 computed, so each half's drain overlaps the other's MMAs.
+//   warp 2      : (L2 only) each step's half norms as an extra K = 16 block
+//                 (-h split into three BF16 parts against a ones block of the
+//                 queries), so the accumulator holds the relaxed score
+//                 <q,x> - |x|^2/2 (App. A.2, Eq. 19).
+//   warps 4..19 : epilogue, four warpgroups (query half x column half); a
+//                 thread owns one query and 8 bins of the step; it keeps each
+//                 bin's best score and grid row, and when the CTA moves to
+//                 the next group of bins it merges them into G[query][bin] by
+//                 64-bit atomicMax on the ordered key (score, ~row): ties
+//                 keep the smaller row, and bins split between CTAs merge
+//                 exactly.
+//   warp 3      : idle.
+// Steps that reach past the last full grid row or the last bin take a
+// column-by-column path with a validity test. Rows of the ragged last grid
+// row (t = floor(N/L), b < N mod L) are scored by k1_tcs_tail. All waits are
+// bounded (see tc_ptx.cuh).
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_bf16.h>
+
+#include "common.cuh"
+#include "kernels.h"
+#include "tc_ptx.cuh"
+
+namespace tpuknn {
+
+namespace {
+
+constexpr int kThreadsS = 640;   // 4 control warps + 4 epilogue warpgroups
+constexpr int kQH = 128;         // queries per half: MMA M, TMEM lanes
+constexpr int kQT = 256;         // queries per CTA
+constexpr int kBinsStep = 16;    // bins per step
+constexpr int kRowsBin = 16;     // grid rows per bin per step
+constexpr int kCols = kBinsStep * kRowsBin;  // 256 = MMA N
+constexpr int kSpanS = 128;      // bytes of one 128-byte swizzle span (one K block)
+constexpr int kStageS = kCols * kSpanS;      // 32 KB: one K block of a step
+constexpr int kBoxBytes = kRowsBin * kSpanS;  // 2 KB: one bin's 16 rows
+constexpr int kExtAS = kQH * 32;             // ones block (K = 16 BF16)
+constexpr int kExtBS = kCols * 32;           // half-norm block of a step
+constexpr int kExtSlotsS = 2;
+// Register split (setmaxnreg): the control warpgroup gives up registers so
+// the epilogue can keep four 16-column runs in flight. 128*64 + 512*104 =
+// 61440 = 640*96, the registers the kernel is launched with (checked on the
+// host before every launch).
+constexpr int kCtrlRegsS = 64, kEpiRegsS = 104;
+
+struct TcsArgs {
+  int64_t N, M, L, T;              // T = floor(N / L) full grid rows
+  int64_t ntg, nbg;                // grid-row groups of 16, bin groups of 16
+  int64_t steps_per_cta, steps_per_q, nqt;
+  int pitch;                       // row length in elements (multiple of 16)
+  int nkb, nksteps, stages;
+  uint32_t a_bytes;
+  int ext;
+  uint32_t idesc;
+  const float* hnorm;
+  unsigned long long* G;
+};
+
+// 32 columns of this thread's lane as two runs of 16 with their maxima, waited for.
+__device__ __forceinline__ void tmem_ld2x16_max(uint32_t taddr, float (&r)[2][16], float (&m)[2]) {
+  asm volatile(
+      "tcgen05.ld.red.sync.aligned.32x32b.x16.max.f32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, %16, [%34];\n\t"
+      "tcgen05.ld.red.sync.aligned.32x32b.x16.max.f32 {%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32}, %33, [%35];\n\t"
+      "tcgen05.wait::ld.sync.aligned;"
+      : "=f"(r[0][0]), "=f"(r[0][1]), "=f"(r[0][2]), "=f"(r[0][3]), "=f"(r[0][4]), "=f"(r[0][5]), "=f"(r[0][6]), "=f"(r[0][7]), "=f"(r[0][8]), "=f"(r[0][9]), "=f"(r[0][10]), "=f"(r[0][11]), "=f"(r[0][12]), "=f"(r[0][13]), "=f"(r[0][14]), "=f"(r[0][15]), "=f"(m[0]),
+        "=f"(r[1][0]), "=f"(r[1][1]), "=f"(r[1][2]), "=f"(r[1][3]), "=f"(r[1][4]), "=f"(r[1][5]), "=f"(r[1][6]), "=f"(r[1][7]), "=f"(r[1][8]), "=f"(r[1][9]), "=f"(r[1][10]), "=f"(r[1][11]), "=f"(r[1][12]), "=f"(r[1][13]), "=f"(r[1][14]), "=f"(r[1][15]), "=f"(m[1])
+      : "r"(taddr), "r"(taddr + 16u)
+      : "memory");
+}
+
+// 64 columns of this thread's lane as four runs of 16 with their maxima, waited for.
+__device__ __forceinline__ void tmem_ld4x16_max_s(uint32_t taddr, float (&r)[4][16], float (&m)[4]) {
+  asm volatile(
+      "tcgen05.ld.red.sync.aligned.32x32b.x16.max.f32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, %16, [%68];\n\t"
+      "tcgen05.ld.red.sync.aligned.32x32b.x16.max.f32 {%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32}, %33, [%69];\n\t"
+      "tcgen05.ld.red.sync.aligned.32x32b.x16.max.f32 {%34,%35,%36,%37,%38,%39,%40,%41,%42,%43,%44,%45,%46,%47,%48,%49}, %50, [%70];\n\t"
+      "tcgen05.ld.red.sync.aligned.32x32b.x16.max.f32 {%51,%52,%53,%54,%55,%56,%57,%58,%59,%60,%61,%62,%63,%64,%65,%66}, %67, [%71];\n\t"
+      "tcgen05.wait::ld.sync.aligned;"
+      : "=f"(r[0][0]), "=f"(r[0][1]), "=f"(r[0][2]), "=f"(r[0][3]), "=f"(r[0][4]), "=f"(r[0][5]), "=f"(r[0][6]), "=f"(r[0][7]), "=f"(r[0][8]), "=f"(r[0][9]), "=f"(r[0][10]), "=f"(r[0][11]), "=f"(r[0][12]), "=f"(r[0][13]), "=f"(r[0][14]), "=f"(r[0][15]), "=f"(m[0]),
+        "=f"(r[1][0]), "=f"(r[1][1]), "=f"(r[1][2]), "=f"(r[1][3]), "=f"(r[1][4]), "=f"(r[1][5]), "=f"(r[1][6]), "=f"(r[1][7]), "=f"(r[1][8]), "=f"(r[1][9]), "=f"(r[1][10]), "=f"(r[1][11]), "=f"(r[1][12]), "=f"(r[1][13]), "=f"(r[1][14]), "=f"(r[1][15]), "=f"(m[1]),
+        "=f"(r[2][0]), "=f"(r[2][1]), "=f"(r[2][2]), "=f"(r[2][3]), "=f"(r[2][4]), "=f"(r[2][5]), "=f"(r[2][6]), "=f"(r[2][7]), "=f"(r[2][8]), "=f"(r[2][9]), "=f"(r[2][10]), "=f"(r[2][11]), "=f"(r[2][12]), "=f"(r[2][13]), "=f"(r[2][14]), "=f"(r[2][15]), "=f"(m[2]),
+        "=f"(r[3][0]), "=f"(r[3][1]), "=f"(r[3][2]), "=f"(r[3][3]), "=f"(r[3][4]), "=f"(r[3][5]), "=f"(r[3][6]), "=f"(r[3][7]), "=f"(r[3][8]), "=f"(r[3][9]), "=f"(r[3][10]), "=f"(r[3][11]), "=f"(r[3][12]), "=f"(r[3][13]), "=f"(r[3][14]), "=f"(r[3][15]), "=f"(m[3])
+      : "r"(taddr), "r"(taddr + 16u), "r"(taddr + 32u), "r"(taddr + 48u)
+      : "memory");
+}
+
+// 16 columns of this thread's lane, waited for.
+__device__ __forceinline__ void tmem_ld16s(uint32_t taddr, float (&r)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];\n\t"
+      "tcgen05.wait::ld.sync.aligned;"
+      : "=f"(r[0]), "=f"(r[1]), "=f"(r[2]), "=f"(r[3]), "=f"(r[4]), "=f"(r[5]), "=f"(r[6]), "=f"(r[7]), "=f"(r[8]), "=f"(r[9]), "=f"(r[10]), "=f"(r[11]), "=f"(r[12]), "=f"(r[13]), "=f"(r[14]), "=f"(r[15])
+      : "r"(taddr)
+      : "memory");
+}
+
+// byte offset of (row r, 16-byte piece kc) in a K = 16 BF16 block without swizzle
+__device__ __forceinline__ uint32_t ext_off_s(int r, int kc) {
+  return (uint32_t)((r >> 3) * 256 + kc * 128 + (r & 7) * 16);
+}
+
+template <int NKS>
+__global__ void __launch_bounds__(kThreadsS, 1)
+k1_tcs_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmQ,
+              const TcsArgs a) {
+  constexpr int NKB = (NKS + 3) / 4;  // 128-byte K blocks (stages per step)
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
+                                             ~(uintptr_t)1023);
+  const int S = a.stages;
+  uint8_t* sA = smem;                                      // queries, SW128, [kb][256][128 B]
+  uint8_t* sB = sA + a.a_bytes;                            // S stages of one K block
+  uint8_t* sAext = sB + (size_t)S * kStageS;               // ones block (L2)
+  uint8_t* sBext = sAext + (a.ext ? kExtAS : 0);           // 2 half-norm blocks (L2)
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sBext + (a.ext ? kExtSlotsS * kExtBS : 0));
+  const uint32_t b_full = smem_u32(bars), b_empty = smem_u32(bars + S);
+  const uint32_t b_accf = smem_u32(bars + 2 * S), b_acce = smem_u32(bars + 2 * S + 2);
+  const uint32_t b_xf = smem_u32(bars + 2 * S + 4);
+  const uint32_t b_xe = smem_u32(bars + 2 * S + 4 + kExtSlotsS);
+  const uint32_t b_q = smem_u32(bars + 2 * S + 4 + 2 * kExtSlotsS);
+  const uint32_t b_done = smem_u32(bars + 2 * S + 5 + 2 * kExtSlotsS);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * S + 6 + 2 * kExtSlotsS);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t qtile = blockIdx.x % a.nqt;
+  const int64_t part = blockIdx.x / a.nqt;
+  const int64_t s_begin = part * a.steps_per_cta;
+  const int64_t s_end = min(a.steps_per_q, s_begin + a.steps_per_cta);
+  const int ns = (int)max((int64_t)0, s_end - s_begin);
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < S; ++s) {
+      mbar_init(b_full + 8 * s, 1);
+      mbar_init(b_empty + 8 * s, 1);
+    }
+    for (int h = 0; h < 2; ++h) {
+      mbar_init(b_accf + 8 * h, 1);
+      mbar_init(b_acce + 8 * h, 8);
+    }
+    for (int e = 0; e < kExtSlotsS; ++e) {
+      mbar_init(b_xf + 8 * e, 1);
+      mbar_init(b_xe + 8 * e, 1);
+    }
+    mbar_init(b_q, 1);
+    mbar_init(b_done, 1);
+    *abort_flag = 0;
+    fence_barrier_init();
+  }
+  if (a.ext) {
+    // the queries' ones block: K index 0..2 = 1, the rest 0; and the second
+    // 16-byte piece of every half-norm block is always zero
+    const __nv_bfloat16 one = __float2bfloat16_rn(1.0f), zero = __float2bfloat16_rn(0.0f);
+    for (int r = threadIdx.x; r < kQH; r += kThreadsS) {
+      __nv_bfloat16 v[8] = {one, one, one, zero, zero, zero, zero, zero};
+      *reinterpret_cast<uint4*>(sAext + ext_off_s(r, 0)) = *reinterpret_cast<uint4*>(v);
+      *reinterpret_cast<uint4*>(sAext + ext_off_s(r, 1)) = make_uint4(0, 0, 0, 0);
+    }
+    for (int t = threadIdx.x; t < kExtSlotsS * kCols; t += kThreadsS)
+      *reinterpret_cast<uint4*>(sBext + (size_t)(t / kCols) * kExtBS + ext_off_s(t % kCols, 1)) =
+          make_uint4(0, 0, 0, 0);
+    fence_proxy_async_smem();
+  }
+  if (warp == 1) tmem_alloc(smem_u32(tmem_slot), 512);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_base = *tmem_slot;
+
+  if (warp < 4) asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(kCtrlRegsS));
+  if (warp == 0) {
+    // -------------------------------------------------------------- producer
+    if (lane == 0) {
+      mbar_expect_tx(b_q, a.a_bytes);
+      for (int kb = 0; kb < NKB; ++kb)
+        tma_load_2d(smem_u32(sA + (size_t)kb * kQT * kSpanS), &tmQ, b_q, kb * (kSpanS / 2),
+                    (int)(qtile * kQT));
+    }
+    __syncwarp();
+    int s = 0, kb = 0, issued = 0;
+    uint32_t ph = 0;
+    int64_t bg = s_begin / a.ntg, tg = s_begin % a.ntg;
+    const int total = ns * NKB;
+    for (int g = 0; g < total; ++g) {
+      if (g >= S && !mbar_wait_sleep(b_empty + 8 * s, ph ^ 1u, abort_flag, 64)) break;
+      if (lane == 0) {
+        mbar_expect_tx(b_full + 8 * s, kStageS);
+        const uint32_t dst = smem_u32(sB + (size_t)s * kStageS);
+        const int y = (int)(tg * kRowsBin);
+        // box j: bin b0 + j, K block kb, grid rows y .. y + 15; bins past L
+        // and rows past T read the fill value (zero)
+        int x = (int)(bg * kBinsStep * (int64_t)a.pitch) + kb * (kSpanS / 2);
+        for (int j = 0; j < kBinsStep; ++j, x += a.pitch)
+          tma_load_2d(dst + (uint32_t)(j * kBoxBytes), &tmX, b_full + 8 * s, x, y);
+      }
+      __syncwarp();
+      issued = g + 1;
+      if (++kb == NKB) {
+        kb = 0;
+        if (++tg == a.ntg) {
+          tg = 0;
+          ++bg;
+        }
+      }
+      if (++s == S) {
+        s = 0;
+        ph ^= 1u;
+      }
+    }
+    for (int k = 0; k < S && k < issued; ++k) {
+      if (--s < 0) {
+        s = S - 1;
+        ph ^= 1u;
+      }
+      mbar_wait_sleep(b_full + 8 * s, ph, abort_flag, 64);
+    }
+    mbar_wait_sleep(b_q, 0, abort_flag, 64);
+    return;
+  }
+  if (warp == 1) {
+    // -------------------------------------------------------------- MMA issuer
+    // The whole warp runs the loop and the waits; one lane issues. The tensor
+    // pipe holds few instructions, so nothing slow sits between the MMAs of a
+    // half: every wait of a step (its stages, its L2 block, the accumulator
+    // being free) comes before the unrolled run of MMAs it guards, and the
+    // commits come after.
+    if (mbar_wait(b_q, 0, abort_flag)) {
+      const uint64_t a_desc = smem_desc_sw128(smem_u32(sA));
+      const uint64_t b_desc = smem_desc_sw128(smem_u32(sB));
+      const uint64_t ax_desc = smem_desc_noswz(smem_u32(sAext), 128, 256);
+      const uint64_t bx_desc = smem_desc_noswz(smem_u32(sBext), 128, 256);
+      int s0 = 0;           // stage of K block 0 of the current step
+      uint32_t ph0 = 0;
+      bool run = true;
+      for (int i = 0; i < ns && run; ++i) {
+        const int e = i & 1;
+        // the stages of this step (NKB consecutive ring slots)
+        int sk[NKB];
+        {
+          int s = s0;
+          uint32_t ph = ph0;
+#pragma unroll
+          for (int kb = 0; kb < NKB; ++kb) {
+            sk[kb] = s;
+            if (run && !mbar_wait(b_full + 8 * s, ph, abort_flag)) run = false;
+            if (++s == S) {
+              s = 0;
+              ph ^= 1u;
+            }
+          }
+          s0 = s;
+          ph0 = ph;
+        }
+        if (!run) break;
+        if (a.ext && !mbar_wait(b_xf + 8 * e, (uint32_t)((i >> 1) & 1), abort_flag)) break;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          if (i >= 1 && !mbar_wait(b_acce + 8 * h, (uint32_t)((i & 1) ^ 1), abort_flag)) {
+            run = false;
+            break;
+          }
+          tc_fence_after();
+          if (lane == 0) {
+            const uint32_t d_tmem = tmem_base + (uint32_t)(h * kCols);
+            const uint64_t ah = a_desc + (uint64_t)((h * kQH * kSpanS) >> 4);
+#pragma unroll
+            for (int ks = 0; ks < NKS; ++ks) {
+              // descriptors advance by (bytes >> 4) in their address field
+              const uint64_t ad = ah + (uint64_t)(((ks >> 2) * kQT * kSpanS + (ks & 3) * 32) >> 4);
+              const uint64_t bd =
+                  b_desc + (uint64_t)((sk[ks >> 2] * kStageS + (ks & 3) * 32) >> 4);
+              tc_mma<KNN_BF16>(d_tmem, ad, bd, a.idesc, ks > 0 ? 1u : 0u);
+            }
+            if (a.ext)
+              tc_mma<KNN_BF16>(d_tmem, ax_desc, bx_desc + (uint64_t)((e * kExtBS) >> 4), a.idesc,
+                               1u);
+            tc_commit(b_accf + 8 * h);
+            if (h == 1) {
+#pragma unroll
+              for (int kb = 0; kb < NKB; ++kb) tc_commit(b_empty + 8 * sk[kb]);
+              if (a.ext) tc_commit(b_xe + 8 * e);
+            }
+          }
+          __syncwarp();
+        }
+      }
+    }
+    // all MMAs have completed before tensor memory is released
+    if (lane == 0) tc_commit(b_done);
+    __syncwarp();
+    mbar_wait(b_done, 0, abort_flag);
+    asm volatile("bar.sync 1, %0;" ::"n"(32 + 512) : "memory");
+    tc_fence_after();
+    tmem_dealloc(tmem_base, 512);
+    return;
+  }
+  if (warp == 2) {
+    // ---------------------------------------------------------- L2 half norms
+    if (!a.ext) return;
+    // column n = j*16 + u of a step is bin b0 + j, grid row t0 + u. Lane l
+    // writes columns c = l + 32 k (k < 8), i.e. j = c & 15, u = c >> 4, so
+    // that lanes 0..15 read 16 consecutive floats of one grid row. The loads
+    // of the next step are in flight while a step is written.
+    float hb[2][8];
+    int64_t bg = s_begin / a.ntg, tg = s_begin % a.ntg;
+    auto load = [&](int64_t bgx, int64_t tgx, bool live, float (&h)[8]) {
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        const int c = lane + 32 * k;
+        const int64_t b = bgx * kBinsStep + (c & 15);
+        const int64_t t = tgx * kRowsBin + (c >> 4);
+        h[k] = (live && b < a.L && t < a.T) ? a.hnorm[t * a.L + b] : 0.0f;
+      }
+    };
+    int64_t bgn = bg, tgn = tg;
+    auto advance = [&](int64_t& b, int64_t& t) {
+      if (++t == a.ntg) {
+        t = 0;
+        ++b;
+      }
+    };
+    load(bgn, tgn, ns > 0, hb[0]);
+    advance(bgn, tgn);
+    bool run = true;
+    for (int i0 = 0; i0 < ns && run; i0 += 2) {
+#pragma unroll
+      for (int cur = 0; cur < 2; ++cur) {
+        const int i = i0 + cur;
+        if (i >= ns) break;
+        load(bgn, tgn, i + 1 < ns, hb[cur ^ 1]);
+        advance(bgn, tgn);
+        const int e = i & 1;
+        int ok = 1;
+        if (lane == 0 && i >= kExtSlotsS)
+          ok = mbar_wait_sleep(b_xe + 8 * e, (uint32_t)(((i >> 1) & 1) ^ 1), abort_flag, 64) ? 1
+                                                                                           : 0;
+        ok = __shfl_sync(0xffffffffu, ok, 0);
+        if (!ok) {
+          run = false;
+          break;
+        }
+        uint8_t* ext = sBext + (size_t)e * kExtBS;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+          const int c = lane + 32 * k;
+          const int n = (c & 15) * kRowsBin + (c >> 4);
+          const float hv = hb[cur][k];
+          const __nv_bfloat16 hi = __float2bfloat16_rn(hv);
+          const float rem1 = hv - __bfloat162float(hi);
+          const __nv_bfloat16 mid = __float2bfloat16_rn(rem1);
+          const __nv_bfloat16 lo = __float2bfloat16_rn(rem1 - __bfloat162float(mid));
+          const __nv_bfloat16 z = __float2bfloat16_rn(0.0f);
+          __nv_bfloat16 v[8] = {__hneg(hi), __hneg(mid), __hneg(lo), z, z, z, z, z};
+          *reinterpret_cast<uint4*>(ext + ext_off_s(n, 0)) = *reinterpret_cast<uint4*>(v);
+        }
+        fence_proxy_async_smem();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(b_xf + 8 * e);
+      }
+    }
+    return;
+  }
+  if (warp < 4) return;
+
+  // ---------------------------------------------------------------- epilogue
+  asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(kEpiRegsS));
+  const int quad = warp & 3;
+  const int egrp = (warp - 4) >> 2;  // 0..3
+  const int h = egrp >> 1;           // query half = accumulator
+  const int cq = egrp & 1;           // bins cq*8 .. cq*8+7 of each step
+  const int64_t qi = qtile * kQT + h * kQH + quad * 32 + lane;
+  const bool q_ok = qi < a.M;
+  unsigned long long* gq = a.G + (q_ok ? qi : 0) * a.L;
+  const uint32_t tbase =
+      tmem_base + ((uint32_t)(quad * 32) << 16) + (uint32_t)(h * kCols + cq * 128);
+  int64_t bg = s_begin / a.ntg, tg = s_begin % a.ntg;
+  float best[8];
+  int32_t bt[8];
+#pragma unroll
+  for (int g = 0; g < 8; ++g) {
+    best[g] = __uint_as_float(kNegInfBits);
+    bt[g] = -1;
+  }
+  auto flush = [&](int64_t bgx) {
+#pragma unroll
+    for (int g = 0; g < 8; ++g) {
+      const int64_t b = bgx * kBinsStep + cq * 8 + g;
+      if (q_ok && bt[g] >= 0 && b < a.L)
+        atomicMax(&gq[b], (unsigned long long)make_key(best[g], (int32_t)(bt[g] * a.L + b)));
+      best[g] = __uint_as_float(kNegInfBits);
+      bt[g] = -1;
+    }
+  };
+  auto record = [&](float (&r)[4][16], float (&m)[4], int g0, int32_t t0) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int g = g0 + q;
+      if (m[q] > best[g]) {
+        int pos = 0;
+#pragma unroll
+        for (int k = 15; k >= 0; --k) pos = (r[q][k] == m[q]) ? k : pos;
+        best[g] = m[q];
+        bt[g] = t0 + pos;
+      }
+    }
+  };
+  for (int i = 0; i < ns; ++i) {
+    if (!mbar_wait_sleep(b_accf + 8 * h, (uint32_t)(i & 1), abort_flag, 32)) break;
+    tc_fence_after();
+    const int32_t t0 = (int32_t)(tg * kRowsBin);
+    const int64_t bw = bg * kBinsStep + cq * 8;  // first bin of this warpgroup
+    if (t0 + kRowsBin <= a.T && bw + 8 <= a.L) {
+      // every column valid (warp-uniform): one compare per 16 scores. The
+      // accumulator is released as soon as the last run is in registers.
+      float r[4][16], m[4];
+      __syncwarp();
+      tmem_ld4x16_max_s(tbase, r, m);
+      record(r, m, 0, t0);
+      __syncwarp();
+      tmem_ld4x16_max_s(tbase + 64u, r, m);
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(b_acce + 8 * h);
+      record(r, m, 4, t0);
+    } else {
+      // past the last full grid row or the last bin: column by column
+#pragma unroll
+      for (int g = 0; g < 8; ++g) {
+        float r[16];
+        __syncwarp();
+        tmem_ld16s(tbase + (uint32_t)(g * 16), r);
+        if (bw + g < a.L) {
+#pragma unroll
+          for (int k = 0; k < 16; ++k) {
+            if (t0 + k < a.T && r[k] > best[g]) {
+              best[g] = r[k];
+              bt[g] = t0 + k;
+            }
+          }
+        }
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(b_acce + 8 * h);
+    }
+    if (++tg == a.ntg) {
+      flush(bg);
+      tg = 0;
+      ++bg;
+    }
+  }
+  tc_fence_before();
+  asm volatile("bar.arrive 1, %0;" ::"n"(32 + 512) : "memory");
+  flush(bg);
+}
+
+// Rows of the ragged last grid row: j = T*L + b for b < N - T*L. One thread
+// per (query, row); FP32 sum of the BF16 products (minus the half norm for
+// L2), merged into G by the same 64-bit atomicMax.
+__global__ void k1_tcs_tail(const __nv_bfloat16* __restrict__ X, const __nv_bfloat16* __restrict__ Q,
+                            const float* __restrict__ hnorm, int64_t N, int64_t M, int64_t L,
+                            int64_t T, int pitch, int D, int metric, unsigned long long* G) {
+  const int64_t r = N - T * L;
+  const int64_t b = (int64_t)blockIdx.x * 32 + (threadIdx.x & 31);
+  const int64_t i = (int64_t)blockIdx.y * 8 + (threadIdx.x >> 5);
+  if (b >= r || i >= M) return;
+  const int64_t j = T * L + b;
+  const __nv_bfloat16* x = X + j * pitch;
+  const __nv_bfloat16* q = Q + i * pitch;
+  float acc = 0.0f;
+  for (int d = 0; d < D; ++d) acc = fmaf(__bfloat162float(q[d]), __bfloat162float(x[d]), acc);
+  if (metric == KNN_L2) acc -= hnorm[j];
+  atomicMax(&G[i * L + b], (unsigned long long)make_key(acc, (int32_t)j));
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 get_encode_s() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      return nullptr;
+    fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }
+  return fn;
+}
+
+// 2-D BF16 map: inner extent `inner` elements, `rows` rows `stride_el`
+// elements apart, box 64 x box_rows, 128-byte swizzle.
+bool make_map_s(CUtensorMap* m, const void* base, int64_t inner, int64_t rows, int64_t stride_el,
+                int box_rows) {
+  auto enc = get_encode_s();
+  if (!enc) return false;
+  cuuint64_t dims[2] = {(cuuint64_t)inner, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)stride_el * 2};
+  cuuint32_t box[2] = {(cuuint32_t)(kSpanS / 2), (cuuint32_t)box_rows};
+  cuuint32_t estr[2] = {1, 1};
+  return enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box,
+             estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+struct TcsShape {
+  int nkb, nksteps, stages;
+  uint32_t a_bytes;
+  size_t smem;
+};
+
+bool tcs_shape(int D, int metric, TcsShape* sh) {
+  const int pitch = (int)round_up(D, 16);
+  sh->nkb = (int)cdiv((int64_t)pitch * 2, kSpanS);
+  // MMA K-steps (16 BF16 each), rounded up to an even count: the extra step
+  // multiplies zero query columns (the query box reads zeros past the row)
+  sh->nksteps = (int)round_up(cdiv((int64_t)pitch * 2, 32), 2);
+  if (sh->nksteps > 8) return false;
+  sh->a_bytes = (uint32_t)(sh->nkb * kQT * kSpanS);
+  const int ext = metric == KNN_L2;
+  const size_t fixed = 1024 + sh->a_bytes + (ext ? kExtAS + kExtSlotsS * kExtBS : 0) + 512;
+  const size_t budget = 227 * 1024;
+  // at least one full step plus one K block of look-ahead
+  const int need = sh->nkb + 1 > 3 ? sh->nkb + 1 : 3;
+  if (fixed + (size_t)need * kStageS > budget) return false;
+  int stages = (int)((budget - fixed) / kStageS);
+  sh->stages = stages > 8 ? 8 : stages;
+  sh->smem = fixed + (size_t)sh->stages * kStageS;
+  return true;
+}
+
+template <int NKS>
+cudaError_t launch_tcs(const CUtensorMap& mx, const CUtensorMap& mq, const TcsArgs& a, size_t smem,
+                       int64_t blocks, cudaStream_t st) {
+  // setmaxnreg.inc waits until the registers it asks for are free: refuse to
+  // launch unless the launch-time allocation covers the split.
+  cudaFuncAttributes fa;
+  cudaError_t e = cudaFuncGetAttributes(&fa, k1_tcs_kernel<NKS>);
+  if (e != cudaSuccess) return e;
+  if ((int64_t)round_up(fa.numRegs, 8) * kThreadsS < 128 * kCtrlRegsS + 512 * kEpiRegsS)
+    return cudaErrorNotSupported;
+  e = cudaFuncSetAttribute(k1_tcs_kernel<NKS>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  k1_tcs_kernel<NKS><<<(unsigned)blocks, kThreadsS, smem, st>>>(mx, mq, a);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+bool k1_tcs_supported(int dtype, int D, int metric, int64_t N, int64_t L) {
+  TcsShape sh;
+  if (dtype != KNN_BF16 || metric < KNN_IP || metric > KNN_COS) return false;
+  if (!tcs_shape(D, metric, &sh)) return false;
+  if (L < 1 || L > N) return false;
+  // TMA coordinates are 32-bit: the grid row must stay below 2^31 elements
+  const int64_t pitch = round_up(D, 16);
+  return L * pitch + kBinsStep * pitch < ((int64_t)1 << 31) && N / L < ((int64_t)1 << 31);
+}
+
+cudaError_t launch_k1_tcs(int64_t N, int64_t M, int64_t L, int D, int metric, const void* X,
+                          const float* hnorm, const void* Qp, unsigned long long* G,
+                          cudaStream_t st) {
+  TcsShape sh;
+  if (!k1_tcs_supported(KNN_BF16, D, metric, N, L) || !tcs_shape(D, metric, &sh))
+    return cudaErrorNotSupported;
+  if (metric == KNN_L2 && !hnorm) return cudaErrorInvalidValue;
+  if ((reinterpret_cast<uintptr_t>(X) & 15) || (reinterpret_cast<uintptr_t>(Qp) & 15))
+    return cudaErrorInvalidValue;
+  if (M <= 0) return cudaSuccess;
+  const int pitch = (int)round_up(D, 16);
+  TcsArgs a{};
+  a.N = N;
+  a.M = M;
+  a.L = L;
+  a.T = N / L;
+  a.ntg = cdiv(a.T, kRowsBin);
+  a.nbg = cdiv(L, kBinsStep);
+  a.nqt = cdiv(M, kQT);
+  a.steps_per_q = a.ntg * a.nbg;
+  const int64_t sms = device_sm_count();
+  int64_t cpq = a.nqt >= sms ? 1 : sms / a.nqt;
+  if (cpq > a.steps_per_q) cpq = a.steps_per_q;
+  if (cpq < 1) cpq = 1;
+  a.steps_per_cta = cdiv(a.steps_per_q, cpq);
+  cpq = cdiv(a.steps_per_q, a.steps_per_cta);
+  a.pitch = pitch;
+  a.nkb = sh.nkb;
+  a.nksteps = sh.nksteps;
+  a.stages = sh.stages;
+  a.a_bytes = sh.a_bytes;
+  a.ext = metric == KNN_L2 ? 1 : 0;
+  // D = F32, A = B = BF16, both K-major, N = 256, M = 128
+  a.idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kCols >> 3) << 17) |
+            ((uint32_t)(kQH >> 4) << 24);
+  a.hnorm = hnorm;
+  a.G = G;
+  CUtensorMap mx, mq;
+  // the grid view: T rows of L * pitch elements
+  if (!make_map_s(&mx, X, L * (int64_t)pitch, a.T, L * (int64_t)pitch, kRowsBin))
+    return cudaErrorInvalidValue;
+  if (!make_map_s(&mq, Qp, pitch, M, pitch, kQT)) return cudaErrorInvalidValue;
+  const int64_t blocks = a.nqt * cpq;
+  if (blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
+  cudaError_t e;
+  switch (sh.nksteps) {
+    case 2: e = launch_tcs<2>(mx, mq, a, sh.smem, blocks, st); break;
+    case 4: e = launch_tcs<4>(mx, mq, a, sh.smem, blocks, st); break;
+    case 6: e = launch_tcs<6>(mx, mq, a, sh.smem, blocks, st); break;
+    case 8: e = launch_tcs<8>(mx, mq, a, sh.smem, blocks, st); break;
+    default: return cudaErrorNotSupported;
+  }
+  if (e != cudaSuccess) return e;
+  const int64_t r = N - a.T * L;
+  if (r > 0) {
+    dim3 grid((unsigned)cdiv(r, 32), (unsigned)cdiv(M, 8));
+    k1_tcs_tail<<<grid, 256, 0, st>>>(reinterpret_cast<const __nv_bfloat16*>(X),
+                                      reinterpret_cast<const __nv_bfloat16*>(Qp), hnorm, N, M, L,
+                                      a.T, pitch, D, metric, G);
+    e = cudaGetLastError();
+  }
+  return e;
+}
+
+bool k1_tcs_take_timeout() { return tc_take_timeout_local(); }
+
+}  // namespace tpuknn

@@ -67,6 +67,15 @@ cudaError_t launch_k1_tcq(int64_t N, int64_t M, int64_t L, int D, int metric, co
                           cudaStream_t st);
 bool k1_tcq_take_timeout();
 
+// Tensor-core K1 with bins j mod L, queries on TMEM lanes and each bin's rows
+// side by side in the accumulator (BF16, row length up to 128): same output
+// contract as launch_k1_tcq. Also scores the ragged last grid row.
+bool k1_tcs_supported(int dtype, int D, int metric, int64_t N, int64_t L);
+cudaError_t launch_k1_tcs(int64_t N, int64_t M, int64_t L, int D, int metric, const void* X,
+                          const float* hnorm, const void* Qp, unsigned long long* G,
+                          cudaStream_t st);
+bool k1_tcs_take_timeout();
+
 // K2: per query, merge the partials of every split and fold and select the
 // best Kp (score, index) keys, sorted. If run_in is given its Kp keys per
 // query join the selection (running top-K of a chunked search).
