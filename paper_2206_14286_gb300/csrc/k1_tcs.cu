@@ -4,8 +4,9 @@
 //
 // Row j = t*L + b lies in bin b; the database is read as a [T x L*pitch] grid
 // (grid row t holds rows t*L .. t*L + L - 1). One pipeline step covers 16 bins
-// b0..b0+15 and 16 grid rows t0..t0+15: 256 database rows, loaded by one
-// 16-row TMA box per bin, so accumulator column n = (b - b0)*16 + (t - t0)
+// b0..b0+15 and 16 grid rows t0..t0+15: 256 database rows, loaded per K block
+// by ONE 3-D TMA box whose outer dimension is the bin, so accumulator column
+// n = (b - b0)*16 + (t - t0)
 // and every run of 16 consecutive columns holds 16 rows of ONE bin. The
 // epilogue reduces such a run with a single tcgen05.ld.red.max (the load
 // returns the 16 scores and their maximum) and compares the maximum once with
@@ -16,7 +17,7 @@
 // One CTA (640 threads, one per SM) owns 256 queries (two M = 128 halves,
 // A operand resident in shared memory) and a contiguous run of steps:
 //   warp 0      : TMA producer (query tile once; per step and 128-byte K block
-//                 16 boxes of 16 rows into a 32 KB stage of an S-stage ring).
+//                 one 16 x 16-row box into a 32 KB stage of an S-stage ring).
 //   warp 1      : TMEM allocation (512 columns: one 128 x 256 FP32 accumulator
 //                 per query half) and tcgen05.mma issue. Half 0 of a step is
 //                 computed and handed to its epilogue while half 1 is
@@ -57,7 +58,6 @@ constexpr int kRowsBin = 16;     // grid rows per bin per step
 constexpr int kCols = kBinsStep * kRowsBin;  // 256 = MMA N
 constexpr int kSpanS = 128;      // bytes of one 128-byte swizzle span (one K block)
 constexpr int kStageS = kCols * kSpanS;      // 32 KB: one K block of a step
-constexpr int kBoxBytes = kRowsBin * kSpanS;  // 2 KB: one bin's 16 rows
 constexpr int kExtAS = kQH * 32;             // ones block (K = 16 BF16)
 constexpr int kExtBS = kCols * 32;           // half-norm block of a step
 constexpr int kExtSlotsS = 2;
@@ -79,18 +79,6 @@ struct TcsArgs {
   const float* hnorm;
   unsigned long long* G;
 };
-
-// 32 columns of this thread's lane as two runs of 16 with their maxima, waited for.
-__device__ __forceinline__ void tmem_ld2x16_max(uint32_t taddr, float (&r)[2][16], float (&m)[2]) {
-  asm volatile(
-      "tcgen05.ld.red.sync.aligned.32x32b.x16.max.f32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, %16, [%34];\n\t"
-      "tcgen05.ld.red.sync.aligned.32x32b.x16.max.f32 {%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32}, %33, [%35];\n\t"
-      "tcgen05.wait::ld.sync.aligned;"
-      : "=f"(r[0][0]), "=f"(r[0][1]), "=f"(r[0][2]), "=f"(r[0][3]), "=f"(r[0][4]), "=f"(r[0][5]), "=f"(r[0][6]), "=f"(r[0][7]), "=f"(r[0][8]), "=f"(r[0][9]), "=f"(r[0][10]), "=f"(r[0][11]), "=f"(r[0][12]), "=f"(r[0][13]), "=f"(r[0][14]), "=f"(r[0][15]), "=f"(m[0]),
-        "=f"(r[1][0]), "=f"(r[1][1]), "=f"(r[1][2]), "=f"(r[1][3]), "=f"(r[1][4]), "=f"(r[1][5]), "=f"(r[1][6]), "=f"(r[1][7]), "=f"(r[1][8]), "=f"(r[1][9]), "=f"(r[1][10]), "=f"(r[1][11]), "=f"(r[1][12]), "=f"(r[1][13]), "=f"(r[1][14]), "=f"(r[1][15]), "=f"(m[1])
-      : "r"(taddr), "r"(taddr + 16u)
-      : "memory");
-}
 
 // 64 columns of this thread's lane as four runs of 16 with their maxima, waited for.
 __device__ __forceinline__ void tmem_ld4x16_max_s(uint32_t taddr, float (&r)[4][16], float (&m)[4]) {
@@ -210,13 +198,11 @@ k1_tcs_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
       if (g >= S && !mbar_wait_sleep(b_empty + 8 * s, ph ^ 1u, abort_flag, 64)) break;
       if (lane == 0) {
         mbar_expect_tx(b_full + 8 * s, kStageS);
-        const uint32_t dst = smem_u32(sB + (size_t)s * kStageS);
-        const int y = (int)(tg * kRowsBin);
-        // box j: bin b0 + j, K block kb, grid rows y .. y + 15; bins past L
-        // and rows past T read the fill value (zero)
-        int x = (int)(bg * kBinsStep * (int64_t)a.pitch) + kb * (kSpanS / 2);
-        for (int j = 0; j < kBinsStep; ++j, x += a.pitch)
-          tma_load_2d(dst + (uint32_t)(j * kBoxBytes), &tmX, b_full + 8 * s, x, y);
+        // one box: K block kb (64 elements), grid rows tg*16 .. +15, bins
+        // bg*16 .. +15, landing as [bin][grid row][128 B]; bins past L, rows
+        // past T and elements past the row read the fill value (zero)
+        tma_load_3d(smem_u32(sB + (size_t)s * kStageS), &tmX, b_full + 8 * s, kb * (kSpanS / 2),
+                    (int)(tg * kRowsBin), (int)(bg * kBinsStep));
       }
       __syncwarp();
       issued = g + 1;
@@ -527,6 +513,22 @@ bool make_map_s(CUtensorMap* m, const void* base, int64_t inner, int64_t rows, i
              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+// 3-D BF16 view of the database for the step boxes: element d of grid row t,
+// bin b is row t*L + b. Dimensions (d, t, b) with the bin outermost, so a
+// box of (64, 16, 16) lands as [bin][grid row][128 B]: each bin's 16 rows are
+// consecutive accumulator columns.
+bool make_map_grid(CUtensorMap* m, const void* base, int64_t pitch, int64_t L, int64_t T) {
+  auto enc = get_encode_s();
+  if (!enc) return false;
+  cuuint64_t dims[3] = {(cuuint64_t)pitch, (cuuint64_t)T, (cuuint64_t)L};
+  cuuint64_t strides[2] = {(cuuint64_t)(L * pitch * 2), (cuuint64_t)(pitch * 2)};
+  cuuint32_t box[3] = {(cuuint32_t)(kSpanS / 2), (cuuint32_t)kRowsBin, (cuuint32_t)kBinsStep};
+  cuuint32_t estr[3] = {1, 1, 1};
+  return enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(base), dims, strides, box,
+             estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 struct TcsShape {
   int nkb, nksteps, stages;
   uint32_t a_bytes;
@@ -620,9 +622,7 @@ cudaError_t launch_k1_tcs(int64_t N, int64_t M, int64_t L, int D, int metric, co
   a.hnorm = hnorm;
   a.G = G;
   CUtensorMap mx, mq;
-  // the grid view: T rows of L * pitch elements
-  if (!make_map_s(&mx, X, L * (int64_t)pitch, a.T, L * (int64_t)pitch, kRowsBin))
-    return cudaErrorInvalidValue;
+  if (!make_map_grid(&mx, X, pitch, L, a.T)) return cudaErrorInvalidValue;
   if (!make_map_s(&mq, Qp, pitch, M, pitch, kQT)) return cudaErrorInvalidValue;
   const int64_t blocks = a.nqt * cpq;
   if (blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
