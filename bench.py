@@ -201,6 +201,8 @@ def main():
     idx = torch.empty((M, K), dtype=torch.int32, device="cuda")
 
     bins = args.bins
+    # prep, K1 (plus the ragged-row kernel when N mod L != 0), K2, K3
+    launches_per_step = 4 + (1 if bins == "mod" and N % L else 0)
 
     def step():
         db.search(Qd, K, L=L, rerank=rerank, out=(val, idx), bins=bins)
@@ -308,7 +310,8 @@ def main():
             "peak_source": "%s bf16 dense burst (MEASURED_PEAKS.json)" % pk_kind,
             "kernel": ("k1_tcq_kernel (fused BF16 contraction + PartialReduce, contiguous bins)"
                        if bins == "contiguous" else
-                       "k1_tc_kernel (fused BF16 contraction + PartialReduce, j mod L bins)"),
+                       "k1_tcs_kernel (+ k1_tcs_tail for the N mod L ragged rows): fused BF16 "
+                       "contraction + PartialReduce, j mod L bins"),
             "algorithmic": "2*M*N*D = %.4g FLOP per launch" % flops,
             "hbm_context": {"algorithmic_bytes": k1_bytes,
                             "achieved_gbs": k1_bytes / (k1_ms / 1e3) / 1e9,
@@ -341,7 +344,8 @@ def main():
                 "fp32_path": {"value": world * M / (ms32 / 1e3), "unit": "queries/s",
                               "ms_per_step": ms32, "recall_at_10": recall32},
                 "kernels": prof, "roofline": roof, "e2e": e2e,
-                "gpu_launches": 4 * args.steps, "clocks": clk, "cpu_baseline": cpu}
+                "gpu_launches": launches_per_step * args.steps, "clocks": clk,
+                "cpu_baseline": cpu}
         print(json.dumps(line))
     if world > 1:
         dist.destroy_process_group()
@@ -359,21 +363,31 @@ def config_of(w, L, L_min=None, bins="mod"):
             "parallelism": "replicas"}
 
 
-def k1_traffic(M, N, D, bins="contiguous"):
-    """DRAM bytes per K1 launch from the committed ncu summary, if it was taken
-    on the current kernel source (else None)."""
-    p = os.path.join(ROOT, "profiles", "k1_tc_traffic.json")
+def k1_traffic(M, N, D, bins="mod"):
+    """DRAM bytes per K1 launch from the committed ncu summary of the same
+    kernel source and launch shape (else None). The summary holds lines
+    "- kernel source sha256: <16 hex>", "- bins: ...", "- M: ...", "- N: ...",
+    "- D: ..." and "- dram bytes per launch: <int>"."""
+    name = "k1_tcq_mix_l2_1m.md" if bins == "contiguous" else "k1_tcs_mix_l2_1m.md"
+    p = os.path.join(ROOT, "profiles", name)
     if not os.path.exists(p):
         return None
-    d = json.load(open(p))
-    src = os.path.join(ROOT, "paper_2206_14286_gb300", "csrc", d.get("source", "k1_tc.cu"))
-    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
-    if d.get("sha") != h or d.get("bins") != bins:
+    fields = {}
+    for line in open(p):
+        if line.startswith("- ") and ":" in line:
+            k, v = line[2:].split(":", 1)
+            fields[k.strip()] = v.strip().strip("`")
+    src = "k1_tcq.cu" if bins == "contiguous" else "k1_tcs.cu"
+    h = hashlib.sha256(open(os.path.join(ROOT, "paper_2206_14286_gb300", "csrc", src),
+                            "rb").read()).hexdigest()[:16]
+    try:
+        if (fields.get("kernel source sha256") != h or fields.get("bins") != bins
+                or int(fields.get("M", -1)) != M or int(fields.get("N", -1)) != N
+                or int(fields.get("D", -1)) != D):
+            return None
+        return int(fields["dram bytes per launch"])
+    except (KeyError, ValueError):
         return None
-    if d.get("M") != M or d.get("D") != D:
-        return None
-    # the database stream dominates: scale by the rows of the launch
-    return d["dram_bytes_per_launch"] * N / d["N"]
 
 
 if __name__ == "__main__":

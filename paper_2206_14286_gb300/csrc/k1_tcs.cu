@@ -465,23 +465,55 @@ k1_tcs_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
   flush(bg);
 }
 
-// Rows of the ragged last grid row: j = T*L + b for b < N - T*L. One thread
-// per (query, row); FP32 sum of the BF16 products (minus the half norm for
-// L2), merged into G by the same 64-bit atomicMax.
-__global__ void k1_tcs_tail(const __nv_bfloat16* __restrict__ X, const __nv_bfloat16* __restrict__ Q,
-                            const float* __restrict__ hnorm, int64_t N, int64_t M, int64_t L,
-                            int64_t T, int pitch, int D, int metric, unsigned long long* G) {
+// Rows of the ragged last grid row: j = T*L + b for b < r = N - T*L. A CTA
+// stages 16 of these rows in shared memory and each of its 128 threads scores
+// one query against all 16 (FP32 sum of the BF16 products, minus the half
+// norm for L2), merging into G by the same 64-bit atomicMax.
+constexpr int kTailRows = 16, kTailQ = 128;
+__global__ void __launch_bounds__(kTailQ)
+k1_tcs_tail(const __nv_bfloat16* __restrict__ X, const __nv_bfloat16* __restrict__ Q,
+            const float* __restrict__ hnorm, int64_t N, int64_t M, int64_t L, int64_t T,
+            int pitch, int metric, unsigned long long* G) {
+  __shared__ __align__(16) __nv_bfloat16 rows[kTailRows * 128];
   const int64_t r = N - T * L;
-  const int64_t b = (int64_t)blockIdx.x * 32 + (threadIdx.x & 31);
-  const int64_t i = (int64_t)blockIdx.y * 8 + (threadIdx.x >> 5);
-  if (b >= r || i >= M) return;
-  const int64_t j = T * L + b;
-  const __nv_bfloat16* x = X + j * pitch;
-  const __nv_bfloat16* q = Q + i * pitch;
-  float acc = 0.0f;
-  for (int d = 0; d < D; ++d) acc = fmaf(__bfloat162float(q[d]), __bfloat162float(x[d]), acc);
-  if (metric == KNN_L2) acc -= hnorm[j];
-  atomicMax(&G[i * L + b], (unsigned long long)make_key(acc, (int32_t)j));
+  const int64_t b0 = (int64_t)blockIdx.x * kTailRows;
+  const int nr = (int)min((int64_t)kTailRows, r - b0);
+  const int chunks = pitch / 8;  // 16-byte pieces of a row
+  for (int c = threadIdx.x; c < kTailRows * chunks; c += kTailQ) {
+    const int k = c / chunks, part = c % chunks;
+    uint4 v = make_uint4(0, 0, 0, 0);
+    if (k < nr) v = reinterpret_cast<const uint4*>(X + (T * L + b0 + k) * pitch)[part];
+    reinterpret_cast<uint4*>(rows + k * pitch)[part] = v;
+  }
+  __syncthreads();
+  const int64_t i = (int64_t)blockIdx.y * kTailQ + threadIdx.x;
+  if (i >= M) return;
+  float acc[kTailRows];
+#pragma unroll
+  for (int k = 0; k < kTailRows; ++k) acc[k] = 0.0f;
+  const uint4* qrow = reinterpret_cast<const uint4*>(Q + i * pitch);
+  for (int part = 0; part < chunks; ++part) {
+    const uint4 qv = qrow[part];
+    const __nv_bfloat16* qe = reinterpret_cast<const __nv_bfloat16*>(&qv);
+    float qf[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) qf[e] = __bfloat162float(qe[e]);
+#pragma unroll
+    for (int k = 0; k < kTailRows; ++k) {
+      const uint4 xv = reinterpret_cast<const uint4*>(rows + k * pitch)[part];
+      const __nv_bfloat16* xe = reinterpret_cast<const __nv_bfloat16*>(&xv);
+#pragma unroll
+      for (int e = 0; e < 8; ++e) acc[k] = fmaf(qf[e], __bfloat162float(xe[e]), acc[k]);
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < kTailRows; ++k) {
+    if (k < nr) {
+      const int64_t j = T * L + b0 + k;
+      const float sc = metric == KNN_L2 ? acc[k] - hnorm[j] : acc[k];
+      atomicMax(&G[i * L + b0 + k], (unsigned long long)make_key(sc, (int32_t)j));
+    }
+  }
 }
 
 PFN_cuTensorMapEncodeTiled_v12000 get_encode_s() {
@@ -637,10 +669,10 @@ cudaError_t launch_k1_tcs(int64_t N, int64_t M, int64_t L, int D, int metric, co
   if (e != cudaSuccess) return e;
   const int64_t r = N - a.T * L;
   if (r > 0) {
-    dim3 grid((unsigned)cdiv(r, 32), (unsigned)cdiv(M, 8));
-    k1_tcs_tail<<<grid, 256, 0, st>>>(reinterpret_cast<const __nv_bfloat16*>(X),
-                                      reinterpret_cast<const __nv_bfloat16*>(Qp), hnorm, N, M, L,
-                                      a.T, pitch, D, metric, G);
+    dim3 grid((unsigned)cdiv(r, kTailRows), (unsigned)cdiv(M, kTailQ));
+    k1_tcs_tail<<<grid, kTailQ, 0, st>>>(reinterpret_cast<const __nv_bfloat16*>(X),
+                                         reinterpret_cast<const __nv_bfloat16*>(Qp), hnorm, N, M,
+                                         L, a.T, pitch, metric, G);
     e = cudaGetLastError();
   }
   return e;
