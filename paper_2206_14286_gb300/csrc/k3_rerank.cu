@@ -2,7 +2,9 @@
 // and selection of the final K (the precision pattern: BF16 / E4M3 decide
 // the candidates, FP32 decides their order and values).
 //
-// One CTA per query; each warp scores candidates one at a time with lanes
+// Kp <= 32: one warp per query (k3_warp4_kernel for 16-byte aligned FP32
+// rows, k3_warp_kernel otherwise), the keys sorted across the lanes. Larger
+// Kp: one CTA per query; each warp scores candidates one at a time with lanes
 // splitting D (coalesced row reads), then the Kp keys are sorted in shared
 // memory. Values: IP <q,x>; L2 sum (q-x)^2 evaluated directly; COS <q,x> of
 // the unit-length rows.
@@ -126,6 +128,82 @@ k3_warp_kernel(int64_t M, const uint64_t* __restrict__ cand, int Kp, int K, int 
     out_val[i * K + lane] = mine ? (metric == KNN_L2 ? -sc : sc) : __int_as_float(0x7fc00000);
   }
 }
+// The same for FP32 rows with D % 4 == 0 (16-byte aligned rows): a lane
+// loads 4 consecutive elements, so one warp instruction reads 512 bytes of
+// a row, and the rows of 16 candidates are requested before any is used.
+template <int METRIC>
+__global__ void __launch_bounds__(128)
+k3_warp4_kernel(int64_t M, const uint64_t* __restrict__ cand, int Kp, int K, int D,
+                const float* __restrict__ qf32, int64_t q_stride, const float* __restrict__ xf32,
+                int64_t N, float* __restrict__ out_val, int32_t* __restrict__ out_idx) {
+  constexpr int kB = 16;
+  const int lane = threadIdx.x & 31;
+  const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (i >= M) return;
+  const float* q = qf32 + i * q_stride;
+  const uint64_t mykey_in = lane < Kp ? cand[i * Kp + lane] : 0;
+  uint64_t mine = 0;
+  for (int c0 = 0; c0 < Kp; c0 += kB) {
+    int32_t js[kB];
+    float acc[kB];
+#pragma unroll
+    for (int u = 0; u < kB; ++u) {
+      const uint64_t key = __shfl_sync(0xffffffffu, mykey_in, (c0 + u) & 31);
+      const int32_t j = (c0 + u < Kp && key) ? key_index(key) : -1;
+      js[u] = (j >= 0 && j < N) ? j : -1;
+      acc[u] = 0.0f;
+    }
+    for (int d0 = 0; d0 < D; d0 += 128) {
+      const int d = d0 + lane * 4;
+      const bool in = d < D;
+      const float4 qv = in ? *reinterpret_cast<const float4*>(q + d) : make_float4(0, 0, 0, 0);
+      float4 xv[kB];
+#pragma unroll
+      for (int u = 0; u < kB; ++u)
+        xv[u] = (in && js[u] >= 0) ? __ldg(reinterpret_cast<const float4*>(xf32 + (int64_t)js[u] * D + d))
+                                   : make_float4(0, 0, 0, 0);
+#pragma unroll
+      for (int u = 0; u < kB; ++u) {
+        if (METRIC == KNN_L2) {
+          // rows past D contribute 0: both sides are zero there
+          const float t0 = qv.x - xv[u].x, t1 = qv.y - xv[u].y, t2 = qv.z - xv[u].z,
+                      t3 = qv.w - xv[u].w;
+          acc[u] = fmaf(t0, t0, acc[u]);
+          acc[u] = fmaf(t1, t1, acc[u]);
+          acc[u] = fmaf(t2, t2, acc[u]);
+          acc[u] = fmaf(t3, t3, acc[u]);
+        } else {
+          acc[u] = fmaf(qv.x, xv[u].x, acc[u]);
+          acc[u] = fmaf(qv.y, xv[u].y, acc[u]);
+          acc[u] = fmaf(qv.z, xv[u].z, acc[u]);
+          acc[u] = fmaf(qv.w, xv[u].w, acc[u]);
+        }
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < kB; ++u) {
+      float v = acc[u];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      if (lane == c0 + u && js[u] >= 0) mine = make_key(METRIC == KNN_L2 ? -v : v, js[u]);
+    }
+  }
+#pragma unroll
+  for (int k = 2; k <= 32; k <<= 1) {
+#pragma unroll
+    for (int jj = k >> 1; jj > 0; jj >>= 1) {
+      const uint64_t other = shfl_xor_u64(mine, jj);
+      const bool up = (lane & k) == 0, lower = (lane & jj) == 0;
+      const bool keep_max = (up == lower);
+      mine = keep_max ? (other > mine ? other : mine) : (other < mine ? other : mine);
+    }
+  }
+  if (lane < K) {
+    const float sc = key_score(mine);
+    out_idx[i * K + lane] = mine ? key_index(mine) : -1;
+    out_val[i * K + lane] = mine ? (METRIC == KNN_L2 ? -sc : sc) : __int_as_float(0x7fc00000);
+  }
+}
 }  // namespace
 
 cudaError_t launch_k3(int64_t M, int D, int metric, const uint64_t* cand, int Kp, int K,
@@ -133,6 +211,19 @@ cudaError_t launch_k3(int64_t M, int D, int metric, const uint64_t* cand, int Kp
                       int dtype, int pitch, const float* xscale, int64_t N, float* out_val,
                       int32_t* out_idx, cudaStream_t st) {
   if (M <= 0) return cudaSuccess;
+  const bool vec = xf32 && D % 4 == 0 && q_stride % 4 == 0 &&
+                   (reinterpret_cast<uintptr_t>(xf32) & 15) == 0 &&
+                   (reinterpret_cast<uintptr_t>(qf32) & 15) == 0;
+  if (Kp <= 32 && K <= 32 && vec) {
+    const unsigned blocks = (unsigned)cdiv(M * 32, 128);
+    if (metric == KNN_L2)
+      k3_warp4_kernel<KNN_L2><<<blocks, 128, 0, st>>>(M, cand, Kp, K, D, qf32, q_stride, xf32, N,
+                                                      out_val, out_idx);
+    else
+      k3_warp4_kernel<KNN_IP><<<blocks, 128, 0, st>>>(M, cand, Kp, K, D, qf32, q_stride, xf32, N,
+                                                      out_val, out_idx);
+    return cudaGetLastError();
+  }
   if (Kp <= 32 && K <= 32) {
     k3_warp_kernel<<<(unsigned)cdiv(M * 32, 256), 256, 0, st>>>(
         M, cand, Kp, K, D, metric, qf32, q_stride, xf32, xlp, dtype, pitch, xscale, N, out_val,
