@@ -47,6 +47,19 @@ def parse():
     return ap.parse_args()
 
 
+def job_rate(world, units_per_rank, local_ms, device=None):
+    """Whole-job rate of independent replicas: every rank processed
+    units_per_rank units in local_ms; the job took as long as the slowest
+    rank (max over ranks). Returns (units/s over all ranks, job ms)."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(local_ms)], dtype=torch.float64, device=device)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    job_ms = float(t.item())
+    return world * units_per_rank / (job_ms / 1e3), job_ms
+
+
 def peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -228,11 +241,7 @@ def main():
     _lib.check(lib.knn_profile_enable(0))
     step_ms = [a.elapsed_time(b) for a, b in evs]
     total_ms = evs[0][0].elapsed_time(evs[-1][1])
-    t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    total_ms = float(t.item())
-    value = world * M * args.steps / (total_ms / 1e3)
+    value, total_ms = job_rate(world, M * args.steps, total_ms, device="cuda")
 
     prof = {}
     import ctypes

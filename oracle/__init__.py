@@ -11,7 +11,7 @@ Contents
     re-rank, the gradient of selected scores, and the input preparation
     (bfloat16 / E4M3 rounding, cosine normalisation).
   * ``recall.py``: the expected-recall law (Eq. 12-13 and its exact form) and
-    the bin count from a recall target (Eq. 14, App. A.5).
+    the bin count from a recall target (Eq. 14, App. A.4).
   * ``loss.py``: the softmax-over-top-K loss and its gradient in FP64.
 
 Parity status: every function here is pinned by a ``-m "not gpu"`` test

@@ -12,7 +12,7 @@ Test infrastructure only.
   C(N-n, K) / C(N, K). Eq. 13 counts a bin holding two top-K items as losing
   both, so it is a lower bound of this value.
 * ``min_bins(K, r)`` is Eq. 14: the smallest L with Eq. 13 >= r;
-  ``approx_bins(K, r)`` is its first-order form (K-1)/(1-r) (App. A.5).
+  ``approx_bins(K, r)`` is its first-order form (K-1)/(1-r) (App. A.4).
 """
 import math
 
@@ -69,5 +69,5 @@ def min_bins(K, r):
 
 
 def approx_bins(K, r):
-    """App. A.5: L ~ (K-1)/(1-r) for r close to 1."""
+    """App. A.4: L ~ (K-1)/(1-r) for r close to 1."""
     return (K - 1) / (1.0 - r)

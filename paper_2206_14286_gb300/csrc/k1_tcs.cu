@@ -466,10 +466,10 @@ k1_tcs_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
 }
 
 // Rows of the ragged last grid row: j = T*L + b for b < r = N - T*L. A CTA
-// stages 16 of these rows in shared memory and each of its 128 threads scores
-// one query against all 16 (FP32 sum of the BF16 products, minus the half
+// stages 4 of these rows in shared memory and each of its 128 threads scores
+// one query against all 4 (FP32 sum of the BF16 products, minus the half
 // norm for L2), merging into G by the same 64-bit atomicMax.
-constexpr int kTailRows = 16, kTailQ = 128;
+constexpr int kTailRows = 4, kTailQ = 128;
 __global__ void __launch_bounds__(kTailQ)
 k1_tcs_tail(const __nv_bfloat16* __restrict__ X, const __nv_bfloat16* __restrict__ Q,
             const float* __restrict__ hnorm, int64_t N, int64_t M, int64_t L, int64_t T,

@@ -249,7 +249,7 @@ def test_cosine_is_mips_on_normalised_rows():
 
 
 # ----------------------------------------------------------------------------
-# Recall law (Sec. 5.1, Eq. 12-14, App. A.5)
+# Recall law (Sec. 5.1, Eq. 12-14, App. A.4)
 # ----------------------------------------------------------------------------
 def test_exact_recall_closed_forms():
     assert R.exact_expected_recall(1000, 1000, 10) == pytest.approx(1.0, abs=1e-12)  # L = N
@@ -315,7 +315,7 @@ def test_min_bins_inverts_eq13(K, r):
 
 
 def test_min_bins_first_order_form():
-    """App. A.5: L ~ (K-1)/(1-r); the relative gap shrinks as r -> 1."""
+    """App. A.4: L ~ (K-1)/(1-r); the relative gap shrinks as r -> 1."""
     gaps = []
     for r in [0.9, 0.95, 0.99, 0.999]:
         L = R.min_bins(10, r)

@@ -1,5 +1,5 @@
 """The roofline arithmetic used by the benchmark report, pinned to numbers
-printed in the paper (Table 1, Sec. 4.3 after Eq. 9, Table 2, App. A.7)."""
+printed in the paper (Table 1, Sec. 4.3 after Eq. 9, Table 2, App. A.5)."""
 import os
 
 import pytest
@@ -35,7 +35,7 @@ def test_icop_table2():
 
 
 def test_sift_cop_bound_binds_on_v4_not_v3():
-    """Fig. 2 discussion / App. A.6: Sift (C = 6) is COP-bound on TPU V4 only."""
+    """Fig. 2 discussion / App. A.5: Sift (C = 6) is COP-bound on TPU V4 only."""
     icop = RF.i_cop(G["sift_D"], G["sift_C"])
     big_imem = 4701.0  # Table 2, profiler value
     v4 = RF.binding_roof(G["tpuv4_pi"], G["tpuv4_beta"] / 1e3, G["tpuv4_gamma"], big_imem, icop)
