@@ -38,6 +38,7 @@
 // column-by-column path with a validity test. Rows of the ragged last grid
 // row (t = floor(N/L), b < N mod L) are scored by k1_tcs_tail. All waits are
 // bounded (see tc_ptx.cuh).
+#include <algorithm>
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
@@ -73,6 +74,7 @@ struct TcsArgs {
   int64_t steps_per_cta, steps_per_q, nqt;
   int pitch;                       // row length in elements (multiple of 16)
   int nkb, nksteps, stages;
+  uint32_t stage_bytes;            // one K block of a step (+ of the queries when streamed)
   uint32_t a_bytes;
   int ext;
   uint32_t idesc;
@@ -112,18 +114,31 @@ __device__ __forceinline__ uint32_t ext_off_s(int r, int kc) {
   return (uint32_t)((r >> 3) * 256 + kc * 128 + (r & 7) * 16);
 }
 
-template <int NKS>
+// Modes of the K loop:
+//   kFused   : rows up to 128 elements. The whole step's K blocks are resident
+//              together; each query half runs all its MMAs in one unrolled run
+//              (NKS K-steps), so each half's drain overlaps the other's MMAs.
+//   kKLoopA  : longer rows, query tile resident. The step walks its K blocks
+//              one stage at a time, each stage feeding both halves; both
+//              accumulators close at the end of the step (their drain is short
+//              against a long step).
+//   kKLoopQ  : rows too long for a resident query tile: a stage carries the K
+//              block of the 256 queries too.
+constexpr int kFused = 0, kKLoopA = 1, kKLoopQ = 2;
+
+template <int NKS, int MODE>
 __global__ void __launch_bounds__(kThreadsS, 1)
 k1_tcs_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmQ,
               const TcsArgs a) {
-  constexpr int NKB = (NKS + 3) / 4;  // 128-byte K blocks (stages per step)
+  // 128-byte K blocks per step
+  const int NKB = MODE == kFused ? (NKS + 3) / 4 : a.nkb;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                              ~(uintptr_t)1023);
   const int S = a.stages;
   uint8_t* sA = smem;                                      // queries, SW128, [kb][256][128 B]
   uint8_t* sB = sA + a.a_bytes;                            // S stages of one K block
-  uint8_t* sAext = sB + (size_t)S * kStageS;               // ones block (L2)
+  uint8_t* sAext = sB + (size_t)S * a.stage_bytes;         // ones block (L2)
   uint8_t* sBext = sAext + (a.ext ? kExtAS : 0);           // 2 half-norm blocks (L2)
   uint64_t* bars = reinterpret_cast<uint64_t*>(sBext + (a.ext ? kExtSlotsS * kExtBS : 0));
   const uint32_t b_full = smem_u32(bars), b_empty = smem_u32(bars + S);
@@ -184,10 +199,14 @@ k1_tcs_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
   if (warp == 0) {
     // -------------------------------------------------------------- producer
     if (lane == 0) {
-      mbar_expect_tx(b_q, a.a_bytes);
-      for (int kb = 0; kb < NKB; ++kb)
-        tma_load_2d(smem_u32(sA + (size_t)kb * kQT * kSpanS), &tmQ, b_q, kb * (kSpanS / 2),
-                    (int)(qtile * kQT));
+      if (MODE == kKLoopQ) {
+        mbar_arrive(b_q);  // the queries come with every stage
+      } else {
+        mbar_expect_tx(b_q, a.a_bytes);
+        for (int kb = 0; kb < NKB; ++kb)
+          tma_load_2d(smem_u32(sA + (size_t)kb * kQT * kSpanS), &tmQ, b_q, kb * (kSpanS / 2),
+                      (int)(qtile * kQT));
+      }
     }
     __syncwarp();
     int s = 0, kb = 0, issued = 0;
@@ -197,12 +216,18 @@ k1_tcs_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
     for (int g = 0; g < total; ++g) {
       if (g >= S && !mbar_wait_sleep(b_empty + 8 * s, ph ^ 1u, abort_flag, 64)) break;
       if (lane == 0) {
-        mbar_expect_tx(b_full + 8 * s, kStageS);
+        mbar_expect_tx(b_full + 8 * s, a.stage_bytes);
+        uint32_t dst = smem_u32(sB + (size_t)s * a.stage_bytes);
+        if (MODE == kKLoopQ) {
+          // the queries' K block first: [256 queries][128 B]
+          tma_load_2d(dst, &tmQ, b_full + 8 * s, kb * (kSpanS / 2), (int)(qtile * kQT));
+          dst += kStageS;
+        }
         // one box: K block kb (64 elements), grid rows tg*16 .. +15, bins
         // bg*16 .. +15, landing as [bin][grid row][128 B]; bins past L, rows
         // past T and elements past the row read the fill value (zero)
-        tma_load_3d(smem_u32(sB + (size_t)s * kStageS), &tmX, b_full + 8 * s, kb * (kSpanS / 2),
-                    (int)(tg * kRowsBin), (int)(bg * kBinsStep));
+        tma_load_3d(dst, &tmX, b_full + 8 * s, kb * (kSpanS / 2), (int)(tg * kRowsBin),
+                    (int)(bg * kBinsStep));
       }
       __syncwarp();
       issued = g + 1;
@@ -235,6 +260,7 @@ k1_tcs_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
     // half: every wait of a step (its stages, its L2 block, the accumulator
     // being free) comes before the unrolled run of MMAs it guards, and the
     // commits come after.
+    if constexpr (MODE == kFused) {
     if (mbar_wait(b_q, 0, abort_flag)) {
       const uint64_t a_desc = smem_desc_sw128(smem_u32(sA));
       const uint64_t b_desc = smem_desc_sw128(smem_u32(sB));
@@ -246,7 +272,7 @@ k1_tcs_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
       for (int i = 0; i < ns && run; ++i) {
         const int e = i & 1;
         // the stages of this step (NKB consecutive ring slots)
-        int sk[NKB];
+        int sk[(NKS + 3) / 4];
         {
           int s = s0;
           uint32_t ph = ph0;
@@ -295,6 +321,73 @@ k1_tcs_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
           __syncwarp();
         }
       }
+    }
+    }
+    if constexpr (MODE != kFused) {
+    if (mbar_wait(b_q, 0, abort_flag)) {
+      const uint64_t a_desc = smem_desc_sw128(smem_u32(sA));
+      const uint64_t ax_desc = smem_desc_noswz(smem_u32(sAext), 128, 256);
+      const uint64_t bx_desc = smem_desc_noswz(smem_u32(sBext), 128, 256);
+      int s = 0;
+      uint32_t ph = 0;
+      bool run = true;
+      for (int i = 0; i < ns && run; ++i) {
+        const int e = i & 1;
+        // both accumulators are written from the first K block on
+        if (i >= 1 && (!mbar_wait(b_acce, (uint32_t)((i & 1) ^ 1), abort_flag) ||
+                       !mbar_wait(b_acce + 8, (uint32_t)((i & 1) ^ 1), abort_flag)))
+          break;
+        for (int kb = 0; kb < NKB; ++kb) {
+          if (!mbar_wait(b_full + 8 * s, ph, abort_flag)) {
+            run = false;
+            break;
+          }
+          tc_fence_after();
+          if (lane == 0) {
+            const uint32_t st = smem_u32(sB + (size_t)s * a.stage_bytes);
+            const uint64_t bd = smem_desc_sw128(MODE == kKLoopQ ? st + kStageS : st);
+            const int steps = min(4, a.nksteps - kb * 4);
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+              const uint32_t d_tmem = tmem_base + (uint32_t)(h * kCols);
+              // descriptors advance by (bytes >> 4) in their address field
+              const uint64_t ad =
+                  MODE == kKLoopQ
+                      ? smem_desc_sw128(st + (uint32_t)(h * kQH * kSpanS))
+                      : a_desc + (uint64_t)((kb * kQT * kSpanS + h * kQH * kSpanS) >> 4);
+#pragma unroll
+              for (int kk = 0; kk < 4; ++kk)
+                if (kk < steps)
+                  tc_mma<KNN_BF16>(d_tmem, ad + (uint64_t)(kk * 2), bd + (uint64_t)(kk * 2),
+                                   a.idesc, (kb | kk) ? 1u : 0u);
+            }
+            tc_commit(b_empty + 8 * s);
+          }
+          __syncwarp();
+          if (++s == S) {
+            s = 0;
+            ph ^= 1u;
+          }
+        }
+        if (!run) break;
+        if (a.ext) {
+          if (!mbar_wait(b_xf + 8 * e, (uint32_t)((i >> 1) & 1), abort_flag)) break;
+          tc_fence_after();
+        }
+        if (lane == 0) {
+          if (a.ext) {
+#pragma unroll
+            for (int h = 0; h < 2; ++h)
+              tc_mma<KNN_BF16>(tmem_base + (uint32_t)(h * kCols), ax_desc,
+                               bx_desc + (uint64_t)((e * kExtBS) >> 4), a.idesc, 1u);
+            tc_commit(b_xe + 8 * e);
+          }
+          tc_commit(b_accf);
+          tc_commit(b_accf + 8);
+        }
+        __syncwarp();
+      }
+    }
     }
     // all MMAs have completed before tensor memory is released
     if (lane == 0) tc_commit(b_done);
@@ -474,7 +567,8 @@ __global__ void __launch_bounds__(kTailQ)
 k1_tcs_tail(const __nv_bfloat16* __restrict__ X, const __nv_bfloat16* __restrict__ Q,
             const float* __restrict__ hnorm, int64_t N, int64_t M, int64_t L, int64_t T,
             int pitch, int metric, unsigned long long* G) {
-  __shared__ __align__(16) __nv_bfloat16 rows[kTailRows * 128];
+  extern __shared__ uint4 tail_smem[];  // kTailRows rows of `pitch` elements
+  __nv_bfloat16* rows = reinterpret_cast<__nv_bfloat16*>(tail_smem);
   const int64_t r = N - T * L;
   const int64_t b0 = (int64_t)blockIdx.x * kTailRows;
   const int nr = (int)min((int64_t)kTailRows, r - b0);
@@ -562,45 +656,70 @@ bool make_map_grid(CUtensorMap* m, const void* base, int64_t pitch, int64_t L, i
 }
 
 struct TcsShape {
-  int nkb, nksteps, stages;
-  uint32_t a_bytes;
+  int mode, nkb, nksteps, stages;
+  uint32_t a_bytes, stage_bytes;
   size_t smem;
 };
 
+// The first mode whose shared memory fits: kFused (resident query tile, the
+// whole step's K blocks plus one of look-ahead), kKLoopA (resident query
+// tile, at least 2 stages of one K block), kKLoopQ (query K block streamed in
+// every stage).
 bool tcs_shape(int D, int metric, TcsShape* sh) {
   const int pitch = (int)round_up(D, 16);
-  sh->nkb = (int)cdiv((int64_t)pitch * 2, kSpanS);
-  // MMA K-steps (16 BF16 each), rounded up to an even count: the extra step
-  // multiplies zero query columns (the query box reads zeros past the row)
-  sh->nksteps = (int)round_up(cdiv((int64_t)pitch * 2, 32), 2);
-  if (sh->nksteps > 8) return false;
-  sh->a_bytes = (uint32_t)(sh->nkb * kQT * kSpanS);
-  const int ext = metric == KNN_L2;
-  const size_t fixed = 1024 + sh->a_bytes + (ext ? kExtAS + kExtSlotsS * kExtBS : 0) + 512;
   const size_t budget = 227 * 1024;
-  // at least one full step plus one K block of look-ahead
-  const int need = sh->nkb + 1 > 3 ? sh->nkb + 1 : 3;
-  if (fixed + (size_t)need * kStageS > budget) return false;
-  int stages = (int)((budget - fixed) / kStageS);
-  sh->stages = stages > 8 ? 8 : stages;
-  sh->smem = fixed + (size_t)sh->stages * kStageS;
+  const int ext = metric == KNN_L2;
+  const size_t fixed0 = 1024 + (ext ? kExtAS + kExtSlotsS * kExtBS : 0) + 512;
+  sh->nkb = (int)cdiv((int64_t)pitch * 2, kSpanS);
+  const int nks = (int)cdiv((int64_t)pitch * 2, 32);
+  const uint32_t a_res = (uint32_t)(sh->nkb * kQT * kSpanS);
+  // kFused: K-steps rounded up to an even count (the extra step multiplies
+  // zero query columns: the query box reads zeros past the row)
+  const int nks_even = (int)round_up(nks, 2);
+  if (nks_even <= 8) {
+    const size_t fixed = fixed0 + a_res;
+    const int need = sh->nkb + 1 > 3 ? sh->nkb + 1 : 3;
+    if (fixed + (size_t)need * kStageS <= budget) {
+      sh->mode = kFused;
+      sh->nksteps = nks_even;
+      sh->a_bytes = a_res;
+      sh->stage_bytes = kStageS;
+      sh->stages = (int)std::min<size_t>(8, (budget - fixed) / kStageS);
+      sh->smem = fixed + (size_t)sh->stages * kStageS;
+      return true;
+    }
+  }
+  sh->nksteps = nks;
+  if (fixed0 + a_res + 2 * (size_t)kStageS <= budget) {
+    sh->mode = kKLoopA;
+    sh->a_bytes = a_res;
+    sh->stage_bytes = kStageS;
+    sh->stages = (int)std::min<size_t>(8, (budget - fixed0 - a_res) / kStageS);
+  } else {
+    sh->mode = kKLoopQ;
+    sh->a_bytes = 0;
+    sh->stage_bytes = 2 * kStageS;
+    sh->stages = (int)std::min<size_t>(4, (budget - fixed0) / (2 * kStageS));
+    if (sh->stages < 2) return false;
+  }
+  sh->smem = fixed0 + sh->a_bytes + (size_t)sh->stages * sh->stage_bytes;
   return true;
 }
 
-template <int NKS>
+template <int NKS, int MODE>
 cudaError_t launch_tcs(const CUtensorMap& mx, const CUtensorMap& mq, const TcsArgs& a, size_t smem,
                        int64_t blocks, cudaStream_t st) {
   // setmaxnreg.inc waits until the registers it asks for are free: refuse to
   // launch unless the launch-time allocation covers the split.
   cudaFuncAttributes fa;
-  cudaError_t e = cudaFuncGetAttributes(&fa, k1_tcs_kernel<NKS>);
+  cudaError_t e = cudaFuncGetAttributes(&fa, k1_tcs_kernel<NKS, MODE>);
   if (e != cudaSuccess) return e;
   if ((int64_t)round_up(fa.numRegs, 8) * kThreadsS < 128 * kCtrlRegsS + 512 * kEpiRegsS)
     return cudaErrorNotSupported;
-  e = cudaFuncSetAttribute(k1_tcs_kernel<NKS>,
+  e = cudaFuncSetAttribute(k1_tcs_kernel<NKS, MODE>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  k1_tcs_kernel<NKS><<<(unsigned)blocks, kThreadsS, smem, st>>>(mx, mq, a);
+  k1_tcs_kernel<NKS, MODE><<<(unsigned)blocks, kThreadsS, smem, st>>>(mx, mq, a);
   return cudaGetLastError();
 }
 
@@ -647,6 +766,7 @@ cudaError_t launch_k1_tcs(int64_t N, int64_t M, int64_t L, int D, int metric, co
   a.nksteps = sh.nksteps;
   a.stages = sh.stages;
   a.a_bytes = sh.a_bytes;
+  a.stage_bytes = sh.stage_bytes;
   a.ext = metric == KNN_L2 ? 1 : 0;
   // D = F32, A = B = BF16, both K-major, N = 256, M = 128
   a.idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kCols >> 3) << 17) |
@@ -659,18 +779,25 @@ cudaError_t launch_k1_tcs(int64_t N, int64_t M, int64_t L, int D, int metric, co
   const int64_t blocks = a.nqt * cpq;
   if (blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
   cudaError_t e;
-  switch (sh.nksteps) {
-    case 2: e = launch_tcs<2>(mx, mq, a, sh.smem, blocks, st); break;
-    case 4: e = launch_tcs<4>(mx, mq, a, sh.smem, blocks, st); break;
-    case 6: e = launch_tcs<6>(mx, mq, a, sh.smem, blocks, st); break;
-    case 8: e = launch_tcs<8>(mx, mq, a, sh.smem, blocks, st); break;
-    default: return cudaErrorNotSupported;
+  if (sh.mode == kKLoopA) {
+    e = launch_tcs<4, kKLoopA>(mx, mq, a, sh.smem, blocks, st);
+  } else if (sh.mode == kKLoopQ) {
+    e = launch_tcs<4, kKLoopQ>(mx, mq, a, sh.smem, blocks, st);
+  } else {
+    switch (sh.nksteps) {
+      case 2: e = launch_tcs<2, kFused>(mx, mq, a, sh.smem, blocks, st); break;
+      case 4: e = launch_tcs<4, kFused>(mx, mq, a, sh.smem, blocks, st); break;
+      case 6: e = launch_tcs<6, kFused>(mx, mq, a, sh.smem, blocks, st); break;
+      case 8: e = launch_tcs<8, kFused>(mx, mq, a, sh.smem, blocks, st); break;
+      default: return cudaErrorNotSupported;
+    }
   }
   if (e != cudaSuccess) return e;
   const int64_t r = N - a.T * L;
   if (r > 0) {
     dim3 grid((unsigned)cdiv(r, kTailRows), (unsigned)cdiv(M, kTailQ));
-    k1_tcs_tail<<<grid, kTailQ, 0, st>>>(reinterpret_cast<const __nv_bfloat16*>(X),
+    const size_t tsmem = (size_t)kTailRows * pitch * 2;  // <= 32 KB (pitch <= 4096)
+    k1_tcs_tail<<<grid, kTailQ, tsmem, st>>>(reinterpret_cast<const __nv_bfloat16*>(X),
                                          reinterpret_cast<const __nv_bfloat16*>(Qp), hnorm, N, M,
                                          L, a.T, pitch, metric, G);
     e = cudaGetLastError();

@@ -195,7 +195,11 @@ k2_topk_kernel(Src src, int64_t nelem, int Kp, int CH, int CAP, const uint64_t* 
     __syncthreads();
   };
   for (int64_t base = 0; base < nelem; base += blockDim.x) {
-    if (cnt + (int)blockDim.x > CH) flush();
+    // every thread reads the count before any thread appends again, so the
+    // flush decision (which contains barriers) is the same in every thread
+    const int c = cnt;
+    __syncthreads();
+    if (c + (int)blockDim.x > CH) flush();
     const int64_t e = base + threadIdx.x;
     if (e < nelem) {
       const uint64_t k = src.key(i, e);

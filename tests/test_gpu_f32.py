@@ -246,3 +246,46 @@ def test_backward_deterministic_is_bitwise_repeatable():
     assert all(np.array_equal(outs[0], o) for o in outs[1:])
     _, odx = oracle.grad(Q, X, idx.astype(np.int64), w.astype(np.float64), "ip", want_dq=False)
     np.testing.assert_allclose(outs[0], odx, rtol=1e-5, atol=1e-4)
+
+
+@pytest.mark.parametrize("dtype", ["f32", "bf16"])
+def test_search_many_queries_large_L_cta_rescoring(dtype):
+    """L > 1024 and K' > 64 take the CTA ExactRescoring kernel, whose
+    candidate buffer fills and flushes many times per query; 1500 queries
+    against the oracle catch a lost candidate."""
+    X, Q = inputs(20000, 1500, 32, seed=91)
+    K, L = 100, 2048
+    if dtype == "f32":
+        # few queries are decided at all 100 ranks; the per-query rules (values
+        # by rank, own values, bin maxima) still apply to every query, and the
+        # returned sets must match the oracle's
+        _, gi = run_and_check(X, Q, "ip", K, L, 2)
+        V, A = oracle.partial_reduce(Q, X, L, "ip")
+        _, cand = oracle.topk_pairs(V, A, 2 * K)
+        _, oi = oracle.rerank(Q, X, cand, K, "ip")
+        agree = np.mean([len(set(gi[r]) & set(oi[r])) / K for r in range(len(Q))])
+        assert agree > 0.999, agree
+    else:
+        from tests.test_gpu_lowp import run_lowp
+        run_lowp(X, Q, "ip", "bf16", K, L, 2)
+
+
+@pytest.mark.parametrize("dtype,metric", [("f32", "ip"), ("bf16", "l2"), ("bf16", "cos"),
+                                          ("e4m3", "cos")])
+def test_search_is_repeatable_whatever_the_workspace_holds(dtype, metric):
+    """The same call twice, the workspace filled with different bytes before
+    each: results must be bit-identical (nothing reads scratch it did not
+    write, and no step depends on thread timing)."""
+    X, Q = inputs(30000, 700, 64, seed=93)
+    d = db(X, metric, dtype)
+    outs = []
+    for fill in (0x00, 0xA5, 0x5A):
+        for t in d._ws.values():
+            t.fill_(fill)
+        v, i = d.search(dev(Q), 100, L=2048, rerank=2)
+        outs.append((host(v), host(i)))
+        for t in d._ws.values():
+            t.fill_(fill ^ 0xFF)
+    for v, i in outs[1:]:
+        assert np.array_equal(i, outs[0][1])
+        assert np.array_equal(v.view(np.uint32), outs[0][0].view(np.uint32))

@@ -85,6 +85,55 @@ def test_partial_reduce_lowp(dtype, metric, shape):
         assert np.all(np.abs(V - own) <= tight), (L,)
 
 
+@pytest.mark.parametrize("metric", METRICS)
+@pytest.mark.parametrize("shape", [(1500, 33, 768), (900, 5, 1000), (600, 3, 4096), (2049, 17, 200)])
+def test_partial_reduce_bf16_long_rows(metric, shape):
+    """BF16 rows longer than 128 elements: the K loop walks one 128-byte K
+    block per stage (query tile resident up to 256, streamed beyond)."""
+    N, M, D = shape
+    X, Q = inputs(N, M, D, seed=N + D)
+    Xs, _ = stored(X, metric, "bf16")
+    Qs, _ = stored(Q, metric, "bf16")
+    d = db(X, metric, "bf16")
+    Sm = PT.score_matrix(Qs, Xs, om(metric))
+    scale = PT.query_scale(Qs, Xs, metric)
+    for L in (1, 16, 100, N):
+        V, A = d.partial_reduce(dev(Q), L)
+        V, A = host(V).astype(np.float64), host(A)
+        Vo, Ao = oracle.partial_reduce(Qs, Xs, L, om(metric))
+        if metric == "l2":
+            Vo = (Vo + (Qs ** 2).sum(1)[:, None]) / 2.0
+        tol = PT.REL_LOWP * scale
+        best, second = PT.bin_best_second(Sm, L)
+        decided = (best - second) > 2 * tol[:, None]
+        assert np.all(A % L == np.arange(L)[None, :])
+        np.testing.assert_array_equal(A[decided], Ao[decided])
+        # FP32 accumulation of D products (and the three-part split of h for L2)
+        tight = 3e-5 * scale[:, None] + 2.0 ** -20 * np.abs(Vo)
+        own = Sm[np.arange(M)[:, None], A]
+        if metric == "l2":
+            own = (own + (Qs ** 2).sum(1)[:, None]) / 2.0
+        assert np.all(np.abs(V - Vo)[decided] <= tight[decided]), (L,)
+        assert np.all(np.abs(V - own) <= tight), (L,)
+
+
+@pytest.mark.parametrize("metric", METRICS)
+def test_search_bf16_long_rows(metric):
+    X, Q = inputs(3000, 40, 768, seed=77)
+    # i.i.d. rows of length 768: the score gaps lie inside the stated tolerance,
+    # so few queries are decided; the within-tolerance checks still apply
+    for K, L, rr in [(10, 128, 2), (5, 3000, 1)]:
+        run_lowp(X, Q, metric, "bf16", K, L, rr)
+    # planted neighbours: each query is a row plus small noise, so that row is
+    # the best by a wide margin (score ~ D against ~3.5 sqrt(D) for the rest)
+    # and must come back first
+    g = rng(78)
+    rows = g.choice(3000, size=40, replace=False)
+    Qp = (X[rows] + 0.01 * g.standard_normal((40, 768))).astype(np.float32)
+    _, gi = run_lowp(X, Qp, metric, "bf16", 1, 128, 2)
+    assert np.array_equal(gi[:, 0], rows)
+
+
 # ----------------------------------------------------------------------------
 # Search with FP32 re-rank
 # ----------------------------------------------------------------------------
