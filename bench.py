@@ -44,6 +44,10 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--fp32-steps", type=int, default=10)
     ap.add_argument("--bins", default="mod", choices=["mod", "contiguous"])
+    ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--serving-requests", type=int, default=1200)
+    ap.add_argument("--serving-rates", default="6000,40000",
+                    help="offered requests/s, one trace per rate")
     return ap.parse_args()
 
 
@@ -326,6 +330,8 @@ def main():
                             "achieved_gbs": k1_bytes / (k1_ms / 1e3) / 1e9,
                             "peak_gbs": pk["hbm_gbs"]}}
 
+    serving = None if args.no_serving else serving_leg(args, db, w)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import oracle
@@ -353,12 +359,53 @@ def main():
                 "fp32_path": {"value": world * M / (ms32 / 1e3), "unit": "queries/s",
                               "ms_per_step": ms32, "recall_at_10": recall32},
                 "kernels": prof, "roofline": roof, "e2e": e2e,
+                "serving": serving,
                 "gpu_launches": launches_per_step * args.steps, "clocks": clk,
                 "cpu_baseline": cpu}
         print(json.dumps(line))
     if world > 1:
         dist.destroy_process_group()
     return 0
+
+
+def serving_leg(args, db1, w1):
+    """Continuous batching over two resident databases: the bench's own
+    (1M x 128, L2) and a 500,000 x 768 inner-product mixture (the serving
+    configuration's second database, scaled from 4M rows so that its host
+    generation stays short). Seeded Poisson arrivals, m log-uniform in
+    [1, 512], K in {10, 100}. Latency = completion - arrival, wall clock."""
+    import torch
+    from paper_2206_14286_gb300 import search as S, serve as SV, synth
+    X2 = synth.mixture(500_000, 768, 256, 11)
+    db2 = S.Database(torch.from_numpy(X2).cuda(), metric="ip", dtype="bf16")
+    del X2
+    dbs = {"db1_1m_x128_l2": db1, "db2_500k_x768_ip": db2}
+    shapes = {"db1_1m_x128_l2": (128, 256), "db2_500k_x768_ip": (768, 256)}
+    runs = []
+    for rate in [float(r) for r in args.serving_rates.split(",") if r]:
+        trace = synth.serving_trace(args.serving_requests, rate, shapes)
+        trace = [(t, n, torch.from_numpy(q).pin_memory(), K) for t, n, q, K in trace]
+        srv = SV.Server(dbs, hbm_budget=4 << 30, max_batch=4096, slots=3)
+        # warm-up: one request of every class, then the timed trace
+        for n in dbs:
+            for K in (10, 100):
+                srv.submit(n, torch.zeros((8, shapes[n][0])), K)
+        srv.drain()
+        srv.take_finished()
+        srv.batches = srv.max_in_flight = 0
+        t0 = time.perf_counter()
+        done = SV.run_trace(srv, trace)
+        wall = time.perf_counter() - t0
+        out = SV.latency_summary(done, wall)
+        out.update({"offered_requests_per_s": rate, "batches": srv.batches,
+                    "max_in_flight": srv.max_in_flight,
+                    "errors": sum(r.error is not None for r in done)})
+        runs.append(out)
+    S.sync_status()
+    del db2
+    return {"databases": "1M x 128 L2 and 500k x 768 IP, BF16, FP32 re-rank of 2K",
+            "arrivals": "seeded Poisson, m log-uniform in [1, 512], K in {10, 100}",
+            "runs": runs}
 
 
 def config_of(w, L, L_min=None, bins="mod"):
