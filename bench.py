@@ -321,7 +321,7 @@ def main():
     roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
             "frac": achieved / peak, "traffic": traffic,
             "peak_source": "%s bf16 dense burst (MEASURED_PEAKS.json)" % pk_kind,
-            "kernel": ("k1_tcq_kernel (fused BF16 contraction + PartialReduce, contiguous bins)"
+            "kernel": ("k1_tcs_kernel: fused BF16 contraction + PartialReduce, contiguous bins"
                        if bins == "contiguous" else
                        "k1_tcs_kernel (+ k1_tcs_tail for the N mod L ragged rows): fused BF16 "
                        "contraction + PartialReduce, j mod L bins"),
@@ -424,7 +424,7 @@ def k1_traffic(M, N, D, bins="mod"):
     kernel source and launch shape (else None). The summary holds lines
     "- kernel source sha256: <16 hex>", "- bins: ...", "- M: ...", "- N: ...",
     "- D: ..." and "- dram bytes per launch: <int>"."""
-    name = "k1_tcq_mix_l2_1m.md" if bins == "contiguous" else "k1_tcs_mix_l2_1m.md"
+    name = "k1_tcs_mix_l2_1m.md"
     p = os.path.join(ROOT, "profiles", name)
     if not os.path.exists(p):
         return None
@@ -433,8 +433,7 @@ def k1_traffic(M, N, D, bins="mod"):
         if line.startswith("- ") and ":" in line:
             k, v = line[2:].split(":", 1)
             fields[k.strip()] = v.strip().strip("`")
-    src = "k1_tcq.cu" if bins == "contiguous" else "k1_tcs.cu"
-    h = hashlib.sha256(open(os.path.join(ROOT, "paper_2206_14286_gb300", "csrc", src),
+    h = hashlib.sha256(open(os.path.join(ROOT, "paper_2206_14286_gb300", "csrc", "k1_tcs.cu"),
                             "rb").read()).hexdigest()[:16]
     try:
         if (fields.get("kernel source sha256") != h or fields.get("bins") != bins

@@ -227,8 +227,8 @@ knn_status layout_search(const SearchArgs& a, SearchLayout* s) {
   int64_t L;
   if ((st = resolve_L(a, &L)) != KNN_OK) return st;
   s->contiguous = a.bin_map == KNN_BINS_CONTIGUOUS;
-  s->keys64 = s->contiguous ? true : k1_tcs_supported(a.dtype, a.D, a.metric, a.N, L);
-  if (s->contiguous && !k1_tcq_supported(a.dtype, a.D, a.metric)) return KNN_EUNSUPPORTED;
+  s->keys64 = k1_tcs_supported(a.dtype, a.D, a.metric, a.N, L);
+  if (s->contiguous && !s->keys64) return KNN_EUNSUPPORTED;
   if (s->keys64) {
     // K2 reads the merged [M][L] keys directly: a plan with one bin per L
     K1Plan p{};
@@ -323,11 +323,8 @@ cudaError_t prep_queries(const SearchArgs& a, const SearchLayout& s, char* ws, c
 cudaError_t run_k1(const K1Plan& p, const SearchArgs& a, const void* xlp, const float* xscale,
                    const float* hnorm, const void* qlp, const float* qscale, Partials parts,
                    cudaStream_t st) {
-  if (parts.keys64 && a.bin_map == KNN_BINS_CONTIGUOUS)
-    return launch_k1_tcq(p.N, p.M, p.L, p.D, p.metric, xlp, hnorm, qlp,
-                         reinterpret_cast<unsigned long long*>(parts.v), st);
   if (parts.keys64)
-    return launch_k1_tcs(p.N, p.M, p.L, p.D, p.metric, xlp, hnorm, qlp,
+    return launch_k1_tcs(p.N, p.M, p.L, p.D, p.metric, a.bin_map, xlp, hnorm, qlp,
                          reinterpret_cast<unsigned long long*>(parts.v), st);
   if (a.dtype == KNN_F32)
     return launch_k1_simt(p, reinterpret_cast<const float*>(xlp), hnorm,
@@ -757,9 +754,8 @@ knn_status knn_sync_status(void) {
   cudaError_t e = cudaDeviceSynchronize();
   if (e != cudaSuccess) return cuda_status(e);
   const bool t1 = k1_tc_take_timeout();
-  const bool t2 = k1_tcq_take_timeout();
-  const bool t3 = k1_tcs_take_timeout();
-  if (t1 || t2 || t3) return KNN_ETIMEOUT;
+  const bool t2 = k1_tcs_take_timeout();
+  if (t1 || t2) return KNN_ETIMEOUT;
   return KNN_OK;
 }
 

@@ -70,7 +70,8 @@ constexpr int kCtrlRegsS = 64, kEpiRegsS = 104;
 
 struct TcsArgs {
   int64_t N, M, L, T;              // T = floor(N / L) full grid rows
-  int64_t ntg, nbg;                // grid-row groups of 16, bin groups of 16
+  int64_t ntg, nbg;                // grid-row groups of 16, bin groups of 16 (j mod L)
+  int64_t bq, br;                  // contiguous bins: q = N / L, r = N mod L
   int64_t steps_per_cta, steps_per_q, nqt;
   int pitch;                       // row length in elements (multiple of 16)
   int nkb, nksteps, stages;
@@ -126,7 +127,20 @@ __device__ __forceinline__ uint32_t ext_off_s(int r, int kc) {
 //              block of the 256 queries too.
 constexpr int kFused = 0, kKLoopA = 1, kKLoopQ = 2;
 
-template <int NKS, int MODE>
+// Bin maps: kBinsMod (bin = j mod L, steps over the [T][L] grid view) and
+// kBinsRun (Alg. 1's ShiftRight generalised to L balanced runs of consecutive
+// rows; a step is 256 consecutive rows, and a thread follows one current bin).
+constexpr int kBinsMod = 0, kBinsRun = 1;
+
+__device__ __forceinline__ int64_t run_bin_of(int64_t p, int64_t q, int64_t r) {
+  const int64_t big = r * (q + 1);
+  return p < big ? p / (q + 1) : r + (p - big) / q;
+}
+__device__ __forceinline__ int64_t run_bin_end(int64_t b, int64_t q, int64_t r) {
+  return (b + 1) * q + min(b + 1, r);
+}
+
+template <int NKS, int MODE, int BM>
 __global__ void __launch_bounds__(kThreadsS, 1)
 k1_tcs_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmQ,
               const TcsArgs a) {
@@ -223,11 +237,17 @@ k1_tcs_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
           tma_load_2d(dst, &tmQ, b_full + 8 * s, kb * (kSpanS / 2), (int)(qtile * kQT));
           dst += kStageS;
         }
-        // one box: K block kb (64 elements), grid rows tg*16 .. +15, bins
-        // bg*16 .. +15, landing as [bin][grid row][128 B]; bins past L, rows
-        // past T and elements past the row read the fill value (zero)
-        tma_load_3d(dst, &tmX, b_full + 8 * s, kb * (kSpanS / 2), (int)(tg * kRowsBin),
-                    (int)(bg * kBinsStep));
+        if constexpr (BM == kBinsRun) {
+          // 256 consecutive rows; rows past N read the fill value (zero)
+          tma_load_2d(dst, &tmX, b_full + 8 * s, kb * (kSpanS / 2),
+                      (int)((s_begin + g / NKB) * kCols));
+        } else {
+          // one box: K block kb (64 elements), grid rows tg*16 .. +15, bins
+          // bg*16 .. +15, landing as [bin][grid row][128 B]; bins past L, rows
+          // past T and elements past the row read the fill value (zero)
+          tma_load_3d(dst, &tmX, b_full + 8 * s, kb * (kSpanS / 2), (int)(tg * kRowsBin),
+                      (int)(bg * kBinsStep));
+        }
       }
       __syncwarp();
       issued = g + 1;
@@ -407,14 +427,22 @@ k1_tcs_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
     // of the next step are in flight while a step is written.
     float hb[2][8];
     int64_t bg = s_begin / a.ntg, tg = s_begin % a.ntg;
+    // (with contiguous bins: column n is row step*256 + n)
+    int64_t rstep = s_begin;  // contiguous bins: the step being loaded
     auto load = [&](int64_t bgx, int64_t tgx, bool live, float (&h)[8]) {
 #pragma unroll
       for (int k = 0; k < 8; ++k) {
         const int c = lane + 32 * k;
-        const int64_t b = bgx * kBinsStep + (c & 15);
-        const int64_t t = tgx * kRowsBin + (c >> 4);
-        h[k] = (live && b < a.L && t < a.T) ? a.hnorm[t * a.L + b] : 0.0f;
+        if constexpr (BM == kBinsRun) {
+          const int64_t p = rstep * kCols + c;
+          h[k] = (live && p < a.N) ? a.hnorm[p] : 0.0f;
+        } else {
+          const int64_t b = bgx * kBinsStep + (c & 15);
+          const int64_t t = tgx * kRowsBin + (c >> 4);
+          h[k] = (live && b < a.L && t < a.T) ? a.hnorm[t * a.L + b] : 0.0f;
+        }
       }
+      ++rstep;
     };
     int64_t bgn = bg, tgn = tg;
     auto advance = [&](int64_t& b, int64_t& t) {
@@ -447,7 +475,7 @@ k1_tcs_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
 #pragma unroll
         for (int k = 0; k < 8; ++k) {
           const int c = lane + 32 * k;
-          const int n = (c & 15) * kRowsBin + (c >> 4);
+          const int n = BM == kBinsRun ? c : (c & 15) * kRowsBin + (c >> 4);
           const float hv = hb[cur][k];
           const __nv_bfloat16 hi = __float2bfloat16_rn(hv);
           const float rem1 = hv - __bfloat162float(hi);
@@ -477,6 +505,75 @@ k1_tcs_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
   unsigned long long* gq = a.G + (q_ok ? qi : 0) * a.L;
   const uint32_t tbase =
       tmem_base + ((uint32_t)(quad * 32) << 16) + (uint32_t)(h * kCols + cq * 128);
+  if constexpr (BM == kBinsRun) {
+    // Contiguous bins: this warpgroup sees rows s*256 + cq*128 .. +127 of
+    // every step s, in increasing order. A thread follows the current bin
+    // (the same for every lane: bins depend on rows only) with its best score
+    // and row, and merges it into G when the rows leave the bin.
+    const int64_t first = min((s_begin * kCols + cq * 128), a.N - 1);
+    int64_t cur = run_bin_of(first, a.bq, a.br);
+    int64_t seg_end = run_bin_end(cur, a.bq, a.br);
+    float bv = __uint_as_float(kNegInfBits);
+    int64_t brow = -1;
+    auto flush_run = [&]() {
+      if (q_ok && brow >= 0)
+        atomicMax(&gq[cur], (unsigned long long)make_key(bv, (int32_t)brow));
+    };
+    for (int i = 0; i < ns; ++i) {
+      if (!mbar_wait_sleep(b_accf + 8 * h, (uint32_t)(i & 1), abort_flag, 32)) break;
+      tc_fence_after();
+      const int64_t p0 = (s_begin + i) * kCols + cq * 128;
+#pragma unroll
+      for (int half64 = 0; half64 < 2; ++half64) {
+        float r[4][16], m[4];
+        __syncwarp();
+        tmem_ld4x16_max_s(tbase + (uint32_t)(half64 * 64), r, m);
+        if (half64 == 1) {
+          // everything of this accumulator is in registers: release it
+          tc_fence_before();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(b_acce + 8 * h);
+        }
+#pragma unroll
+        for (int g = 0; g < 4; ++g) {
+          const int64_t pg = p0 + half64 * 64 + g * 16;
+          if (pg + 16 <= seg_end && pg + 16 <= a.N) {
+            // the 16 rows lie inside the current bin: one compare
+            if (m[g] > bv) {
+              int pos = 0;
+#pragma unroll
+              for (int k = 15; k >= 0; --k) pos = (r[g][k] == m[g]) ? k : pos;
+              bv = m[g];
+              brow = pg + pos;
+            }
+          } else {
+            // a bin boundary or the end of the rows falls in this run
+#pragma unroll
+            for (int k = 0; k < 16; ++k) {
+              const int64_t p = pg + k;
+              if (p < a.N) {
+                while (p >= seg_end) {
+                  flush_run();
+                  ++cur;
+                  seg_end = run_bin_end(cur, a.bq, a.br);
+                  bv = __uint_as_float(kNegInfBits);
+                  brow = -1;
+                }
+                if (r[g][k] > bv) {
+                  bv = r[g][k];
+                  brow = p;
+                }
+              }
+            }
+          }
+        }
+      }
+    }
+    tc_fence_before();
+    asm volatile("bar.arrive 1, %0;" ::"n"(32 + 512) : "memory");
+    flush_run();
+    return;
+  }
   int64_t bg = s_begin / a.ntg, tg = s_begin % a.ntg;
   float best[8];
   int32_t bt[8];
@@ -706,20 +803,20 @@ bool tcs_shape(int D, int metric, TcsShape* sh) {
   return true;
 }
 
-template <int NKS, int MODE>
+template <int NKS, int MODE, int BM>
 cudaError_t launch_tcs(const CUtensorMap& mx, const CUtensorMap& mq, const TcsArgs& a, size_t smem,
                        int64_t blocks, cudaStream_t st) {
   // setmaxnreg.inc waits until the registers it asks for are free: refuse to
   // launch unless the launch-time allocation covers the split.
   cudaFuncAttributes fa;
-  cudaError_t e = cudaFuncGetAttributes(&fa, k1_tcs_kernel<NKS, MODE>);
+  cudaError_t e = cudaFuncGetAttributes(&fa, k1_tcs_kernel<NKS, MODE, BM>);
   if (e != cudaSuccess) return e;
   if ((int64_t)round_up(fa.numRegs, 8) * kThreadsS < 128 * kCtrlRegsS + 512 * kEpiRegsS)
     return cudaErrorNotSupported;
-  e = cudaFuncSetAttribute(k1_tcs_kernel<NKS, MODE>,
+  e = cudaFuncSetAttribute(k1_tcs_kernel<NKS, MODE, BM>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  k1_tcs_kernel<NKS, MODE><<<(unsigned)blocks, kThreadsS, smem, st>>>(mx, mq, a);
+  k1_tcs_kernel<NKS, MODE, BM><<<(unsigned)blocks, kThreadsS, smem, st>>>(mx, mq, a);
   return cudaGetLastError();
 }
 
@@ -729,15 +826,28 @@ bool k1_tcs_supported(int dtype, int D, int metric, int64_t N, int64_t L) {
   TcsShape sh;
   if (dtype != KNN_BF16 || metric < KNN_IP || metric > KNN_COS) return false;
   if (!tcs_shape(D, metric, &sh)) return false;
-  if (L < 1 || L > N) return false;
-  // TMA coordinates are 32-bit: the grid row must stay below 2^31 elements
-  const int64_t pitch = round_up(D, 16);
-  return L * pitch + kBinsStep * pitch < ((int64_t)1 << 31) && N / L < ((int64_t)1 << 31);
+  if (L < 1 || L > N || N >= ((int64_t)1 << 31)) return false;
+  // the grid view's row stride (L rows) must stay below 2^40 bytes
+  return L * round_up(D, 16) * 2 < ((int64_t)1 << 40);
 }
 
-cudaError_t launch_k1_tcs(int64_t N, int64_t M, int64_t L, int D, int metric, const void* X,
-                          const float* hnorm, const void* Qp, unsigned long long* G,
-                          cudaStream_t st) {
+template <int BM>
+cudaError_t launch_tcs_mode(const TcsShape& sh, const CUtensorMap& mx, const CUtensorMap& mq,
+                            const TcsArgs& a, int64_t blocks, cudaStream_t st) {
+  if (sh.mode == kKLoopA) return launch_tcs<4, kKLoopA, BM>(mx, mq, a, sh.smem, blocks, st);
+  if (sh.mode == kKLoopQ) return launch_tcs<4, kKLoopQ, BM>(mx, mq, a, sh.smem, blocks, st);
+  switch (sh.nksteps) {
+    case 2: return launch_tcs<2, kFused, BM>(mx, mq, a, sh.smem, blocks, st);
+    case 4: return launch_tcs<4, kFused, BM>(mx, mq, a, sh.smem, blocks, st);
+    case 6: return launch_tcs<6, kFused, BM>(mx, mq, a, sh.smem, blocks, st);
+    case 8: return launch_tcs<8, kFused, BM>(mx, mq, a, sh.smem, blocks, st);
+    default: return cudaErrorNotSupported;
+  }
+}
+
+cudaError_t launch_k1_tcs(int64_t N, int64_t M, int64_t L, int D, int metric, int bin_map,
+                          const void* X, const float* hnorm, const void* Qp,
+                          unsigned long long* G, cudaStream_t st) {
   TcsShape sh;
   if (!k1_tcs_supported(KNN_BF16, D, metric, N, L) || !tcs_shape(D, metric, &sh))
     return cudaErrorNotSupported;
@@ -745,6 +855,7 @@ cudaError_t launch_k1_tcs(int64_t N, int64_t M, int64_t L, int D, int metric, co
   if ((reinterpret_cast<uintptr_t>(X) & 15) || (reinterpret_cast<uintptr_t>(Qp) & 15))
     return cudaErrorInvalidValue;
   if (M <= 0) return cudaSuccess;
+  const bool runs = bin_map == KNN_BINS_CONTIGUOUS;
   const int pitch = (int)round_up(D, 16);
   TcsArgs a{};
   a.N = N;
@@ -753,8 +864,11 @@ cudaError_t launch_k1_tcs(int64_t N, int64_t M, int64_t L, int D, int metric, co
   a.T = N / L;
   a.ntg = cdiv(a.T, kRowsBin);
   a.nbg = cdiv(L, kBinsStep);
+  a.bq = N / L;
+  a.br = N % L;
   a.nqt = cdiv(M, kQT);
-  a.steps_per_q = a.ntg * a.nbg;
+  // a step: 16 bins x 16 grid rows (j mod L), or 256 consecutive rows
+  a.steps_per_q = runs ? cdiv(N, kCols) : a.ntg * a.nbg;
   const int64_t sms = device_sm_count();
   int64_t cpq = a.nqt >= sms ? 1 : sms / a.nqt;
   if (cpq > a.steps_per_q) cpq = a.steps_per_q;
@@ -774,27 +888,17 @@ cudaError_t launch_k1_tcs(int64_t N, int64_t M, int64_t L, int D, int metric, co
   a.hnorm = hnorm;
   a.G = G;
   CUtensorMap mx, mq;
-  if (!make_map_grid(&mx, X, pitch, L, a.T)) return cudaErrorInvalidValue;
+  const bool mapped = runs ? make_map_s(&mx, X, pitch, N, pitch, kCols)
+                           : make_map_grid(&mx, X, pitch, L, a.T);
+  if (!mapped) return cudaErrorInvalidValue;
   if (!make_map_s(&mq, Qp, pitch, M, pitch, kQT)) return cudaErrorInvalidValue;
   const int64_t blocks = a.nqt * cpq;
   if (blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
-  cudaError_t e;
-  if (sh.mode == kKLoopA) {
-    e = launch_tcs<4, kKLoopA>(mx, mq, a, sh.smem, blocks, st);
-  } else if (sh.mode == kKLoopQ) {
-    e = launch_tcs<4, kKLoopQ>(mx, mq, a, sh.smem, blocks, st);
-  } else {
-    switch (sh.nksteps) {
-      case 2: e = launch_tcs<2, kFused>(mx, mq, a, sh.smem, blocks, st); break;
-      case 4: e = launch_tcs<4, kFused>(mx, mq, a, sh.smem, blocks, st); break;
-      case 6: e = launch_tcs<6, kFused>(mx, mq, a, sh.smem, blocks, st); break;
-      case 8: e = launch_tcs<8, kFused>(mx, mq, a, sh.smem, blocks, st); break;
-      default: return cudaErrorNotSupported;
-    }
-  }
+  cudaError_t e = runs ? launch_tcs_mode<kBinsRun>(sh, mx, mq, a, blocks, st)
+                       : launch_tcs_mode<kBinsMod>(sh, mx, mq, a, blocks, st);
   if (e != cudaSuccess) return e;
   const int64_t r = N - a.T * L;
-  if (r > 0) {
+  if (!runs && r > 0) {
     dim3 grid((unsigned)cdiv(r, kTailRows), (unsigned)cdiv(M, kTailQ));
     const size_t tsmem = (size_t)kTailRows * pitch * 2;  // <= 32 KB (pitch <= 4096)
     k1_tcs_tail<<<grid, kTailQ, tsmem, st>>>(reinterpret_cast<const __nv_bfloat16*>(X),
