@@ -52,6 +52,7 @@ def _load():
             lib.orc_partial_reduce.argtypes = [P, i64, P, i64, i32, i32, i64, P, P]
             lib.orc_partial_reduce_contiguous.argtypes = [P, i64, P, i64, i32, i32, i64, P, P]
             lib.orc_topk_pairs.argtypes = [P, P, i64, i64, i32, P, P]
+            lib.orc_bin_max.argtypes = [P, i64, i64, i64, i32, P, P]
             lib.orc_rerank.argtypes = [P, i64, P, i64, i32, i32, P, i32, i32, P, P]
             lib.orc_grad.argtypes = [P, i64, P, i64, i32, i32, P, i32, P, P, P]
             lib.orc_score.argtypes = [P, P, i32, i32]
@@ -131,6 +132,32 @@ def topk_pairs(V, A, K):
     idx = np.empty((M, K), np.int64)
     _load().orc_topk_pairs(_p(V), _p(A), M, L, K, _p(val), _p(idx))
     return val, idx
+
+
+def bin_max(S, L, bins="mod"):
+    """Per row of the score matrix S (M x N) and bin: the largest score and its
+    column (App. A.1 applied to given scores). (V, A), each M x L; an empty
+    bin has V = -inf, A = -1."""
+    S = _f64(S)
+    M, N = S.shape
+    V = np.empty((M, L), np.float64)
+    A = np.empty((M, L), np.int64)
+    _load().orc_bin_max(_p(S), M, N, L, 0 if bins == "mod" else 1, _p(V), _p(A))
+    return V, A
+
+
+def approx_max_k(S, K, L, bins="mod", is_min=False, aggregate_to_topk=True):
+    """The paper's approx_max_k / approx_min_k operator on a score matrix.
+
+    is_min: the K smallest (approx_min_k), done as the K largest of -S.
+    aggregate_to_topk=False returns the L bin winners (V, A), M x L, in bin
+    order; True returns the best K of them, best first. Values keep the sign
+    of S."""
+    Sx = -_f64(S) if is_min else _f64(S)
+    V, A = bin_max(Sx, L, bins)
+    if aggregate_to_topk:
+        V, A = topk_pairs(V, A, K)
+    return (-V if is_min else V), A
 
 
 def _report(v, metric):

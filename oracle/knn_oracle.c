@@ -183,6 +183,35 @@ void orc_partial_reduce_contiguous(const double *Q, int64_t M, const double *X, 
 }
 
 /* ---------------------------------------------------------------------- */
+/* approx_max_k on a score matrix the caller already has (App. A.1: the   */
+/* operator behind Alg. 1, applied to given scores). For every row i of S */
+/* (M x N, row-major) and bin l, the largest S[i][j] over the columns j of */
+/* bin l and that j: bins j mod L, or (contiguous != 0) the balanced runs  */
+/* of consecutive columns above. Strict '>' while j ascends, so ties keep  */
+/* the smaller j; an empty bin keeps V = -inf, A = -1.                    */
+/* ---------------------------------------------------------------------- */
+void orc_bin_max(const double *S, int64_t M, int64_t N, int64_t L, int contiguous, double *V,
+                 int64_t *A) {
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int64_t i = 0; i < M; ++i) {
+    double *v = V + i * L;
+    int64_t *a = A + i * L;
+    for (int64_t l = 0; l < L; ++l) {
+      v[l] = -INFINITY;
+      a[l] = -1;
+    }
+    for (int64_t j = 0; j < N; ++j) {
+      const double y = S[i * N + j];
+      const int64_t l = contiguous ? contiguous_bin(j, N, L) : j % L;
+      if (y > v[l]) {
+        v[l] = y;
+        a[l] = j;
+      }
+    }
+  }
+}
+
+/* ---------------------------------------------------------------------- */
 /* ExactRescoring (Sec. 5): the top-K of the L (score, index) pairs of     */
 /* each query, best first. Empty bins (A = -1) are skipped. Values stay in */
 /* the internal orientation; indices -1 pad when fewer than K are valid.   */

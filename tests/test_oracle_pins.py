@@ -454,3 +454,62 @@ def test_recall_law_golden_file():
         assert R.min_bins(K, float(r)) == L
         assert R.paper_expected_recall(L, K) == pytest.approx(float(paper), rel=1e-9)
         assert R.exact_expected_recall(N, L, K) == pytest.approx(float(exact), rel=1e-9)
+
+
+# ----------------------------------------------------------------------------
+# approx_max_k on a given score matrix (App. A.1)
+# ----------------------------------------------------------------------------
+@pytest.mark.parametrize("bins", ["mod", "contiguous"])
+def test_bin_max_brute_force_every_L(bins):
+    g = np.random.Generator(np.random.PCG64(31))
+    M, N = 3, 11
+    S = g.integers(-4, 5, size=(M, N)).astype(np.float64)   # many ties
+    for L in range(1, N + 1):
+        V, A = oracle.bin_max(S, L, bins)
+        if bins == "mod":
+            members = [np.arange(l, N, L) for l in range(L)]
+        else:
+            q, r = N // L, N % L
+            members = [np.arange(l * q + min(l, r), (l + 1) * q + min(l + 1, r)) for l in range(L)]
+        for i in range(M):
+            for l in range(L):
+                cols = members[l]
+                j = cols[np.argmax(S[i, cols])]      # numpy keeps the first maximum
+                assert A[i, l] == j and V[i, l] == S[i, j]
+
+
+@pytest.mark.parametrize("bins", ["mod", "contiguous"])
+def test_bin_max_equals_partial_reduce_on_ip_scores(bins):
+    """Integer rows keep every FP64 score exact, so the two definitions meet."""
+    g = np.random.Generator(np.random.PCG64(32))
+    Q = g.integers(-3, 4, size=(5, 6)).astype(np.float64)
+    X = g.integers(-3, 4, size=(40, 6)).astype(np.float64)
+    for L in (1, 3, 7, 40):
+        V1, A1 = oracle.bin_max(Q @ X.T, L, bins)
+        V2, A2 = oracle.partial_reduce(Q, X, L, "ip", bins=bins)
+        assert np.array_equal(A1, A2) and np.array_equal(V1, V2)
+
+
+def test_approx_max_k_with_L_equal_N_is_exact_top_k():
+    g = np.random.Generator(np.random.PCG64(33))
+    S = g.standard_normal((4, 30))
+    S[0, 5] = S[0, 9] = S[0].max() + 1.0          # a tie at the top: smaller index first
+    for is_min in (False, True):
+        v, a = oracle.approx_max_k(S, 6, 30, is_min=is_min)
+        for i in range(4):
+            order = np.lexsort((np.arange(30), S[i] if is_min else -S[i]))[:6]
+            assert np.array_equal(a[i], order)
+            assert np.array_equal(v[i], S[i, order])
+
+
+def test_approx_max_k_bins_only_and_min_orientation():
+    g = np.random.Generator(np.random.PCG64(34))
+    S = g.standard_normal((3, 50))
+    v, a = oracle.approx_max_k(S, 5, 8, aggregate_to_topk=False)
+    assert v.shape == (3, 8) and np.all(a % 8 == np.arange(8))
+    vmin, amin = oracle.approx_max_k(S, 5, 8, is_min=True, aggregate_to_topk=False)
+    for i in range(3):
+        for l in range(8):
+            cols = np.arange(l, 50, 8)
+            assert amin[i, l] == cols[np.argmin(S[i, cols])]
+            assert vmin[i, l] == S[i, cols].min()
