@@ -217,6 +217,38 @@ size_t knn_partial_reduce_workspace(int64_t N, int32_t D, int32_t dtype, int32_t
                                     int64_t M, int64_t L, int32_t bin_map);
 
 /*
+ * The approx_max_k / approx_min_k operator on a score matrix the caller
+ * already has (App. A.1: PartialReduce of Alg. 1 and ExactRescoring without
+ * the fused contraction).
+ *   scores      : M x N row-major, score_dtype KNN_F32 or KNN_BF16 (device).
+ *   K           : results per row with aggregate_to_topk; also the K of the
+ *                 recall law when L <= 0.
+ *   L           : bins (1 <= L <= N); if L <= 0, the smallest L whose Eq. 13
+ *                 recall for K is at least recall_target, computed for
+ *                 planning_size rows (the paper's reduction_input_size_override:
+ *                 the full input size when the caller holds one shard; <= 0
+ *                 means N), clamped to N.
+ *   bin_map     : knn_bin_map over the columns.
+ *   is_min      : 0 = largest scores (approx_max_k), 1 = smallest (approx_min_k).
+ *   aggregate_to_topk : 0 -> out_val / out_idx are M x L, the winner of every
+ *                 bin in bin order (-1 / NaN for an empty bin); 1 -> M x K,
+ *                 the best K bin winners, best first.
+ *   workspace   : knn_approx_max_k_workspace(...) bytes, 256-byte aligned.
+ * Values are the scores as given (same sign); ties keep the smaller column.
+ * Reads every score once: HBM-bound. Errors: KNN_EINVAL (sizes, K > L with
+ * aggregation, NULL, alignment, N >= 2^31), KNN_ENOMEM (workspace).
+ */
+knn_status knn_approx_max_k(const void* scores, int32_t score_dtype, int64_t M, int64_t N,
+                            int32_t K, int64_t L, int64_t planning_size, double recall_target,
+                            int32_t bin_map, int32_t is_min, int32_t aggregate_to_topk,
+                            float* out_val, int32_t* out_idx, void* workspace, size_t ws_bytes,
+                            void* stream);
+
+size_t knn_approx_max_k_workspace(int64_t M, int64_t N, int32_t K, int64_t L,
+                                  int64_t planning_size, double recall_target,
+                                  int32_t aggregate_to_topk);
+
+/*
  * Exact K-NN (Eq. 1-2): the top K over all N rows, scored in `dtype` with
  * FP32 accumulation (the L = N case of PartialReduce), then values recomputed
  * in FP32 from db_f32 (or db_lp if NULL). Same arguments and rules as

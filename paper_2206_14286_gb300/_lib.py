@@ -38,6 +38,9 @@ SIGNATURES = {
     "knn_search_exact": (ctypes.c_int, [P, P, P, P, I64, I32, I32, I32, P, I64, I32, P, P, P, SZ,
                                         P]),
     "knn_search_exact_workspace": (SZ, [I64, I32, I32, I32, I64, I32]),
+    "knn_approx_max_k": (ctypes.c_int, [P, I32, I64, I64, I32, I64, I64, DBL, I32, I32, I32, P, P,
+                                        P, SZ, P]),
+    "knn_approx_max_k_workspace": (SZ, [I64, I64, I32, I64, I64, DBL, I32]),
     "knn_backward": (ctypes.c_int, [P, P, P, I64, I32, I32, I32, P, I64, I32, P, P, P, P, I32,
                                     I32, P, SZ, P]),
     "knn_backward_workspace": (SZ, [I64, I32, I64, I32, I32]),

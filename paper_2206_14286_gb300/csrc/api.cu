@@ -665,6 +665,76 @@ knn_status knn_partial_reduce(const void* db_lp, const float* db_scale, const fl
   return cuda_status(launch_merge_bins(s.plan, parts, out_v, out_a, st));
 }
 
+// ---------------------------------------------------------------------------
+// approx_max_k on a given score matrix (App. A.1)
+// ---------------------------------------------------------------------------
+static knn_status amk_resolve(int64_t M, int64_t N, int32_t K, int64_t L, int64_t planning_size,
+                              double recall_target, int32_t aggregate, int64_t* Lout) {
+  if (M < 0 || N < 1 || N >= ((int64_t)1 << 31)) return KNN_EINVAL;
+  if (L <= 0) {
+    if (K < 1) return KNN_EINVAL;
+    L = plan_bins(planning_size > 0 ? planning_size : N, K, recall_target, 1);
+    if (L < 1) return KNN_EINVAL;
+    if (L > N) L = N;
+  }
+  if (L > N) return KNN_EINVAL;
+  if (aggregate && (K < 1 || K > L || K > kMaxK)) return KNN_EINVAL;
+  *Lout = L;
+  return KNN_OK;
+}
+
+size_t knn_approx_max_k_workspace(int64_t M, int64_t N, int32_t K, int64_t L,
+                                  int64_t planning_size, double recall_target,
+                                  int32_t aggregate_to_topk) {
+  int64_t Lr;
+  if (amk_resolve(M, N, K, L, planning_size, recall_target, aggregate_to_topk, &Lr) != KNN_OK)
+    return 0;
+  size_t t = al((size_t)M * Lr * 8) + (aggregate_to_topk ? al((size_t)M * K * 8) : 0);
+  return t > kAlign ? t : kAlign;
+}
+
+knn_status knn_approx_max_k(const void* scores, int32_t score_dtype, int64_t M, int64_t N,
+                            int32_t K, int64_t L, int64_t planning_size, double recall_target,
+                            int32_t bin_map, int32_t is_min, int32_t aggregate_to_topk,
+                            float* out_val, int32_t* out_idx, void* workspace, size_t ws_bytes,
+                            void* stream) {
+  int64_t Lr;
+  knn_status rc = amk_resolve(M, N, K, L, planning_size, recall_target, aggregate_to_topk, &Lr);
+  if (rc != KNN_OK) return rc;
+  if (score_dtype != KNN_F32 && score_dtype != KNN_BF16) return KNN_EINVAL;
+  if (bin_map != KNN_BINS_MOD && bin_map != KNN_BINS_CONTIGUOUS) return KNN_EINVAL;
+  if (M == 0) return KNN_OK;
+  if (!scores || !out_val || !out_idx || !aligned(out_val, 4) || !aligned(out_idx, 4) ||
+      !aligned(scores, score_dtype == KNN_BF16 ? 2 : 4))
+    return KNN_EINVAL;
+  if (!workspace || !aligned(workspace, kAlign)) return KNN_EINVAL;
+  const size_t need = knn_approx_max_k_workspace(M, N, K, Lr, 0, recall_target, aggregate_to_topk);
+  if (ws_bytes < need) return KNN_ENOMEM;
+  cudaStream_t st = (cudaStream_t)stream;
+  char* ws = reinterpret_cast<char*>(workspace);
+  unsigned long long* G = reinterpret_cast<unsigned long long*>(ws);
+  cudaError_t e = cudaMemsetAsync(G, 0, (size_t)M * Lr * 8, st);
+  if (e == cudaSuccess)
+    e = launch_bin_max(scores, score_dtype, M, N, Lr, bin_map, is_min ? 1 : 0, G, st);
+  if (e != cudaSuccess) return cuda_status(e);
+  if (!aggregate_to_topk)
+    return cuda_status(launch_keys_to_pairs(reinterpret_cast<const uint64_t*>(G), M * Lr,
+                                            is_min ? 1 : 0, out_val, out_idx, st));
+  K1Plan p{};
+  p.M = M;
+  p.N = N;
+  p.L = Lr;
+  p.Lk = Lr;
+  p.g = 1;
+  p.nsplits = 1;
+  Partials parts{reinterpret_cast<float*>(G), nullptr, 0, false, true};
+  uint64_t* keys = reinterpret_cast<uint64_t*>(ws + al((size_t)M * Lr * 8));
+  e = launch_k2(p, parts, K, nullptr, keys, st);
+  if (e == cudaSuccess)
+    e = launch_keys_to_pairs(keys, M * K, is_min ? 1 : 0, out_val, out_idx, st);
+  return cuda_status(e);
+}
+
 size_t knn_search_exact_workspace(int64_t N, int32_t D, int32_t dtype, int32_t metric, int64_t M,
                                   int32_t K) {
   SearchArgs a{nullptr, nullptr, nullptr, nullptr, N, D, dtype, metric, nullptr, M, K, N, 0.5, 1,

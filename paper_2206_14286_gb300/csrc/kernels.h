@@ -69,6 +69,14 @@ cudaError_t launch_k1_tcs(int64_t N, int64_t M, int64_t L, int D, int metric, in
                           unsigned long long* G, cudaStream_t st);
 bool k1_tcs_take_timeout();
 
+// approx_max_k on a caller's score matrix (FP32 or BF16, M x N): the bin
+// winners merged as ordered 64-bit keys into G[M][L] (zero on entry), scores
+// negated first when neg != 0; and the keys turned back into (value, index).
+cudaError_t launch_bin_max(const void* S, int dtype, int64_t M, int64_t N, int64_t L, int bin_map,
+                           int neg, unsigned long long* G, cudaStream_t st);
+cudaError_t launch_keys_to_pairs(const uint64_t* keys, int64_t n, int neg, float* out_v,
+                                 int32_t* out_a, cudaStream_t st);
+
 // K2: per query, merge the partials of every split and fold and select the
 // best Kp (score, index) keys, sorted. If run_in is given its Kp keys per
 // query join the selection (running top-K of a chunked search).

@@ -212,5 +212,37 @@ class Database:
         return dq, dx
 
 
+def approx_max_k(scores, K, L=None, recall_target=0.95, bins="mod", is_min=False,
+                 aggregate_to_topk=True, planning_size=0, stream=None):
+    """The approx_max_k / approx_min_k operator (knn_approx_max_k) on an M x N
+    FP32 or BF16 CUDA score matrix. Returns (values, indices): M x K best
+    first with aggregate_to_topk, else M x L bin winners in bin order."""
+    if scores.dim() != 2 or not scores.is_cuda or scores.dtype not in (torch.float32,
+                                                                        torch.bfloat16):
+        raise ValueError("scores must be a 2-D float32 or bfloat16 CUDA tensor")
+    S = scores.contiguous()
+    M, N = S.shape
+    dt = DTYPE["f32"] if S.dtype == torch.float32 else DTYPE["bf16"]
+    lib = _lib.get()
+    Lr = int(L) if L else 0
+    nb = lib.knn_approx_max_k_workspace(M, N, int(K), Lr, int(planning_size), recall_target,
+                                        int(bool(aggregate_to_topk)))
+    if nb == 0:
+        raise ValueError("invalid approx_max_k arguments (M=%d N=%d K=%d L=%d)" % (M, N, K, Lr))
+    if not Lr:
+        Lr = min(plan_bins(planning_size or N, K, recall_target), N)
+    width = int(K) if aggregate_to_topk else Lr
+    val = torch.empty((M, width), dtype=torch.float32, device=S.device)
+    idx = torch.empty((M, width), dtype=torch.int32, device=S.device)
+    ws = _workspace(nb, S.device)
+    with torch.cuda.device(S.device):
+        check(lib.knn_approx_max_k(S.data_ptr(), dt, M, N, int(K), Lr, int(planning_size),
+                                   recall_target, BINS[bins], int(bool(is_min)),
+                                   int(bool(aggregate_to_topk)), val.data_ptr(), idx.data_ptr(),
+                                   ws.data_ptr(), ws.numel(), _stream(stream)),
+              "knn_approx_max_k")
+    return val, idx
+
+
 def sync_status():
     check(_lib.get().knn_sync_status(), "knn_sync_status")

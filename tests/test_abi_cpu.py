@@ -101,3 +101,28 @@ def test_workspace_grows_with_queries(lib):
         b = lib.knn_search_workspace(10 ** 6, 128, 1, 1, 2048, 10, 256, bm, 0.95, 2)
         assert 0 < a < b
         assert lib.knn_search_host_workspace(10 ** 6, 128, 1, 1, 1024, 10, 256, bm, 0.95, 2) > a
+
+
+def test_approx_max_k_argument_checks_need_no_device(lib):
+    f = lib.knn_approx_max_k
+    # (scores, dtype, M, N, K, L, planning, r, bins, is_min, agg, val, idx, ws, wsb, stream)
+    base = [None, 0, 4, 100, 5, 10, 0, 0.9, 0, 0, 1, None, None, None, 0, None]
+
+    def call(**kw):
+        a = list(base)
+        pos = {"dt": 1, "M": 2, "N": 3, "K": 4, "L": 5, "bins": 8, "agg": 10}
+        for k, v in kw.items():
+            a[pos[k]] = v
+        return f(*a)
+
+    assert call(M=0) == _lib.KNN_OK
+    assert call(N=0) == _lib.KNN_EINVAL
+    assert call(L=101) == _lib.KNN_EINVAL
+    assert call(K=11) == _lib.KNN_EINVAL                 # K > L with aggregation
+    assert call(K=11, agg=0) == _lib.KNN_EINVAL          # still NULL pointers
+    assert call(dt=2) == _lib.KNN_EINVAL                 # E4M3 scores are not accepted
+    assert call(bins=5) == _lib.KNN_EINVAL
+    assert call() == _lib.KNN_EINVAL                     # NULL pointers
+    assert lib.knn_approx_max_k_workspace(4, 100, 5, 10, 0, 0.9, 1) >= 4 * 10 * 8 + 4 * 5 * 8
+    assert lib.knn_approx_max_k_workspace(4, 100, 5, 0, 0, 0.9, 0) > 0   # L planned
+    assert lib.knn_approx_max_k_workspace(4, 100, 0, 0, 0, 0.9, 0) == 0  # no K to plan L
