@@ -45,6 +45,7 @@ def parse():
     ap.add_argument("--fp32-steps", type=int, default=10)
     ap.add_argument("--bins", default="mod", choices=["mod", "contiguous"])
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--no-unfused", action="store_true")
     ap.add_argument("--serving-requests", type=int, default=1200)
     ap.add_argument("--serving-rates", default="6000,40000",
                     help="offered requests/s, one trace per rate")
@@ -331,6 +332,7 @@ def main():
                             "peak_gbs": pk["hbm_gbs"]}}
 
     serving = None if args.no_serving else serving_leg(args, db, w)
+    unfused = None if args.no_unfused else unfused_leg(Xd, Qd, K, L)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -360,12 +362,54 @@ def main():
                               "ms_per_step": ms32, "recall_at_10": recall32},
                 "kernels": prof, "roofline": roof, "e2e": e2e,
                 "serving": serving,
+                "unfused_baseline": unfused,
                 "gpu_launches": launches_per_step * args.steps, "clocks": clk,
                 "cpu_baseline": cpu}
         print(json.dumps(line))
     if world > 1:
         dist.destroy_process_group()
     return 0
+
+
+def unfused_leg(Xd, Qd, K, L):
+    """The fusion argument (App. A.6) on this GPU: the same inner-product
+    search done unfused -- a cuBLAS BF16 GEMM writes the M x N score matrix
+    to HBM, then approx_max_k reads it back (bins, top-K) -- against the fused
+    search (PartialReduce inside the contraction, ExactRescoring, re-rank of
+    the K winners). Same rows and queries as the main workload, BF16, K, L."""
+    import torch
+    from paper_2206_14286_gb300 import search as S
+    M, N = Qd.shape[0], Xd.shape[0]
+    db_ip = S.Database(Xd, metric="ip", dtype="bf16", keep_f32=True)
+    Xb, Qb = Xd.to(torch.bfloat16), Qd.to(torch.bfloat16)
+    scores = torch.empty((M, N), dtype=torch.bfloat16, device="cuda")
+
+    def events(fn, reps=5):
+        for _ in range(2):
+            fn()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(reps):
+            fn()
+        b.record()
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / reps
+
+    gemm_ms = events(lambda: torch.matmul(Qb, Xb.t(), out=scores))
+    amk_ms = events(lambda: S.approx_max_k(scores, K, L=L))
+    unfused_ms = events(lambda: S.approx_max_k(torch.matmul(Qb, Xb.t(), out=scores), K, L=L))
+    fused_ms = events(lambda: db_ip.search(Qd, K, L=L, rerank=1))
+    sbytes = M * N * 2
+    out = {"workload": "IP, BF16, N=%d x D=%d, M=%d, K=%d, L=%d" % (N, Xd.shape[1], M, K, L),
+           "gemm_ms": gemm_ms, "approx_max_k_ms": amk_ms,
+           "approx_max_k_gbs": sbytes / (amk_ms / 1e3) / 1e9,
+           "score_matrix_bytes": sbytes, "unfused_ms": unfused_ms, "fused_ms": fused_ms,
+           "fused_speedup": unfused_ms / fused_ms,
+           "paper": "24.9 ms unfused vs 2.6 ms fused (9.6x) on one TPU v4 core, App. A.6"}
+    del scores, Xb, Qb, db_ip
+    torch.cuda.empty_cache()
+    return out
 
 
 def serving_leg(args, db1, w1):

@@ -41,11 +41,22 @@ bin_max_mod_kernel(const void* __restrict__ S, int64_t N, int64_t L, int64_t kch
   const int64_t k1 = min(cdiv(N, L), k0 + kchunk);
   const float sg = neg ? -1.0f : 1.0f;
   uint64_t best = 0;
-  for (int64_t k = k0; k < k1; ++k) {
-    const int64_t j = k * L + b;
-    if (j >= N) break;
-    const uint64_t key = make_key(load_score<DT>(S, i * N + j, sg), (int32_t)j);
-    best = key > best ? key : best;
+  // eight independent loads in flight per thread
+  for (int64_t k = k0; k < k1; k += 8) {
+    float v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int64_t j = (k + u) * L + b;
+      v[u] = (k + u < k1 && j < N) ? load_score<DT>(S, i * N + j, sg) : 0.0f;
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int64_t j = (k + u) * L + b;
+      if (k + u < k1 && j < N) {
+        const uint64_t key = make_key(v[u], (int32_t)j);
+        best = key > best ? key : best;
+      }
+    }
   }
   if (best) atomicMax(&G[i * L + b], (unsigned long long)best);
 }
@@ -69,15 +80,29 @@ bin_max_runs_kernel(const void* __restrict__ S, int64_t N, int64_t L, int64_t ch
   const float sg = neg ? -1.0f : 1.0f;
   int64_t cur = -1, end = 0;
   uint64_t best = 0;
-  for (int64_t j = j0 + threadIdx.x; j < j1; j += blockDim.x) {
-    if (j >= end) {
-      if (best) atomicMax(&G[i * L + cur], (unsigned long long)best);
-      cur = runs_bin_of(j, q, r);
-      end = (cur + 1) * q + min(cur + 1, r);
-      best = 0;
+  const int64_t step = blockDim.x;
+  for (int64_t j8 = j0 + threadIdx.x; j8 < j1; j8 += 8 * step) {
+    // eight independent loads in flight per thread
+    float v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int64_t j = j8 + u * step;
+      v[u] = j < j1 ? load_score<DT>(S, i * N + j, sg) : 0.0f;
     }
-    const uint64_t key = make_key(load_score<DT>(S, i * N + j, sg), (int32_t)j);
-    best = key > best ? key : best;
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int64_t j = j8 + u * step;
+      if (j < j1) {
+        if (j >= end) {
+          if (best) atomicMax(&G[i * L + cur], (unsigned long long)best);
+          cur = runs_bin_of(j, q, r);
+          end = (cur + 1) * q + min(cur + 1, r);
+          best = 0;
+        }
+        const uint64_t key = make_key(v[u], (int32_t)j);
+        best = key > best ? key : best;
+      }
+    }
   }
   if (best) atomicMax(&G[i * L + cur], (unsigned long long)best);
 }
@@ -125,7 +150,7 @@ cudaError_t launch_bin_max(const void* S, int dtype, int64_t M, int64_t N, int64
     else
       bin_max_mod_kernel<KNN_F32><<<grid, 256, 0, st>>>(S, N, L, kchunk, neg, G);
   } else {
-    const int64_t chunk = 256 * 16;
+    const int64_t chunk = 256 * 32;
     const int64_t bx = cdiv(N, chunk);
     if (bx > 0x7fffffffLL) return cudaErrorInvalidValue;
     dim3 grid((unsigned)bx, (unsigned)M);
