@@ -52,6 +52,24 @@ def parse():
     return ap.parse_args()
 
 
+def eq6_block(M, N, D, k1_ms, pk, bytes_moved):
+    """The paper's three-roof bound (Eq. 6) for K1 on this GPU: pi and beta
+    measured, gamma from unit counts x clock (ALU pipe), C from the kernel's
+    design: one compare per 16-score maximum (tcgen05.ld.red), plus the
+    searches of new bests, which depend on the data and are not counted."""
+    from paper_2206_14286_gb300 import roofline as RF
+    C = 1.0 / 16.0
+    r = RF.report(M, N, D, k1_ms / 1e3, pk["bf16_tflops"] * 1e12, pk["hbm_gbs"] * 1e9,
+                  RF.gb300_gamma("alu"), C, bytes_moved)
+    return {"C_design_alu_cops_per_score": C, "I_MEM_flop_per_byte": r["I_MEM"],
+            "I_COP_flop_per_cop": r["I_COP"],
+            "roofs_tflops": {k: v / 1e12 for k, v in r["roofs"].items()},
+            "binding": r["binding"], "fraction_of_attainable": r["fraction_of_attainable"],
+            "gamma_alu_tcops": RF.gb300_gamma("alu") / 1e12,
+            "cop_budget_per_score": RF.cop_budget(D, RF.gb300_gamma("alu"),
+                                                  pk["bf16_tflops"] * 1e12)}
+
+
 def job_rate(world, units_per_rank, local_ms, device=None):
     """Whole-job rate of independent replicas: every rank processed
     units_per_rank units in local_ms; the job took as long as the slowest
@@ -327,6 +345,7 @@ def main():
                        "k1_tcs_kernel (+ k1_tcs_tail for the N mod L ragged rows): fused BF16 "
                        "contraction + PartialReduce, j mod L bins"),
             "algorithmic": "2*M*N*D = %.4g FLOP per launch" % flops,
+            "eq6": eq6_block(M, N, D, k1_ms, pk, traffic or k1_bytes),
             "hbm_context": {"algorithmic_bytes": k1_bytes,
                             "achieved_gbs": k1_bytes / (k1_ms / 1e3) / 1e9,
                             "peak_gbs": pk["hbm_gbs"]}}

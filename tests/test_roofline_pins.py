@@ -58,3 +58,23 @@ def test_eq20_approaches_min_m_n():
 def test_alt_impl_speedup():
     assert G["alt_baseline_ms"] / G["alt_fused_ms"] == pytest.approx(G["alt_speedup"], abs=0.05)
     assert G["alt_N"] / G["alt_L"] == G["alt_bin_width"]
+
+
+def test_gb300_gamma_and_cop_budget():
+    """Unit counts x clock: 152 x 64 x 2.07e9 ALU-pipe COP/s; against the
+    measured BF16 peak the budget at D = 128 is under 3 COPs per score, so a
+    compare-and-select per score (2 ALU COPs) already reaches the tensor time."""
+    g_alu = RF.gb300_gamma("alu")
+    assert g_alu == pytest.approx(152 * 64 * 2.07e9)
+    assert RF.gb300_gamma("fma") == pytest.approx(2 * g_alu)
+    budget = RF.cop_budget(128, g_alu, 1938.1e12)
+    assert 2.5 < budget < 3.0
+
+
+def test_report_picks_the_binding_roof():
+    r = RF.report(1024, 10 ** 6, 128, 0.2e-3, 1938e12, 6686e9, RF.gb300_gamma(), 2.0,
+                  260e6)
+    assert r["binding"] == "tensor" and r["I_COP"] == pytest.approx(128.0)
+    assert r["measured"] == pytest.approx(2 * 1024 * 10 ** 6 * 128 / 0.2e-3)
+    r2 = RF.report(1024, 10 ** 6, 128, 0.2e-3, 1938e12, 6686e9, RF.gb300_gamma(), 4.0, 260e6)
+    assert r2["binding"] == "cop"
