@@ -251,7 +251,6 @@ def main():
         dist.barrier()
     torch.cuda.synchronize()
 
-    _lib.check(lib.knn_profile_enable(1))
     clocks = Clocks(local)
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
            for _ in range(args.steps)]
@@ -261,11 +260,17 @@ def main():
         b.record()
     torch.cuda.synchronize()
     clk = clocks.stop()
-    _lib.check(lib.knn_profile_enable(0))
     step_ms = [a.elapsed_time(b) for a, b in evs]
     total_ms = evs[0][0].elapsed_time(evs[-1][1])
     value, total_ms = job_rate(world, M * args.steps, total_ms, device="cuda")
 
+    # per-kernel times from the library's event profiler, in a separate pass
+    # (its events are not part of the timed steps above)
+    _lib.check(lib.knn_profile_enable(1))
+    for _ in range(min(args.steps, 20)):
+        step()
+    torch.cuda.synchronize()
+    _lib.check(lib.knn_profile_enable(0))
     prof = {}
     import ctypes
     for c, name in enumerate(["prep", "k1_partial_reduce", "k2_rescoring", "k3_rerank"]):
@@ -273,6 +278,29 @@ def main():
         n = ctypes.c_int64()
         _lib.check(lib.knn_profile_read(c, ctypes.byref(tot), ctypes.byref(n)))
         prof[name] = {"ms_avg": tot.value / max(1, n.value), "launches": n.value}
+    S.sync_status()
+
+    # the same step replayed from a CUDA graph (knn_search allocates nothing,
+    # so a caller can capture it once and replay it)
+    graph = None
+    try:
+        gr = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(gr):
+            step()
+        for _ in range(3):
+            gr.replay()
+        torch.cuda.synchronize()
+        ga, gb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ga.record()
+        for _ in range(args.steps):
+            gr.replay()
+        gb.record()
+        torch.cuda.synchronize()
+        g_ms = ga.elapsed_time(gb) / args.steps
+        graph = {"value": world * M / (g_ms / 1e3), "unit": "queries/s", "ms_per_step": g_ms}
+        del gr
+    except RuntimeError as e:  # capture refused: report why
+        graph = {"unavailable": str(e)[:200]}
     S.sync_status()
 
     # recall@10 against the exact FP32 search on the same data
@@ -380,6 +408,7 @@ def main():
                 "fp32_path": {"value": world * M / (ms32 / 1e3), "unit": "queries/s",
                               "ms_per_step": ms32, "recall_at_10": recall32},
                 "kernels": prof, "roofline": roof, "e2e": e2e,
+                "graph_replay": graph,
                 "serving": serving,
                 "unfused_baseline": unfused,
                 "gpu_launches": launches_per_step * args.steps, "clocks": clk,
