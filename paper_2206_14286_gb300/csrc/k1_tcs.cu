@@ -14,10 +14,13 @@
 // is about one compare per 16 scores instead of a compare (and a key pack)
 // per score, which keeps the CUDA-core work well below the tensor-core time.
 //
-// One CTA (640 threads, one per SM) owns 256 queries (two M = 128 halves,
-// A operand resident in shared memory) and a contiguous run of steps:
-//   warp 0      : TMA producer (query tile once; per step and 128-byte K block
-//                 one 16 x 16-row box into a 32 KB stage of an S-stage ring).
+// One CTA (640 threads, one per SM) owns a contiguous run of steps and takes
+// kq query tiles of 256 (two M = 128 halves, A operand resident in shared
+// memory) in turn over it, one segment each; kq > 1 only when the tiles do
+// not spread evenly over the SMs (the host picks kq and the runs):
+//   warp 0      : TMA producer (the query tile once per segment; per step and
+//                 128-byte K block one 16 x 16-row box into a 32 KB stage of
+//                 an S-stage ring).
 //   warp 1      : TMEM allocation (512 columns: one 128 x 256 FP32 accumulator
 //                 per query half) and tcgen05.mma issue. Half 0 of a step is
 //                 computed and handed to its epilogue while half 1 is
@@ -72,7 +75,9 @@ struct TcsArgs {
   int64_t N, M, L, T;              // T = floor(N / L) full grid rows
   int64_t ntg, nbg;                // grid-row groups of 16, bin groups of 16 (j mod L)
   int64_t bq, br;                  // contiguous bins: q = N / L, r = N mod L
-  int64_t steps_per_cta, steps_per_q, nqt;
+  int64_t steps_per_q, nqt;        // steps over the whole database; query tiles
+  int64_t parts, steps_per_part;   // the database steps split into `parts` ranges
+  int64_t kq, groups;              // query tiles one CTA takes in turn; tile groups
   int pitch;                       // row length in elements (multiple of 16)
   int nkb, nksteps, stages;
   uint32_t stage_bytes;            // one K block of a step (+ of the queries when streamed)
@@ -161,15 +166,24 @@ k1_tcs_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
   const uint32_t b_xe = smem_u32(bars + 2 * S + 4 + kExtSlotsS);
   const uint32_t b_q = smem_u32(bars + 2 * S + 4 + 2 * kExtSlotsS);
   const uint32_t b_done = smem_u32(bars + 2 * S + 5 + 2 * kExtSlotsS);
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * S + 6 + 2 * kExtSlotsS);
+  const uint32_t b_qe = smem_u32(bars + 2 * S + 6 + 2 * kExtSlotsS);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * S + 7 + 2 * kExtSlotsS);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t qtile = blockIdx.x % a.nqt;
-  const int64_t part = blockIdx.x / a.nqt;
-  const int64_t s_begin = part * a.steps_per_cta;
-  const int64_t s_end = min(a.steps_per_q, s_begin + a.steps_per_cta);
+  // CTA = (part, group): the steps [s_begin, s_end) of the database for the
+  // query tiles q0 .. q0 + nseg - 1, one after the other (a segment each).
+  // The CTAs of one part walk the same rows at the same time, so the rows
+  // they share meet in L2; their block indices are adjacent, which keeps
+  // them on neighbouring SMs (the same die). Step i of the CTA is step
+  // i mod ns of segment i / ns; barrier phases count i across segments.
+  const int64_t part = blockIdx.x / a.groups;
+  const int64_t q0 = (blockIdx.x % a.groups) * a.kq;
+  const int nseg = (int)max((int64_t)0, min(a.kq, a.nqt - q0));
+  const int64_t s_begin = part * a.steps_per_part;
+  const int64_t s_end = min(a.steps_per_q, s_begin + a.steps_per_part);
   const int ns = (int)max((int64_t)0, s_end - s_begin);
+  const int nt = nseg * ns;  // steps of this CTA
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < S; ++s) {
@@ -186,6 +200,7 @@ k1_tcs_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
     }
     mbar_init(b_q, 1);
     mbar_init(b_done, 1);
+    mbar_init(b_qe, 1);
     *abort_flag = 0;
     fence_barrier_init();
   }
@@ -212,6 +227,16 @@ k1_tcs_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
   if (warp < 4) asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(kCtrlRegsS));
   if (warp == 0) {
     // -------------------------------------------------------------- producer
+    int s = 0, issued = 0;
+    uint32_t ph = 0;
+    bool prun = true;
+    for (int sg = 0; sg < nseg && prun; ++sg) {
+    const int64_t qtile = q0 + sg;
+    // the segment's query tile (phase sg of b_q); from the second segment on
+    // only after the MMAs of the previous one are done with the old tile
+    if (MODE != kKLoopQ && sg > 0 &&
+        !mbar_wait_sleep(b_qe, (uint32_t)((sg - 1) & 1), abort_flag, 64))
+      break;
     if (lane == 0) {
       if (MODE == kKLoopQ) {
         mbar_arrive(b_q);  // the queries come with every stage
@@ -223,12 +248,14 @@ k1_tcs_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
       }
     }
     __syncwarp();
-    int s = 0, kb = 0, issued = 0;
-    uint32_t ph = 0;
+    int kb = 0;
     int64_t bg = s_begin / a.ntg, tg = s_begin % a.ntg;
     const int total = ns * NKB;
     for (int g = 0; g < total; ++g) {
-      if (g >= S && !mbar_wait_sleep(b_empty + 8 * s, ph ^ 1u, abort_flag, 64)) break;
+      if (issued >= S && !mbar_wait_sleep(b_empty + 8 * s, ph ^ 1u, abort_flag, 64)) {
+        prun = false;
+        break;
+      }
       if (lane == 0) {
         mbar_expect_tx(b_full + 8 * s, a.stage_bytes);
         uint32_t dst = smem_u32(sB + (size_t)s * a.stage_bytes);
@@ -250,7 +277,7 @@ k1_tcs_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
         }
       }
       __syncwarp();
-      issued = g + 1;
+      ++issued;
       if (++kb == NKB) {
         kb = 0;
         if (++tg == a.ntg) {
@@ -263,6 +290,7 @@ k1_tcs_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
         ph ^= 1u;
       }
     }
+    }
     for (int k = 0; k < S && k < issued; ++k) {
       if (--s < 0) {
         s = S - 1;
@@ -270,7 +298,7 @@ k1_tcs_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
       }
       mbar_wait_sleep(b_full + 8 * s, ph, abort_flag, 64);
     }
-    mbar_wait_sleep(b_q, 0, abort_flag, 64);
+    if (nseg > 0) mbar_wait_sleep(b_q, (uint32_t)((nseg - 1) & 1), abort_flag, 64);
     return;
   }
   if (warp == 1) {
@@ -280,8 +308,10 @@ k1_tcs_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
     // half: every wait of a step (its stages, its L2 block, the accumulator
     // being free) comes before the unrolled run of MMAs it guards, and the
     // commits come after.
+    // b_q phase sg: the query tile of segment sg has landed; a commit to b_qe
+    // after a segment's last MMAs frees the tile for the next one
     if constexpr (MODE == kFused) {
-    if (mbar_wait(b_q, 0, abort_flag)) {
+    {
       const uint64_t a_desc = smem_desc_sw128(smem_u32(sA));
       const uint64_t b_desc = smem_desc_sw128(smem_u32(sB));
       const uint64_t ax_desc = smem_desc_noswz(smem_u32(sAext), 128, 256);
@@ -289,7 +319,10 @@ k1_tcs_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
       int s0 = 0;           // stage of K block 0 of the current step
       uint32_t ph0 = 0;
       bool run = true;
-      for (int i = 0; i < ns && run; ++i) {
+      for (int sg = 0; sg < nseg && run; ++sg) {
+      if (!mbar_wait(b_q, (uint32_t)(sg & 1), abort_flag)) break;
+      for (int li = 0; li < ns && run; ++li) {
+        const int i = sg * ns + li;
         const int e = i & 1;
         // the stages of this step (NKB consecutive ring slots)
         int sk[(NKS + 3) / 4];
@@ -309,7 +342,10 @@ k1_tcs_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
           ph0 = ph;
         }
         if (!run) break;
-        if (a.ext && !mbar_wait(b_xf + 8 * e, (uint32_t)((i >> 1) & 1), abort_flag)) break;
+        if (a.ext && !mbar_wait(b_xf + 8 * e, (uint32_t)((i >> 1) & 1), abort_flag)) {
+          run = false;
+          break;
+        }
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
           if (i >= 1 && !mbar_wait(b_acce + 8 * h, (uint32_t)((i & 1) ^ 1), abort_flag)) {
@@ -341,22 +377,31 @@ k1_tcs_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
           __syncwarp();
         }
       }
+      if (!run) break;
+      if (lane == 0) tc_commit(b_qe);
+      __syncwarp();
+      }
     }
     }
     if constexpr (MODE != kFused) {
-    if (mbar_wait(b_q, 0, abort_flag)) {
+    {
       const uint64_t a_desc = smem_desc_sw128(smem_u32(sA));
       const uint64_t ax_desc = smem_desc_noswz(smem_u32(sAext), 128, 256);
       const uint64_t bx_desc = smem_desc_noswz(smem_u32(sBext), 128, 256);
       int s = 0;
       uint32_t ph = 0;
       bool run = true;
-      for (int i = 0; i < ns && run; ++i) {
+      for (int sg = 0; sg < nseg && run; ++sg) {
+      if (!mbar_wait(b_q, (uint32_t)(sg & 1), abort_flag)) break;
+      for (int li = 0; li < ns && run; ++li) {
+        const int i = sg * ns + li;
         const int e = i & 1;
         // both accumulators are written from the first K block on
         if (i >= 1 && (!mbar_wait(b_acce, (uint32_t)((i & 1) ^ 1), abort_flag) ||
-                       !mbar_wait(b_acce + 8, (uint32_t)((i & 1) ^ 1), abort_flag)))
+                       !mbar_wait(b_acce + 8, (uint32_t)((i & 1) ^ 1), abort_flag))) {
+          run = false;
           break;
+        }
         for (int kb = 0; kb < NKB; ++kb) {
           if (!mbar_wait(b_full + 8 * s, ph, abort_flag)) {
             run = false;
@@ -391,7 +436,10 @@ k1_tcs_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
         }
         if (!run) break;
         if (a.ext) {
-          if (!mbar_wait(b_xf + 8 * e, (uint32_t)((i >> 1) & 1), abort_flag)) break;
+          if (!mbar_wait(b_xf + 8 * e, (uint32_t)((i >> 1) & 1), abort_flag)) {
+            run = false;
+            break;
+          }
           tc_fence_after();
         }
         if (lane == 0) {
@@ -406,6 +454,10 @@ k1_tcs_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
           tc_commit(b_accf + 8);
         }
         __syncwarp();
+      }
+      if (!run) break;
+      if (lane == 0) tc_commit(b_qe);
+      __syncwarp();
       }
     }
     }
@@ -442,24 +494,30 @@ k1_tcs_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
           h[k] = (live && b < a.L && t < a.T) ? a.hnorm[t * a.L + b] : 0.0f;
         }
       }
-      ++rstep;
+      if (++rstep == s_end) rstep = s_begin;  // the next segment repeats the steps
     };
     int64_t bgn = bg, tgn = tg;
+    int lsn = 0;  // step within the segment of (bgn, tgn)
     auto advance = [&](int64_t& b, int64_t& t) {
       if (++t == a.ntg) {
         t = 0;
         ++b;
       }
+      if (++lsn == ns) {
+        lsn = 0;
+        b = s_begin / a.ntg;
+        t = s_begin % a.ntg;
+      }
     };
-    load(bgn, tgn, ns > 0, hb[0]);
+    load(bgn, tgn, nt > 0, hb[0]);
     advance(bgn, tgn);
     bool run = true;
-    for (int i0 = 0; i0 < ns && run; i0 += 2) {
+    for (int i0 = 0; i0 < nt && run; i0 += 2) {
 #pragma unroll
       for (int cur = 0; cur < 2; ++cur) {
         const int i = i0 + cur;
-        if (i >= ns) break;
-        load(bgn, tgn, i + 1 < ns, hb[cur ^ 1]);
+        if (i >= nt) break;
+        load(bgn, tgn, i + 1 < nt, hb[cur ^ 1]);
         advance(bgn, tgn);
         const int e = i & 1;
         int ok = 1;
@@ -500,9 +558,14 @@ k1_tcs_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
   const int egrp = (warp - 4) >> 2;  // 0..3
   const int h = egrp >> 1;           // query half = accumulator
   const int cq = egrp & 1;           // bins cq*8 .. cq*8+7 of each step
-  const int64_t qi = qtile * kQT + h * kQH + quad * 32 + lane;
-  const bool q_ok = qi < a.M;
-  unsigned long long* gq = a.G + (q_ok ? qi : 0) * a.L;
+  // this thread's query in the current segment
+  bool q_ok = false;
+  unsigned long long* gq = a.G;
+  auto set_query = [&](int sg) {
+    const int64_t qi = (q0 + sg) * kQT + h * kQH + quad * 32 + lane;
+    q_ok = qi < a.M;
+    gq = a.G + (q_ok ? qi : 0) * a.L;
+  };
   const uint32_t tbase =
       tmem_base + ((uint32_t)(quad * 32) << 16) + (uint32_t)(h * kCols + cq * 128);
   if constexpr (BM == kBinsRun) {
@@ -511,18 +574,28 @@ k1_tcs_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
     // (the same for every lane: bins depend on rows only) with its best score
     // and row, and merges it into G when the rows leave the bin.
     const int64_t first = min((s_begin * kCols + cq * 128), a.N - 1);
-    int64_t cur = run_bin_of(first, a.bq, a.br);
-    int64_t seg_end = run_bin_end(cur, a.bq, a.br);
+    int64_t cur = 0, seg_end = 0, brow = -1;
     float bv = __uint_as_float(kNegInfBits);
-    int64_t brow = -1;
     auto flush_run = [&]() {
       if (q_ok && brow >= 0)
         atomicMax(&gq[cur], (unsigned long long)make_key(bv, (int32_t)brow));
     };
-    for (int i = 0; i < ns; ++i) {
-      if (!mbar_wait_sleep(b_accf + 8 * h, (uint32_t)(i & 1), abort_flag, 32)) break;
+    bool erun = true;
+    for (int sg = 0; sg < nseg && erun; ++sg) {
+    if (sg > 0) flush_run();
+    set_query(sg);
+    cur = run_bin_of(first, a.bq, a.br);
+    seg_end = run_bin_end(cur, a.bq, a.br);
+    bv = __uint_as_float(kNegInfBits);
+    brow = -1;
+    for (int li = 0; li < ns; ++li) {
+      const int i = sg * ns + li;
+      if (!mbar_wait_sleep(b_accf + 8 * h, (uint32_t)(i & 1), abort_flag, 32)) {
+        erun = false;
+        break;
+      }
       tc_fence_after();
-      const int64_t p0 = (s_begin + i) * kCols + cq * 128;
+      const int64_t p0 = (s_begin + li) * kCols + cq * 128;
 #pragma unroll
       for (int half64 = 0; half64 < 2; ++half64) {
         float r[4][16], m[4];
@@ -569,12 +642,13 @@ k1_tcs_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
         }
       }
     }
+    }
     tc_fence_before();
     asm volatile("bar.arrive 1, %0;" ::"n"(32 + 512) : "memory");
     flush_run();
     return;
   }
-  int64_t bg = s_begin / a.ntg, tg = s_begin % a.ntg;
+  int64_t bg = 0, tg = 0;
   float best[8];
   int32_t bt[8];
 #pragma unroll
@@ -605,8 +679,18 @@ k1_tcs_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
       }
     }
   };
-  for (int i = 0; i < ns; ++i) {
-    if (!mbar_wait_sleep(b_accf + 8 * h, (uint32_t)(i & 1), abort_flag, 32)) break;
+  bool erun = true;
+  for (int sg = 0; sg < nseg && erun; ++sg) {
+  if (sg > 0) flush(bg);  // the previous segment's last group of bins
+  set_query(sg);
+  bg = s_begin / a.ntg;
+  tg = s_begin % a.ntg;
+  for (int li = 0; li < ns; ++li) {
+    const int i = sg * ns + li;
+    if (!mbar_wait_sleep(b_accf + 8 * h, (uint32_t)(i & 1), abort_flag, 32)) {
+      erun = false;
+      break;
+    }
     tc_fence_after();
     const int32_t t0 = (int32_t)(tg * kRowsBin);
     const int64_t bw = bg * kBinsStep + cq * 8;  // first bin of this warpgroup
@@ -649,6 +733,7 @@ k1_tcs_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
       tg = 0;
       ++bg;
     }
+  }
   }
   tc_fence_before();
   asm volatile("bar.arrive 1, %0;" ::"n"(32 + 512) : "memory");
@@ -750,6 +835,33 @@ bool make_map_grid(CUtensorMap* m, const void* base, int64_t pitch, int64_t L, i
   return enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(base), dims, strides, box,
              estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// One CTA per SM at most: the database steps split into `parts` ranges and
+// the query tiles into groups of kq; CTA (group, part) runs the tiles of its
+// group one after the other over its range. Picks the kq (and the parts it
+// allows) with the least work per CTA, counting a query-tile reload as one
+// step; ties go to the smaller kq (fewer reloads, fewer database passes).
+void tcs_schedule(int64_t nqt, int64_t steps, int64_t sms, int64_t* kq_out, int64_t* parts_out,
+                  int64_t* spp_out, int64_t* groups_out) {
+  if (sms < 1) sms = 1;
+  const int64_t kq_min = cdiv(nqt, sms);
+  int64_t best = -1;
+  for (int64_t kq = kq_min; kq <= min(nqt, kq_min + 16); ++kq) {
+    const int64_t groups = cdiv(nqt, kq);
+    if (groups > sms) continue;
+    int64_t parts = min(sms / groups, steps);
+    const int64_t spp = cdiv(steps, parts);
+    parts = cdiv(steps, spp);
+    const int64_t work = kq * (spp + 1);
+    if (best < 0 || work < best) {
+      best = work;
+      *kq_out = kq;
+      *parts_out = parts;
+      *spp_out = spp;
+      *groups_out = groups;
+    }
+  }
 }
 
 struct TcsShape {
@@ -870,11 +982,9 @@ cudaError_t launch_k1_tcs(int64_t N, int64_t M, int64_t L, int D, int metric, in
   // a step: 16 bins x 16 grid rows (j mod L), or 256 consecutive rows
   a.steps_per_q = runs ? cdiv(N, kCols) : a.ntg * a.nbg;
   const int64_t sms = device_sm_count();
-  int64_t cpq = a.nqt >= sms ? 1 : sms / a.nqt;
-  if (cpq > a.steps_per_q) cpq = a.steps_per_q;
-  if (cpq < 1) cpq = 1;
-  a.steps_per_cta = cdiv(a.steps_per_q, cpq);
-  cpq = cdiv(a.steps_per_q, a.steps_per_cta);
+  tcs_schedule(a.nqt, a.steps_per_q, sms, &a.kq, &a.parts, &a.steps_per_part, &a.groups);
+  // step counters of a CTA are 32-bit
+  if (a.kq * a.steps_per_part * sh.nkb >= ((int64_t)1 << 31)) return cudaErrorNotSupported;
   a.pitch = pitch;
   a.nkb = sh.nkb;
   a.nksteps = sh.nksteps;
@@ -892,7 +1002,7 @@ cudaError_t launch_k1_tcs(int64_t N, int64_t M, int64_t L, int D, int metric, in
                            : make_map_grid(&mx, X, pitch, L, a.T);
   if (!mapped) return cudaErrorInvalidValue;
   if (!make_map_s(&mq, Qp, pitch, M, pitch, kQT)) return cudaErrorInvalidValue;
-  const int64_t blocks = a.nqt * cpq;
+  const int64_t blocks = a.groups * a.parts;
   if (blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
   cudaError_t e = runs ? launch_tcs_mode<kBinsRun>(sh, mx, mq, a, blocks, st)
                        : launch_tcs_mode<kBinsMod>(sh, mx, mq, a, blocks, st);

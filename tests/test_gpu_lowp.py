@@ -268,3 +268,32 @@ def test_exact_search_lowp(dtype, metric):
     tol = PT.REL_LOWP * PT.query_scale(Qs, Xs, metric)
     dec = PT.decided_mask(S_lp, 9000, 7, S_f, cand, 7, tol)
     PT.check_search(gv, gi, ov, oi, S_lp, S_f, 9000, metric, tol, dec)
+
+
+@pytest.mark.parametrize("bins", ["mod", "contiguous"])
+@pytest.mark.parametrize("metric", ["ip", "l2"])
+def test_partial_reduce_many_query_tiles(bins, metric):
+    """More 256-query tiles than SMs: a CTA takes several tiles in turn over
+    the same database rows (query tile reloaded between them)."""
+    N, M, D = 600, 39500, 32
+    X, Q = inputs(N, M, D, seed=5)
+    Xs, _ = stored(X, metric, "bf16")
+    Qs, _ = stored(Q, metric, "bf16")
+    d = db(X, metric, "bf16")
+    Sm = PT.score_matrix(Qs, Xs, om(metric))
+    scale = PT.query_scale(Qs, Xs, metric)
+    tight = 3e-5 * scale[:, None] + 2.0 ** -20 * np.abs(Sm).max(1)[:, None]
+    for L in (7, 100):
+        V, A = d.partial_reduce(dev(Q), L, bins=bins)
+        V, A = host(V).astype(np.float64), host(A)
+        Vo, Ao = oracle.partial_reduce(Qs, Xs, L, om(metric), bins=bins)
+        if metric == "l2":
+            Vo = (Vo + (Qs ** 2).sum(1)[:, None]) / 2.0
+        best, second = PT.bin_best_second(Sm, L, bins=bins)
+        decided = (best - second) > 2 * tight
+        np.testing.assert_array_equal(A[decided], Ao[decided])
+        own = Sm[np.arange(M)[:, None], A]
+        if metric == "l2":
+            own = (own + (Qs ** 2).sum(1)[:, None]) / 2.0
+        assert np.all(np.abs(V - own) <= tight), L
+        assert decided.mean() > 0.9, L
