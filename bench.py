@@ -237,8 +237,6 @@ def main():
     idx = torch.empty((M, K), dtype=torch.int32, device="cuda")
 
     bins = args.bins
-    # prep, K1 (plus the ragged-row kernel when N mod L != 0), K2, K3
-    launches_per_step = 4 + (1 if bins == "mod" and N % L else 0)
 
     def step():
         db.search(Qd, K, L=L, rerank=rerank, out=(val, idx), bins=bins)
@@ -278,6 +276,13 @@ def main():
         n = ctypes.c_int64()
         _lib.check(lib.knn_profile_read(c, ctypes.byref(tot), ctypes.byref(n)))
         prof[name] = {"ms_avg": tot.value / max(1, n.value), "launches": n.value}
+    # prep, K1 (plus the ragged-row kernel when N mod L != 0), then K2 and K3,
+    # or one launch of both when the library fuses them (no K3 launches)
+    fused23 = prof["k3_rerank"]["launches"] == 0
+    if fused23:
+        prof["k2_k3_rescoring_rerank_fused"] = prof.pop("k2_rescoring")
+        prof.pop("k3_rerank")
+    launches_per_step = (3 if fused23 else 4) + (1 if bins == "mod" and N % L else 0)
     S.sync_status()
 
     # the same step replayed from a CUDA graph (knn_search allocates nothing,

@@ -362,6 +362,13 @@ knn_status search_impl(const SearchArgs& a, float* out_val, int32_t* out_idx, vo
   }
   if (e == cudaErrorNotSupported) return KNN_EUNSUPPORTED;
   if (e != cudaSuccess) return cuda_status(e);
+  if (k64 && k23_supported(a.M, s.plan.L, s.Kp, a.K, a.D, qf32, q_stride, a.db_f32)) {
+    // ExactRescoring and the FP32 re-rank in one launch (profiled as K2)
+    ProfScope ps(2, st);
+    e = launch_k23(reinterpret_cast<const uint64_t*>(parts.v), a.M, s.plan.L, s.Kp, a.K, a.D,
+                   a.metric, qf32, q_stride, a.db_f32, a.N, out_val, out_idx, st);
+    return cuda_status(e);
+  }
   uint64_t* cand = reinterpret_cast<uint64_t*>(ws + s.off_cand);
   {
     ProfScope ps(2, st);

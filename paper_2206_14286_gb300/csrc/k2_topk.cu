@@ -243,6 +243,147 @@ cudaError_t run_k2(const Src& src, int64_t M, int64_t nelem, int Kp, const uint6
   kern<<<(unsigned)M, threads, smem, st>>>(src, nelem, Kp, CH, CAP, run_in, out);
   return cudaGetLastError();
 }
+
+// ExactRescoring and the FP32 re-rank in one CTA of 4 warps per query, for
+// the merged 64-bit keys of K1 (L <= 1024, Kp <= 32, K <= 32, 16-byte
+// aligned FP32 rows with D % 4 == 0). Warp 0 takes the best Kp of the L keys:
+// each lane sorts its KPL keys, then every round the warp's maximum key
+// comes from two 32-bit max-reductions (high word, then the low word among
+// the lanes that hold the high maximum) and the lane that holds it shifts
+// its list. The 4 warps then score the Kp candidates against the FP32 rows
+// (a lane reads 4 consecutive elements; a warp has up to 8 rows in flight),
+// and warp 0 sorts the Kp exact keys across its lanes and writes the best K.
+// Same results as the two-kernel path: the candidates are the Kp largest
+// keys, and the re-rank scores and orders them the same way.
+template <int METRIC, int KPL>
+__global__ void __launch_bounds__(128)
+k23_kernel(const uint64_t* __restrict__ G, int64_t L, int Kp, int K, int D,
+           const float* __restrict__ qf32, int64_t q_stride, const float* __restrict__ xf32,
+           int64_t N, float* __restrict__ out_val, int32_t* __restrict__ out_idx) {
+  constexpr int kWarps = 4, kPerWarp = 8;  // 4 x 8 = 32 candidates at most
+  __shared__ uint64_t s_cand[32];
+  __shared__ uint64_t s_key[32];
+  const int64_t i = blockIdx.x;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (warp == 0) {
+    uint64_t k[KPL];
+#pragma unroll
+    for (int r = 0; r < KPL; ++r) {
+      const int64_t b = lane + 32 * r;
+      k[r] = b < L ? G[i * L + b] : 0;
+    }
+    reg_sort_desc<KPL>(k);
+    uint64_t mine = 0;
+    for (int r = 0; r < Kp; ++r) {
+      const uint32_t hi = (uint32_t)(k[0] >> 32);
+      const uint32_t mh = __reduce_max_sync(0xffffffffu, hi);
+      const uint32_t ml = __reduce_max_sync(0xffffffffu, hi == mh ? (uint32_t)k[0] : 0u);
+      const uint64_t m = ((uint64_t)mh << 32) | ml;
+      if (lane == r) mine = m;
+      // keys are unique (distinct rows), so one lane pops
+      if (m != 0 && k[0] == m) {
+#pragma unroll
+        for (int t = 0; t + 1 < KPL; ++t) k[t] = k[t + 1];
+        k[KPL - 1] = 0;
+      }
+    }
+    s_cand[lane] = mine;
+  }
+  __syncthreads();
+  const float* q = qf32 + i * q_stride;
+  {
+    int32_t js[kPerWarp];
+    float acc[kPerWarp];
+#pragma unroll
+    for (int u = 0; u < kPerWarp; ++u) {
+      const int c = warp + kWarps * u;
+      const uint64_t key = c < Kp ? s_cand[c] : 0;
+      const int32_t j = key ? key_index(key) : -1;
+      js[u] = (j >= 0 && j < N) ? j : -1;
+      acc[u] = 0.0f;
+    }
+    for (int d0 = 0; d0 < D; d0 += 128) {
+      const int d = d0 + lane * 4;
+      const bool in = d < D;
+      const float4 qv = in ? *reinterpret_cast<const float4*>(q + d) : make_float4(0, 0, 0, 0);
+      float4 xv[kPerWarp];
+#pragma unroll
+      for (int u = 0; u < kPerWarp; ++u)
+        xv[u] = (in && js[u] >= 0)
+                    ? __ldg(reinterpret_cast<const float4*>(xf32 + (int64_t)js[u] * D + d))
+                    : make_float4(0, 0, 0, 0);
+#pragma unroll
+      for (int u = 0; u < kPerWarp; ++u) {
+        if (METRIC == KNN_L2) {
+          // elements past D contribute 0: both sides are zero there
+          const float t0 = qv.x - xv[u].x, t1 = qv.y - xv[u].y, t2 = qv.z - xv[u].z,
+                      t3 = qv.w - xv[u].w;
+          acc[u] = fmaf(t0, t0, acc[u]);
+          acc[u] = fmaf(t1, t1, acc[u]);
+          acc[u] = fmaf(t2, t2, acc[u]);
+          acc[u] = fmaf(t3, t3, acc[u]);
+        } else {
+          acc[u] = fmaf(qv.x, xv[u].x, acc[u]);
+          acc[u] = fmaf(qv.y, xv[u].y, acc[u]);
+          acc[u] = fmaf(qv.z, xv[u].z, acc[u]);
+          acc[u] = fmaf(qv.w, xv[u].w, acc[u]);
+        }
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < kPerWarp; ++u) {
+      float v = acc[u];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      const int c = warp + kWarps * u;
+      if (lane == 0 && c < 32)
+        s_key[c] = js[u] >= 0 ? make_key(METRIC == KNN_L2 ? -v : v, js[u]) : 0;
+    }
+  }
+  __syncthreads();
+  if (warp != 0) return;
+  uint64_t mine = s_key[lane];
+#pragma unroll
+  for (int k2 = 2; k2 <= 32; k2 <<= 1) {
+#pragma unroll
+    for (int jj = k2 >> 1; jj > 0; jj >>= 1) {
+      const uint64_t other = shfl_xor_u64(mine, jj);
+      const bool up = (lane & k2) == 0, lower = (lane & jj) == 0;
+      const bool keep_max = (up == lower);
+      mine = keep_max ? (other > mine ? other : mine) : (other < mine ? other : mine);
+    }
+  }
+  if (lane < K) {
+    const float sc = key_score(mine);
+    out_idx[i * K + lane] = mine ? key_index(mine) : -1;
+    out_val[i * K + lane] = mine ? (METRIC == KNN_L2 ? -sc : sc) : __int_as_float(0x7fc00000);
+  }
+}
+
+template <int METRIC>
+cudaError_t run_k23(const uint64_t* G, int64_t M, int64_t L, int Kp, int K, int D,
+                    const float* qf32, int64_t q_stride, const float* xf32, int64_t N,
+                    float* out_val, int32_t* out_idx, cudaStream_t st) {
+  const int kpl = next_pow2((int)cdiv(L, 32));
+  const unsigned blocks = (unsigned)M;
+#define K23_CASE(P)                                                                          \
+  case P:                                                                                    \
+    k23_kernel<METRIC, P><<<blocks, 128, 0, st>>>(G, L, Kp, K, D, qf32, q_stride, xf32, N,  \
+                                                  out_val, out_idx);                         \
+    break;
+  switch (kpl) {
+    K23_CASE(1)
+    K23_CASE(2)
+    K23_CASE(4)
+    K23_CASE(8)
+    K23_CASE(16)
+    K23_CASE(32)
+    default: return cudaErrorNotSupported;
+  }
+#undef K23_CASE
+  return cudaGetLastError();
+}
+
 }  // namespace
 
 cudaError_t launch_merge_bins(const K1Plan& p, Partials parts, float* out_v, int32_t* out_a,
@@ -298,6 +439,25 @@ cudaError_t launch_k2(const K1Plan& p, Partials parts, int Kp, const uint64_t* r
                  p.tiles_per_split, parts.index_offset, p.g, p.code_bits};
   return warp ? run_k2_warp(s, p.M, p.L, Kp, out_keys, st)
               : run_k2(s, p.M, p.L, Kp, run_in, out_keys, st);
+}
+
+bool k23_supported(int64_t M, int64_t L, int Kp, int K, int D, const float* qf32,
+                   int64_t q_stride, const float* xf32) {
+  return M > 0 && M <= 0x7fffffffLL && L >= 1 && L <= 1024 && Kp >= 1 && Kp <= 32 &&
+         K >= 1 && K <= 32 && xf32 && D % 4 == 0 && q_stride % 4 == 0 &&
+         (reinterpret_cast<uintptr_t>(xf32) & 15) == 0 &&
+         (reinterpret_cast<uintptr_t>(qf32) & 15) == 0;
+}
+
+cudaError_t launch_k23(const uint64_t* G, int64_t M, int64_t L, int Kp, int K, int D, int metric,
+                       const float* qf32, int64_t q_stride, const float* xf32, int64_t N,
+                       float* out_val, int32_t* out_idx, cudaStream_t st) {
+  if (M <= 0) return cudaSuccess;
+  if (!k23_supported(M, L, Kp, K, D, qf32, q_stride, xf32)) return cudaErrorNotSupported;
+  return metric == KNN_L2 ? run_k23<KNN_L2>(G, M, L, Kp, K, D, qf32, q_stride, xf32, N, out_val,
+                                            out_idx, st)
+                          : run_k23<KNN_IP>(G, M, L, Kp, K, D, qf32, q_stride, xf32, N, out_val,
+                                            out_idx, st);
 }
 
 }  // namespace tpuknn

@@ -90,6 +90,17 @@ cudaError_t launch_merge_bins(const K1Plan& p, Partials parts, float* out_v, int
 
 // K3: score the Kp candidates of each query in FP32 and keep the best K.
 // Rows come from xf32 (N x D) when given, else from the stored rows.
+// ExactRescoring and the FP32 re-rank fused (one CTA of 4 warps per query)
+// for K1's merged [M][L] keys; the same results as launch_k2 followed by
+// launch_k3. Supported when k23_supported(...) holds (L <= 1024, Kp <= 32,
+// K <= 32, 16-byte aligned FP32 rows and queries with D % 4 == 0);
+// otherwise returns cudaErrorNotSupported.
+bool k23_supported(int64_t M, int64_t L, int Kp, int K, int D, const float* qf32,
+                   int64_t q_stride, const float* xf32);
+cudaError_t launch_k23(const uint64_t* G, int64_t M, int64_t L, int Kp, int K, int D, int metric,
+                       const float* qf32, int64_t q_stride, const float* xf32, int64_t N,
+                       float* out_val, int32_t* out_idx, cudaStream_t st);
+
 cudaError_t launch_k3(int64_t M, int D, int metric, const uint64_t* cand, int Kp, int K,
                       const float* qf32, int64_t q_stride, const float* xf32, const void* xlp,
                       int dtype, int pitch, const float* xscale, int64_t N, float* out_val,
