@@ -8,6 +8,37 @@
 
 namespace tpuknn {
 
+// ---------------------------------------------------------------------------
+// Programmatic dependent launch inside one search call. A kernel launched
+// with launch_pdl may start (and run its prologue) before the previous kernel
+// of the stream has finished; it calls pdl_wait() before it touches global
+// memory that kernel writes. pdl_wait() returns once the previous grid has
+// completed and its writes are visible (at once for a plain launch). A
+// kernel calls pdl_trigger() in every CTA to let the next one launch early;
+// the next kernel then launches only after every CTA of this one has
+// started, so its CTAs never hold back this kernel's.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void pdl_trigger() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                       cudaStream_t st, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
 constexpr int kMaxK = 4096;       // largest K (and K') a search accepts
 constexpr int kMaxD = 4096;       // largest row length
 constexpr uint32_t kNegInfBits = 0xff800000u;

@@ -223,6 +223,10 @@ k1_tcs_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem_base = *tmem_slot;
+  // the prologue above touches no global memory; the queries and the zeroed
+  // key array come from the preceding kernel
+  pdl_wait();
+  pdl_trigger();
 
   if (warp < 4) asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(kCtrlRegsS));
   if (warp == 0) {
@@ -751,6 +755,11 @@ k1_tcs_tail(const __nv_bfloat16* __restrict__ X, const __nv_bfloat16* __restrict
             int pitch, int metric, unsigned long long* G) {
   extern __shared__ uint4 tail_smem[];  // kTailRows rows of `pitch` elements
   __nv_bfloat16* rows = reinterpret_cast<__nv_bfloat16*>(tail_smem);
+  // Launched behind the contraction, which has already waited for the
+  // queries and the zeroed keys: this kernel's atomics merge with the
+  // contraction's in any order. It finishes only after the contraction has
+  // (the pdl_wait at the end), so the kernel after it sees both.
+  pdl_trigger();
   const int64_t r = N - T * L;
   const int64_t b0 = (int64_t)blockIdx.x * kTailRows;
   const int nr = (int)min((int64_t)kTailRows, r - b0);
@@ -763,7 +772,7 @@ k1_tcs_tail(const __nv_bfloat16* __restrict__ X, const __nv_bfloat16* __restrict
   }
   __syncthreads();
   const int64_t i = (int64_t)blockIdx.y * kTailQ + threadIdx.x;
-  if (i >= M) return;
+  if (i < M) {
   float acc[kTailRows];
 #pragma unroll
   for (int k = 0; k < kTailRows; ++k) acc[k] = 0.0f;
@@ -790,6 +799,8 @@ k1_tcs_tail(const __nv_bfloat16* __restrict__ X, const __nv_bfloat16* __restrict
       atomicMax(&G[i * L + b0 + k], (unsigned long long)make_key(sc, (int32_t)j));
     }
   }
+  }
+  pdl_wait();
 }
 
 PFN_cuTensorMapEncodeTiled_v12000 get_encode_s() {
@@ -928,8 +939,8 @@ cudaError_t launch_tcs(const CUtensorMap& mx, const CUtensorMap& mq, const TcsAr
   e = cudaFuncSetAttribute(k1_tcs_kernel<NKS, MODE, BM>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  k1_tcs_kernel<NKS, MODE, BM><<<(unsigned)blocks, kThreadsS, smem, st>>>(mx, mq, a);
-  return cudaGetLastError();
+  return launch_pdl(k1_tcs_kernel<NKS, MODE, BM>, dim3((unsigned)blocks), dim3(kThreadsS), smem,
+                    st, mx, mq, a);
 }
 
 }  // namespace
@@ -1011,10 +1022,10 @@ cudaError_t launch_k1_tcs(int64_t N, int64_t M, int64_t L, int D, int metric, in
   if (!runs && r > 0) {
     dim3 grid((unsigned)cdiv(r, kTailRows), (unsigned)cdiv(M, kTailQ));
     const size_t tsmem = (size_t)kTailRows * pitch * 2;  // <= 32 KB (pitch <= 4096)
-    k1_tcs_tail<<<grid, kTailQ, tsmem, st>>>(reinterpret_cast<const __nv_bfloat16*>(X),
-                                         reinterpret_cast<const __nv_bfloat16*>(Qp), hnorm, N, M,
-                                         L, a.T, pitch, metric, G);
-    e = cudaGetLastError();
+    e = launch_pdl(k1_tcs_tail, grid, dim3(kTailQ), tsmem, st,
+                   reinterpret_cast<const __nv_bfloat16*>(X),
+                   reinterpret_cast<const __nv_bfloat16*>(Qp), hnorm, N, M, L, a.T, pitch, metric,
+                   G);
   }
   return e;
 }

@@ -265,6 +265,7 @@ k23_kernel(const uint64_t* __restrict__ G, int64_t L, int Kp, int K, int D,
   __shared__ uint64_t s_key[32];
   const int64_t i = blockIdx.x;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  pdl_wait();  // the keys come from the contraction (and the ragged-row kernel)
   if (warp == 0) {
     uint64_t k[KPL];
 #pragma unroll
@@ -368,9 +369,8 @@ cudaError_t run_k23(const uint64_t* G, int64_t M, int64_t L, int Kp, int K, int 
   const unsigned blocks = (unsigned)M;
 #define K23_CASE(P)                                                                          \
   case P:                                                                                    \
-    k23_kernel<METRIC, P><<<blocks, 128, 0, st>>>(G, L, Kp, K, D, qf32, q_stride, xf32, N,  \
-                                                  out_val, out_idx);                         \
-    break;
+    return launch_pdl(k23_kernel<METRIC, P>, dim3(blocks), dim3(128), 0, st, G, L, Kp, K, D, \
+                      qf32, q_stride, xf32, N, out_val, out_idx);
   switch (kpl) {
     K23_CASE(1)
     K23_CASE(2)
@@ -381,7 +381,6 @@ cudaError_t run_k23(const uint64_t* G, int64_t M, int64_t L, int Kp, int K, int 
     default: return cudaErrorNotSupported;
   }
 #undef K23_CASE
-  return cudaGetLastError();
 }
 
 }  // namespace

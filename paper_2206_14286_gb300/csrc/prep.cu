@@ -22,6 +22,7 @@ prep_rows_kernel(const float* __restrict__ x, int64_t rows, int D, int pitch, in
                  void* __restrict__ out_lp, float* __restrict__ out_scale,
                  float* __restrict__ out_hnorm, float* __restrict__ out_f32,
                  uint32_t* __restrict__ zero_buf, int64_t zero_n) {
+  pdl_trigger();  // the contraction may launch and run its prologue meanwhile
   if (zero_buf) {
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < zero_n;
          t += (int64_t)gridDim.x * blockDim.x)
