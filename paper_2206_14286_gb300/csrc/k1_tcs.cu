@@ -939,8 +939,16 @@ cudaError_t launch_tcs(const CUtensorMap& mx, const CUtensorMap& mq, const TcsAr
   e = cudaFuncSetAttribute(k1_tcs_kernel<NKS, MODE, BM>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  return launch_pdl(k1_tcs_kernel<NKS, MODE, BM>, dim3((unsigned)blocks), dim3(kThreadsS), smem,
-                    st, mx, mq, a);
+  if constexpr (BM == kBinsRun) {
+    // Contiguous bins: a plain launch. Started early behind the query prep,
+    // the CTAs land on SMs in the order those free up, and the sharers of a
+    // part end up far apart (measured: 0.244 -> 0.284 ms per search).
+    k1_tcs_kernel<NKS, MODE, BM><<<(unsigned)blocks, kThreadsS, smem, st>>>(mx, mq, a);
+    return cudaGetLastError();
+  } else {
+    return launch_pdl(k1_tcs_kernel<NKS, MODE, BM>, dim3((unsigned)blocks), dim3(kThreadsS),
+                      smem, st, mx, mq, a);
+  }
 }
 
 }  // namespace

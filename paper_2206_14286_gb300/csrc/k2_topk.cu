@@ -266,6 +266,7 @@ k23_kernel(const uint64_t* __restrict__ G, int64_t L, int Kp, int K, int D,
   const int64_t i = blockIdx.x;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   pdl_wait();  // the keys come from the contraction (and the ragged-row kernel)
+  pdl_trigger();  // the next call's query prep may launch (it waits for this kernel)
   if (warp == 0) {
     uint64_t k[KPL];
 #pragma unroll

@@ -22,7 +22,11 @@ prep_rows_kernel(const float* __restrict__ x, int64_t rows, int D, int pitch, in
                  void* __restrict__ out_lp, float* __restrict__ out_scale,
                  float* __restrict__ out_hnorm, float* __restrict__ out_f32,
                  uint32_t* __restrict__ zero_buf, int64_t zero_n) {
-  pdl_trigger();  // the contraction may launch and run its prologue meanwhile
+  // Launched behind whatever the stream ran before: wait for it (its output
+  // may be these rows, or it may still read the buffers written here), then
+  // let the contraction launch and run its prologue.
+  pdl_wait();
+  pdl_trigger();
   if (zero_buf) {
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < zero_n;
          t += (int64_t)gridDim.x * blockDim.x)
@@ -100,19 +104,15 @@ cudaError_t launch_prep(const float* x, int64_t rows, int D, int pitch, int metr
   float* f = metric == KNN_COS ? out_f32 : nullptr;
   switch (dtype) {
     case KNN_F32:
-      prep_rows_kernel<KNN_F32><<<(unsigned)blocks, threads, 0, st>>>(
-          x, rows, D, pitch, metric, out_lp, nullptr, h, f, zero_buf, zero_n);
-      break;
+      return launch_pdl(prep_rows_kernel<KNN_F32>, dim3((unsigned)blocks), dim3(threads), 0, st, x,
+                        rows, D, pitch, metric, out_lp, (float*)nullptr, h, f, zero_buf, zero_n);
     case KNN_BF16:
-      prep_rows_kernel<KNN_BF16><<<(unsigned)blocks, threads, 0, st>>>(
-          x, rows, D, pitch, metric, out_lp, nullptr, h, f, zero_buf, zero_n);
-      break;
+      return launch_pdl(prep_rows_kernel<KNN_BF16>, dim3((unsigned)blocks), dim3(threads), 0, st, x,
+                        rows, D, pitch, metric, out_lp, (float*)nullptr, h, f, zero_buf, zero_n);
     default:
-      prep_rows_kernel<KNN_E4M3><<<(unsigned)blocks, threads, 0, st>>>(
-          x, rows, D, pitch, metric, out_lp, out_scale, h, f, zero_buf, zero_n);
-      break;
+      return launch_pdl(prep_rows_kernel<KNN_E4M3>, dim3((unsigned)blocks), dim3(threads), 0, st, x,
+                        rows, D, pitch, metric, out_lp, out_scale, h, f, zero_buf, zero_n);
   }
-  return cudaGetLastError();
 }
 
 }  // namespace tpuknn
