@@ -777,18 +777,25 @@ k1_tcs_tail(const __nv_bfloat16* __restrict__ X, const __nv_bfloat16* __restrict
 #pragma unroll
   for (int k = 0; k < kTailRows; ++k) acc[k] = 0.0f;
   const uint4* qrow = reinterpret_cast<const uint4*>(Q + i * pitch);
-  for (int part = 0; part < chunks; ++part) {
-    const uint4 qv = qrow[part];
-    const __nv_bfloat16* qe = reinterpret_cast<const __nv_bfloat16*>(&qv);
-    float qf[8];
+  // eight 16-byte pieces of the query row in flight at a time
+  for (int p0 = 0; p0 < chunks; p0 += 8) {
+    uint4 qv[8];
 #pragma unroll
-    for (int e = 0; e < 8; ++e) qf[e] = __bfloat162float(qe[e]);
+    for (int u = 0; u < 8; ++u) qv[u] = p0 + u < chunks ? qrow[p0 + u] : make_uint4(0, 0, 0, 0);
 #pragma unroll
-    for (int k = 0; k < kTailRows; ++k) {
-      const uint4 xv = reinterpret_cast<const uint4*>(rows + k * pitch)[part];
-      const __nv_bfloat16* xe = reinterpret_cast<const __nv_bfloat16*>(&xv);
+    for (int u = 0; u < 8; ++u) {
+      if (p0 + u >= chunks) break;
+      const __nv_bfloat16* qe = reinterpret_cast<const __nv_bfloat16*>(&qv[u]);
+      float qf[8];
 #pragma unroll
-      for (int e = 0; e < 8; ++e) acc[k] = fmaf(qf[e], __bfloat162float(xe[e]), acc[k]);
+      for (int e = 0; e < 8; ++e) qf[e] = __bfloat162float(qe[e]);
+#pragma unroll
+      for (int k = 0; k < kTailRows; ++k) {
+        const uint4 xv = reinterpret_cast<const uint4*>(rows + k * pitch)[p0 + u];
+        const __nv_bfloat16* xe = reinterpret_cast<const __nv_bfloat16*>(&xv);
+#pragma unroll
+        for (int e = 0; e < 8; ++e) acc[k] = fmaf(qf[e], __bfloat162float(xe[e]), acc[k]);
+      }
     }
   }
 #pragma unroll
