@@ -28,9 +28,17 @@ prep_rows_kernel(const float* __restrict__ x, int64_t rows, int D, int pitch, in
   pdl_wait();
   pdl_trigger();
   if (zero_buf) {
-    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < zero_n;
-         t += (int64_t)gridDim.x * blockDim.x)
-      zero_buf[t] = 0u;
+    // 16-byte stores where the buffer allows, then the odd words
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int64_t done = 0;
+    if ((reinterpret_cast<uintptr_t>(zero_buf) & 15) == 0) {
+      const int64_t n4 = zero_n / 4;
+      for (int64_t t = t0; t < n4; t += stride)
+        reinterpret_cast<uint4*>(zero_buf)[t] = make_uint4(0u, 0u, 0u, 0u);
+      done = n4 * 4;
+    }
+    for (int64_t t = done + t0; t < zero_n; t += stride) zero_buf[t] = 0u;
   }
   const int lane = threadIdx.x & 31;
   const int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
