@@ -17,6 +17,12 @@
  *     stream). Work is enqueued asynchronously; nothing synchronises unless
  *     stated. A non-OK return means nothing was enqueued, except
  *     KNN_ECUDA (a launch failed; see knn_last_cuda_error).
+ *   - A search's kernels are chained by programmatic dependent launch: each
+ *     waits on the device for the kernel before it. Its last kernel lets a
+ *     following kernel that the caller launches WITH programmatic stream
+ *     serialization start early. Such a kernel must call
+ *     cudaGridDependencySynchronize() before it reads the outputs. Plain
+ *     launches, copies and events are ordered as usual.
  *   - Device-side waits are bounded. A kernel that gives up sets a sticky
  *     device flag; knn_sync_status() synchronises the device and returns
  *     KNN_ETIMEOUT once, then clears it.
