@@ -138,8 +138,24 @@ K1Plan make_plan(int64_t N, int64_t M, int64_t L, int D, int metric, int dtype,
   if (force_splits > 0) {
     splits = force_splits;
   } else {
-    const int64_t target = (int64_t)device_sm_count() * (dtype == KNN_F32 ? 4 : 1);
+    const int64_t sms = device_sm_count();
+    const int64_t target = sms * (dtype == KNN_F32 ? 4 : 1);
     splits = cdiv(target, units);
+    if (dtype != KNN_F32 && sms > 0) {
+      // tensor-core CTAs run one per SM: among a few split counts, take the
+      // one whose last wave is fullest (units * splits CTAs over `sms`)
+      double best = 0.0;
+      int64_t pick = splits;
+      for (int64_t s = splits; s < splits + 8 && s <= cdiv(N, p.Lk); ++s) {
+        const int64_t blocks = units * s;
+        const double fill = (double)blocks / (double)(cdiv(blocks, sms) * sms);
+        if (fill > best + 1e-9) {
+          best = fill;
+          pick = s;
+        }
+      }
+      splits = pick;
+    }
   }
   if (splits < 1) splits = 1;
   if (splits > p.ntiles) splits = p.ntiles;
