@@ -384,6 +384,90 @@ cudaError_t run_k23(const uint64_t* G, int64_t M, int64_t L, int Kp, int K, int 
 #undef K23_CASE
 }
 
+
+// Up to 2048 candidates and 256 selected per query (no running input): a CTA
+// of 8 warps per query. Warp w sorts candidates [256 w, 256 w + 256) held in
+// registers, element e = 32 r + lane in register r, by a bitonic network
+// (partners within a lane swap registers, partners across lanes exchange by
+// shuffle). Three merge rounds then halve the sorted lists: the top 256 of two
+// descending lists A and B are max(A[e], B[255 - e]), a bitonic sequence that
+// eight more bitonic steps sort. The result is the best Kp keys in order, as
+// from the CTA kernel, at O(L log^2 256) compare-exchanges instead of full
+// sorts of the whole buffer.
+__device__ __forceinline__ void wsort_step(uint64_t (&k)[8], int lane, int size, int stride,
+                                           bool all_desc) {
+  if (stride >= 32) {
+    const int rs = stride >> 5;
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+      if ((r & rs) == 0) {
+        const int e = r * 32 + lane;
+        const bool desc = all_desc || (e & size) == 0;
+        const uint64_t a = k[r], b = k[r | rs];
+        const bool sw = desc ? (a < b) : (a > b);
+        k[r] = sw ? b : a;
+        k[r | rs] = sw ? a : b;
+      }
+    }
+  } else {
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+      const int e = r * 32 + lane;
+      const bool desc = all_desc || (e & size) == 0;
+      const uint64_t o = shfl_xor_u64(k[r], stride);
+      const bool lower = (lane & stride) == 0;
+      const bool keep_max = (lower == desc);
+      k[r] = keep_max ? (o > k[r] ? o : k[r]) : (o < k[r] ? o : k[r]);
+    }
+  }
+}
+
+template <class Src>
+__global__ void __launch_bounds__(256)
+k2_wsort_kernel(Src src, int64_t L, int Kp, uint64_t* __restrict__ out_keys) {
+  __shared__ uint64_t lists[8][256];
+  const int64_t i = blockIdx.x;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  uint64_t k[8];
+#pragma unroll
+  for (int r = 0; r < 8; ++r) {
+    const int64_t b = (int64_t)warp * 256 + r * 32 + lane;
+    k[r] = b < L ? src.key(i, b) : 0;
+  }
+#pragma unroll
+  for (int size = 2; size <= 256; size <<= 1)
+#pragma unroll
+    for (int stride = size >> 1; stride > 0; stride >>= 1) wsort_step(k, lane, size, stride, false);
+#pragma unroll
+  for (int r = 0; r < 8; ++r) lists[warp][r * 32 + lane] = k[r];
+  for (int level = 1; level < 8; level <<= 1) {
+    __syncthreads();
+    if ((warp & (2 * level - 1)) == 0) {
+      const uint64_t* B = lists[warp + level];
+#pragma unroll
+      for (int r = 0; r < 8; ++r) {
+        const int e = r * 32 + lane;
+        const uint64_t a = lists[warp][e], b = B[255 - e];
+        k[r] = a > b ? a : b;
+      }
+#pragma unroll
+      for (int stride = 128; stride > 0; stride >>= 1) wsort_step(k, lane, 256, stride, true);
+      __syncwarp();
+#pragma unroll
+      for (int r = 0; r < 8; ++r) lists[warp][r * 32 + lane] = k[r];
+    }
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < Kp; t += blockDim.x) out_keys[i * Kp + t] = lists[0][t];
+}
+
+template <class Src>
+cudaError_t run_k2_wsort(const Src& src, int64_t M, int64_t L, int Kp, uint64_t* out,
+                         cudaStream_t st) {
+  k2_wsort_kernel<Src><<<(unsigned)M, 256, 0, st>>>(src, L, Kp, out);
+  return cudaGetLastError();
+}
+
 }  // namespace
 
 cudaError_t launch_merge_bins(const K1Plan& p, Partials parts, float* out_v, int32_t* out_a,
@@ -409,36 +493,37 @@ cudaError_t launch_merge_bins(const K1Plan& p, Partials parts, float* out_v, int
   return cudaGetLastError();
 }
 
-// The warp kernel serves up to 1024 candidates and 64 selected per query
-// (no running input); the CTA kernel everything else.
-static bool use_warp(int64_t L, int Kp, const uint64_t* run_in) {
-  return run_in == nullptr && L <= 1024 && Kp <= 64;
+// Per query: the warp kernel serves up to 1024 candidates and 64 selected,
+// the sorting CTA kernel up to 2048 candidates and 256 selected (both with
+// no running input); the streaming CTA kernel everything else.
+template <class Src>
+cudaError_t dispatch_k2(const Src& s, const K1Plan& p, int Kp, const uint64_t* run_in,
+                        uint64_t* out_keys, cudaStream_t st) {
+  if (run_in == nullptr && p.L <= 1024 && Kp <= 64) return run_k2_warp(s, p.M, p.L, Kp, out_keys, st);
+  if (run_in == nullptr && p.L <= 2048 && Kp <= 256 && p.M <= 0x7fffffffLL)
+    return run_k2_wsort(s, p.M, p.L, Kp, out_keys, st);
+  return run_k2(s, p.M, p.L, Kp, run_in, out_keys, st);
 }
 
 cudaError_t launch_k2(const K1Plan& p, Partials parts, int Kp, const uint64_t* run_in,
                       uint64_t* out_keys, cudaStream_t st) {
   if (p.M <= 0) return cudaSuccess;
-  const bool warp = use_warp(p.L, Kp, run_in);
   if (parts.keys64) {
     KeySource s{reinterpret_cast<const uint64_t*>(parts.v), p.L};
-    return warp ? run_k2_warp(s, p.M, p.L, Kp, out_keys, st)
-                : run_k2(s, p.M, p.L, Kp, run_in, out_keys, st);
+    return dispatch_k2(s, p, Kp, run_in, out_keys, st);
   }
   if (parts.a) {
     PairSource s{parts.v, parts.a, p.M, p.Lk, p.L, p.nsplits, parts.index_offset, p.g};
-    return warp ? run_k2_warp(s, p.M, p.L, Kp, out_keys, st)
-                : run_k2(s, p.M, p.L, Kp, run_in, out_keys, st);
+    return dispatch_k2(s, p, Kp, run_in, out_keys, st);
   }
   if (parts.merged) {
     MergedSource s{reinterpret_cast<const uint32_t*>(parts.v), p.M, p.Lk, p.L,
                    parts.index_offset, p.g, p.code_bits};
-    return warp ? run_k2_warp(s, p.M, p.L, Kp, out_keys, st)
-                : run_k2(s, p.M, p.L, Kp, run_in, out_keys, st);
+    return dispatch_k2(s, p, Kp, run_in, out_keys, st);
   }
   PackedSource s{reinterpret_cast<const uint32_t*>(parts.v), p.M, p.Lk, p.L, p.nsplits,
                  p.tiles_per_split, parts.index_offset, p.g, p.code_bits};
-  return warp ? run_k2_warp(s, p.M, p.L, Kp, out_keys, st)
-              : run_k2(s, p.M, p.L, Kp, run_in, out_keys, st);
+  return dispatch_k2(s, p, Kp, run_in, out_keys, st);
 }
 
 bool k23_supported(int64_t M, int64_t L, int Kp, int K, int D, const float* qf32,
