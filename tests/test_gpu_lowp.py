@@ -314,3 +314,17 @@ def test_search_fused_rescoring_bounds(metric):
         # every row returned once per query
         for r in gi:
             assert len(set(r[r >= 0].tolist())) == int((r >= 0).sum())
+
+
+@pytest.mark.parametrize("metric", METRICS)
+def test_search_ragged_last_grid_row(metric):
+    """With j mod L bins the N mod L rows of the ragged last grid row are
+    scored by their own kernel and merge with the tensor-core bins: one such
+    row, and a few hundred of them, with L up to the fused rescoring's 1024."""
+    for N, L in [(257, 64), (1456, 300), (2657, 600), (2303, 1024)]:
+        X, Q = inputs(N, 77, 64, seed=N)
+        frac, gi = run_lowp(X, Q, metric, "bf16", 10, L, 2)
+        if metric != "l2":
+            assert frac > 0.25, (N, L, frac)
+        ragged = N - (N // L) * L
+        assert ragged in (1, 256, 257, 255)
