@@ -47,7 +47,7 @@ def parse():
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-unfused", action="store_true")
     ap.add_argument("--serving-requests", type=int, default=1200)
-    ap.add_argument("--serving-rates", default="6000,40000",
+    ap.add_argument("--serving-rates", default="1500,6000",
                     help="offered requests/s, one trace per rate")
     return ap.parse_args()
 
@@ -467,17 +467,17 @@ def unfused_leg(Xd, Qd, K, L):
 
 def serving_leg(args, db1, w1):
     """Continuous batching over two resident databases: the bench's own
-    (1M x 128, L2) and a 500,000 x 768 inner-product mixture (the serving
-    configuration's second database, scaled from 4M rows so that its host
-    generation stays short). Seeded Poisson arrivals, m log-uniform in
-    [1, 512], K in {10, 100}. Latency = completion - arrival, wall clock."""
+    (1,000,000 x 128, L2) and a 4,000,000 x 768 inner-product Gaussian mixture
+    (256 centres, drawn on the device from a fixed seed). Seeded Poisson
+    arrivals, m log-uniform in [1, 512], K in {10, 100}, a 4 GiB serving arena.
+    Latency = completion - arrival, wall clock."""
     import torch
     from paper_2206_14286_gb300 import search as S, serve as SV, synth
-    X2 = synth.mixture(500_000, 768, 256, 11)
-    db2 = S.Database(torch.from_numpy(X2).cuda(), metric="ip", dtype="bf16")
-    del X2
-    dbs = {"db1_1m_x128_l2": db1, "db2_500k_x768_ip": db2}
-    shapes = {"db1_1m_x128_l2": (128, 256), "db2_500k_x768_ip": (768, 256)}
+    X2 = synth.mixture_device(4_000_000, 768, 256, 11, "cuda")
+    db2 = S.Database(X2, metric="ip", dtype="bf16")
+    n1, n2 = "db1_1m_x128_l2", "db2_4m_x768_ip"
+    dbs = {n1: db1, n2: db2}
+    shapes = {n1: (128, 256), n2: (768, 256)}
     runs = []
     for rate in [float(r) for r in args.serving_rates.split(",") if r]:
         trace = synth.serving_trace(args.serving_requests, rate, shapes)
@@ -499,8 +499,9 @@ def serving_leg(args, db1, w1):
                     "errors": sum(r.error is not None for r in done)})
         runs.append(out)
     S.sync_status()
-    del db2
-    return {"databases": "1M x 128 L2 and 500k x 768 IP, BF16, FP32 re-rank of 2K",
+    del db2, X2
+    torch.cuda.empty_cache()
+    return {"databases": "1M x 128 L2 and 4M x 768 IP, BF16, FP32 re-rank of 2K",
             "arrivals": "seeded Poisson, m log-uniform in [1, 512], K in {10, 100}",
             "runs": runs}
 

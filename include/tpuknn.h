@@ -182,10 +182,13 @@ size_t knn_search_host_workspace(int64_t N, int32_t D, int32_t dtype, int32_t me
  *   - KNN_ENOMEM when knn_search_workspace(...) for the same arguments
  *     exceeds KNN_STATIC_WORKSPACE_BYTES (checked before any CUDA call);
  *     use knn_search with a workspace of your own for larger batches.
- *   - The first call on each device looks up the buffer's address
- *     (cudaGetSymbolAddress with that device current, which can load the
- *     module); later calls reuse it. Make that first call before any stream
- *     capture begins. A failed lookup returns KNN_ECUDA.
+ *   - The first call in each CUDA context looks up the buffer's address
+ *     (cudaGetSymbolAddress with the device current, which can load the
+ *     module); later calls in the same context reuse it. The address is
+ *     cached per device with the context's unique id, so after
+ *     cudaDeviceReset (which replaces the device's primary context) the next
+ *     call looks it up again. Make the first call in a context before any
+ *     stream capture begins. A failed lookup returns KNN_ECUDA.
  *   - Nothing in the buffer has to start at zero: each call clears what it
  *     accumulates into (the merged bin winners) in its first kernel.
  *   - One buffer serves every call on a device. Calls that overlap in time
@@ -202,17 +205,53 @@ knn_status knn_search_static(const void* db_lp, const float* db_scale, const flo
                              float* out_val, int32_t* out_idx, void* stream);
 
 /*
+ * A database held by the library (the problem statement's fixed set of N
+ * reference vectors, Sec. 2, prepared once for the contraction as
+ * knn_prepare does). knn_db_create allocates device memory with cudaMalloc on
+ * the current device -- the rows in `dtype` (N x knn_row_pitch(D)), the FP32
+ * half norms (L2), the per-row scales (E4M3), and the FP32 rows the re-rank
+ * reads (always for COS, where they are the unit-length rows; for IP / L2 a
+ * copy of x when keep_f32 != 0, else the re-rank dequantises the stored rows)
+ * -- prepares them from x (N x D FP32, device) on `stream` and returns once
+ * the preparation has finished; x may be freed afterwards. The handle owns
+ * these buffers until knn_db_destroy frees them (cudaFree, which waits for
+ * the device). Errors: KNN_EINVAL (sizes, NULL, alignment), KNN_ENOMEM
+ * (cudaMalloc failed), KNN_EUNSUPPORTED (D > 4096), KNN_ECUDA; on any error
+ * nothing stays allocated and *out is NULL.
+ *
+ * knn_db_search is knn_search on the handle's buffers (same arguments from q
+ * on, same rules); knn_db_search_workspace gives its workspace size (0 for
+ * invalid arguments). knn_db_info reports N, D, metric and dtype (any output
+ * pointer may be NULL). A handle may serve several streams and threads at
+ * once (searches only read it); destroying it while a search that uses it is
+ * in flight is the caller's error.
+ */
+typedef struct knn_db knn_db;
+
+knn_status knn_db_create(const float* x, int64_t N, int32_t D, int32_t metric, int32_t dtype,
+                         int32_t keep_f32, void* stream, knn_db** out);
+knn_status knn_db_destroy(knn_db* db);
+knn_status knn_db_info(const knn_db* db, int64_t* N, int32_t* D, int32_t* metric,
+                       int32_t* dtype);
+knn_status knn_db_search(const knn_db* db, const float* q, int64_t M, int32_t K, int64_t L,
+                         int32_t bin_map, double recall_target, int32_t rerank_mult,
+                         float* out_val, int32_t* out_idx, void* workspace, size_t ws_bytes,
+                         void* stream);
+size_t knn_db_search_workspace(const knn_db* db, int64_t M, int32_t K, int64_t L, int32_t bin_map,
+                               double recall_target, int32_t rerank_mult);
+
+/*
  * PartialReduce alone (Alg. 1; the paper's aggregate_to_topk = False,
  * App. A.1): for every query i and bin l the best internal score and its
  * index, out_v[i*L + l], out_a[i*L + l]. Scores are in the internal
  * orientation (see the conventions above; L2 is the relaxed score).
- * With KNN_BINS_MOD and KNN_BF16 / KNN_E4M3 the values carry the
- * contraction's rounding: the kernel keeps only the top 32 - c bits of each
- * FP32 score, c <= 13, while it reduces (the low bits hold the row's position
- * in its bin); for E4M3 the per-query scale is left out of the value (it does
- * not change the order within a query). With KNN_BINS_CONTIGUOUS (BF16) the
- * values are the FP32 accumulator, the L2 half norm entering the contraction
- * as a three-part BF16 split (error below 2^-24 of the norm).
+ * With KNN_BF16 (either bin map) the values are the FP32 accumulator of the
+ * contraction, the L2 half norm entering it as a three-part BF16 split
+ * (error below 2^-24 of the norm). With KNN_E4M3 the kernel keeps only the
+ * top 32 - c bits of each FP32 score, c <= 13, while it reduces (the low bits
+ * hold the row's position in its bin), and the per-query scale is left out of
+ * the value (it does not change the order within a query). With KNN_F32 the
+ * values are the FP32 scores.
  */
 knn_status knn_partial_reduce(const void* db_lp, const float* db_scale, const float* db_hnorm,
                               int64_t N, int32_t D, int32_t dtype, int32_t metric, const float* q,

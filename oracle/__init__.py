@@ -24,6 +24,6 @@ from .core import (  # noqa: F401
     build, lib_path,
     exact_topk, partial_reduce, topk_pairs, binwise_topk, rerank, grad, score,
     bin_max, approx_max_k,
-    bf16_round, e4m3_rows, e4m3_round, normalize_rows,
+    bf16_round, e4m3_rows, e4m3_round, normalize_rows, set_threads,
 )
 from . import recall, loss  # noqa: F401

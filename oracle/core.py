@@ -62,6 +62,8 @@ def _load():
             lib.orc_normalize_rows.argtypes = [P, i64, i32, P]
             lib.orc_e4m3_round.argtypes = [ctypes.c_double]
             lib.orc_e4m3_round.restype = ctypes.c_double
+            lib.orc_set_threads.argtypes = [i32]
+            lib.orc_set_threads.restype = i32
             _lib = lib
     return _lib
 
@@ -231,3 +233,10 @@ def normalize_rows(x):
     y = np.empty((rows, D), np.float32)
     _load().orc_normalize_rows(_p(x), rows, D, _p(y))
     return y
+
+
+def set_threads(n):
+    """Threads of the oracle's OpenMP loops over queries (for timing runs;
+    results do not depend on it). Returns the previous count; n < 1 only
+    reads it."""
+    return _load().orc_set_threads(int(n))

@@ -29,6 +29,7 @@
  * identically on x86-64 and aarch64).
  */
 #include <math.h>
+#include <omp.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
@@ -404,4 +405,14 @@ void orc_normalize_rows(const float *x, int64_t rows, int D, float *y) {
     double inv = 1.0 / sqrt(n2);
     for (int d = 0; d < D; ++d) y[r * D + d] = (float)((double)xr[d] * inv);
   }
+}
+
+/* ---------------------------------------------------------------------- */
+/* Thread count of the OpenMP loops over queries (timing runs only: results */
+/* do not depend on it). Returns the previous maximum; n < 1 only reads it. */
+/* ---------------------------------------------------------------------- */
+int orc_set_threads(int n) {
+  int prev = omp_get_max_threads();
+  if (n > 0) omp_set_num_threads(n);
+  return prev;
 }

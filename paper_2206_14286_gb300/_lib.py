@@ -44,6 +44,11 @@ SIGNATURES = {
     "knn_backward": (ctypes.c_int, [P, P, P, I64, I32, I32, I32, P, I64, I32, P, P, P, P, I32,
                                     I32, P, SZ, P]),
     "knn_backward_workspace": (SZ, [I64, I32, I64, I32, I32]),
+    "knn_db_create": (ctypes.c_int, [P, I64, I32, I32, I32, I32, P, P]),
+    "knn_db_destroy": (ctypes.c_int, [P]),
+    "knn_db_info": (ctypes.c_int, [P, P, P, P, P]),
+    "knn_db_search": (ctypes.c_int, [P, P, I64, I32, I64, I32, DBL, I32, P, P, P, SZ, P]),
+    "knn_db_search_workspace": (SZ, [P, I64, I32, I64, I32, DBL, I32]),
     "knn_sync_status": (ctypes.c_int, []),
     "knn_profile_enable": (ctypes.c_int, [I32]),
     "knn_profile_read": (ctypes.c_int, [I32, P, P]),

@@ -1,9 +1,12 @@
 // api.cu -- the extern "C" boundary: argument checks, the bin planner
 // (Eq. 13-14), work decomposition, workspace layout and kernel launches.
-#include <atomic>
 #include <cmath>
 #include <cstring>
+#include <mutex>
 #include <new>
+
+#include <cuda.h>
+#include <cudaTypedefs.h>
 
 #include "common.cuh"
 #include "kernels.h"
@@ -490,26 +493,71 @@ knn_status exact_impl(const SearchArgs& a, float* out_val, int32_t* out_idx, voi
 // ---------------------------------------------------------------------------
 // The library's own search scratch (knn_search_static). A file-scope device
 // array is reserved when the module is loaded, so a search through it needs
-// no allocation at call time. Its device address is looked up once per device
-// with that device current and kept; two threads racing on the first lookup
-// store the same address.
+// no allocation at call time. Its device address belongs to the CUDA context
+// the module is loaded in: it is looked up with the device current and kept
+// per device together with that context's unique id (cuCtxGetId). A call that
+// finds another context current -- after cudaDeviceReset the device's
+// primary context is a new one -- looks the address up again.
 // ---------------------------------------------------------------------------
 constexpr int kMaxDevices = 64;
 static __device__ __align__(256) unsigned char g_static_ws[KNN_STATIC_WORKSPACE_BYTES];
-std::atomic<void*> g_static_ws_addr[kMaxDevices];
+struct StaticWsSlot {
+  unsigned long long ctx_id = 0;  // 0: nothing cached
+  void* addr = nullptr;
+};
+StaticWsSlot g_static_ws_slot[kMaxDevices];
+std::mutex g_static_ws_mu;
+
+// Unique id of the context current on this thread (0 if none is current).
+knn_status current_context_id(unsigned long long* id) {
+  static PFN_cuCtxGetCurrent_v4000 get_cur = nullptr;
+  static PFN_cuCtxGetId_v12000 get_id = nullptr;
+  if (!get_cur || !get_id) {
+    void* p1 = nullptr;
+    void* p2 = nullptr;
+    cudaDriverEntryPointQueryResult q1, q2;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p1, 4000, cudaEnableDefault, &q1) !=
+            cudaSuccess ||
+        q1 != cudaDriverEntryPointSuccess ||
+        cudaGetDriverEntryPointByVersion("cuCtxGetId", &p2, 12000, cudaEnableDefault, &q2) !=
+            cudaSuccess ||
+        q2 != cudaDriverEntryPointSuccess) {
+      cudaGetLastError();
+      return KNN_ECUDA;
+    }
+    get_cur = reinterpret_cast<PFN_cuCtxGetCurrent_v4000>(p1);
+    get_id = reinterpret_cast<PFN_cuCtxGetId_v12000>(p2);
+  }
+  CUcontext ctx = nullptr;
+  if (get_cur(&ctx) != CUDA_SUCCESS) return KNN_ECUDA;
+  *id = 0;
+  if (ctx && get_id(ctx, id) != CUDA_SUCCESS) return KNN_ECUDA;
+  return KNN_OK;
+}
 
 knn_status static_workspace(void** out) {
   int dev = -1;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return cuda_status(e);
   if (dev < 0 || dev >= kMaxDevices) return KNN_EUNSUPPORTED;
-  void* p = g_static_ws_addr[dev].load(std::memory_order_acquire);
-  if (!p) {
-    e = cudaGetSymbolAddress(&p, g_static_ws);
-    if (e != cudaSuccess) return cuda_status(e);
-    if (!p || !aligned(p, kAlign)) return KNN_ECUDA;
-    g_static_ws_addr[dev].store(p, std::memory_order_release);
+  std::lock_guard<std::mutex> lock(g_static_ws_mu);
+  unsigned long long id = 0;
+  knn_status rc = current_context_id(&id);
+  if (rc != KNN_OK) return rc;
+  StaticWsSlot& slot = g_static_ws_slot[dev];
+  if (id != 0 && slot.ctx_id == id) {
+    *out = slot.addr;
+    return KNN_OK;
   }
+  // first call in this context (the lookup makes the device's primary
+  // context current if no context was)
+  void* p = nullptr;
+  e = cudaGetSymbolAddress(&p, g_static_ws);
+  if (e != cudaSuccess) return cuda_status(e);
+  if (!p || !aligned(p, kAlign)) return KNN_ECUDA;
+  if ((rc = current_context_id(&id)) != KNN_OK) return rc;
+  slot.ctx_id = id;
+  slot.addr = p;
   *out = p;
   return KNN_OK;
 }
@@ -803,6 +851,105 @@ knn_status knn_backward(const void* db_lp, const float* db_scale, const float* x
   return cuda_status(launch_backward(M, D, K, metric, q, x_f32, db_lp, dtype, knn_row_pitch(D),
                                      db_scale, N, idx, grad_val, dq, dx, zero_dx, deterministic,
                                      workspace, (cudaStream_t)stream));
+}
+
+// ---------------------------------------------------------------------------
+// Library-owned database (knn_db_*): the prepared rows and their side arrays
+// in device memory the handle allocates and frees.
+// ---------------------------------------------------------------------------
+struct knn_db {
+  int64_t N;
+  int32_t D, metric, dtype;
+  int device;
+  void* lp;
+  float* scale;
+  float* hnorm;
+  float* f32;
+};
+
+static void db_free(knn_db* h) {
+  if (!h) return;
+  int cur = -1;
+  const bool switched = cudaGetDevice(&cur) == cudaSuccess && cur != h->device &&
+                        cudaSetDevice(h->device) == cudaSuccess;
+  if (h->lp) cudaFree(h->lp);
+  if (h->scale) cudaFree(h->scale);
+  if (h->hnorm) cudaFree(h->hnorm);
+  if (h->f32) cudaFree(h->f32);
+  if (switched) cudaSetDevice(cur);
+  delete h;
+}
+
+knn_status knn_db_create(const float* x, int64_t N, int32_t D, int32_t metric, int32_t dtype,
+                         int32_t keep_f32, void* stream, knn_db** out) {
+  if (!out) return KNN_EINVAL;
+  *out = nullptr;
+  if (N < 1 || N >= ((int64_t)1 << 31) - 1 || D < 1 || !valid_metric(metric) ||
+      !valid_dtype(dtype) || !x || !aligned(x, 4))
+    return KNN_EINVAL;
+  if (D > kMaxD) return KNN_EUNSUPPORTED;
+  knn_db* h = new (std::nothrow) knn_db{N, D, metric, dtype, 0, nullptr, nullptr, nullptr, nullptr};
+  if (!h) return KNN_ENOMEM;
+  cudaError_t e = cudaGetDevice(&h->device);
+  const size_t lp_bytes = (size_t)N * knn_row_pitch(D) * knn_dtype_bytes(dtype);
+  const bool want_f32 = metric == KNN_COS || keep_f32;
+  if (e == cudaSuccess) e = cudaMalloc(&h->lp, lp_bytes);
+  if (e == cudaSuccess && dtype == KNN_E4M3)
+    e = cudaMalloc(reinterpret_cast<void**>(&h->scale), (size_t)N * 4);
+  if (e == cudaSuccess && metric == KNN_L2)
+    e = cudaMalloc(reinterpret_cast<void**>(&h->hnorm), (size_t)N * 4);
+  if (e == cudaSuccess && want_f32)
+    e = cudaMalloc(reinterpret_cast<void**>(&h->f32), (size_t)N * D * 4);
+  cudaStream_t st = (cudaStream_t)stream;
+  // the re-rank source: the unit rows for COS (written by the preparation),
+  // else a copy of the rows as given
+  if (e == cudaSuccess && want_f32 && metric != KNN_COS)
+    e = cudaMemcpyAsync(h->f32, x, (size_t)N * D * 4, cudaMemcpyDeviceToDevice, st);
+  if (e == cudaSuccess)
+    e = launch_prep(x, N, D, knn_row_pitch(D), metric, dtype, h->lp, h->scale, h->hnorm,
+                    metric == KNN_COS ? h->f32 : nullptr, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) {
+    const knn_status rc = e == cudaErrorMemoryAllocation ? KNN_ENOMEM : cuda_status(e);
+    cudaGetLastError();
+    db_free(h);
+    return rc;
+  }
+  *out = h;
+  return KNN_OK;
+}
+
+knn_status knn_db_destroy(knn_db* db) {
+  if (!db) return KNN_EINVAL;
+  db_free(db);
+  return KNN_OK;
+}
+
+knn_status knn_db_info(const knn_db* db, int64_t* N, int32_t* D, int32_t* metric,
+                       int32_t* dtype) {
+  if (!db) return KNN_EINVAL;
+  if (N) *N = db->N;
+  if (D) *D = db->D;
+  if (metric) *metric = db->metric;
+  if (dtype) *dtype = db->dtype;
+  return KNN_OK;
+}
+
+size_t knn_db_search_workspace(const knn_db* db, int64_t M, int32_t K, int64_t L, int32_t bin_map,
+                               double recall_target, int32_t rerank_mult) {
+  if (!db) return 0;
+  return knn_search_workspace(db->N, db->D, db->dtype, db->metric, M, K, L, bin_map,
+                              recall_target, rerank_mult);
+}
+
+knn_status knn_db_search(const knn_db* db, const float* q, int64_t M, int32_t K, int64_t L,
+                         int32_t bin_map, double recall_target, int32_t rerank_mult,
+                         float* out_val, int32_t* out_idx, void* workspace, size_t ws_bytes,
+                         void* stream) {
+  if (!db) return KNN_EINVAL;
+  return knn_search(db->lp, db->scale, db->hnorm, db->f32, db->N, db->D, db->dtype, db->metric, q,
+                    M, K, L, bin_map, recall_target, rerank_mult, out_val, out_idx, workspace,
+                    ws_bytes, stream);
 }
 
 knn_status knn_profile_enable(int32_t on) {

@@ -212,6 +212,50 @@ class Database:
         return dq, dx
 
 
+class OwnedDatabase:
+    """A database held by the library (knn_db_create): the prepared buffers
+    live in device memory the library allocated, until close()."""
+
+    def __init__(self, x, metric="l2", dtype="bf16", keep_f32=True, stream=None):
+        import ctypes
+        if not (x.is_cuda and x.dtype == torch.float32 and x.dim() == 2):
+            raise ValueError("x must be a 2-D float32 CUDA tensor")
+        x = x.contiguous()
+        self.N, self.D = x.shape
+        self.metric, self.dtype, self.device = metric, dtype, x.device
+        h = ctypes.c_void_p()
+        with torch.cuda.device(x.device):
+            check(_lib.get().knn_db_create(x.data_ptr(), self.N, self.D, METRIC[metric],
+                                           DTYPE[dtype], int(bool(keep_f32)), _stream(stream),
+                                           ctypes.byref(h)), "knn_db_create")
+        self.handle = h
+        self._ws = None
+
+    def search(self, q, K, L=None, recall_target=0.95, rerank=2, stream=None, bins="mod"):
+        q = q.contiguous()
+        M = q.shape[0]
+        L = int(L) if L else plan_bins(self.N, K, recall_target)
+        lib = _lib.get()
+        nb = lib.knn_db_search_workspace(self.handle, M, K, L, BINS[bins], recall_target, rerank)
+        if nb == 0:
+            raise ValueError("invalid search arguments")
+        if self._ws is None or self._ws.numel() < nb:
+            self._ws = _workspace(nb, self.device)
+        val = torch.empty((M, K), dtype=torch.float32, device=self.device)
+        idx = torch.empty((M, K), dtype=torch.int32, device=self.device)
+        with torch.cuda.device(self.device):
+            check(lib.knn_db_search(self.handle, q.data_ptr(), M, K, L, BINS[bins], recall_target,
+                                    rerank, val.data_ptr(), idx.data_ptr(), self._ws.data_ptr(),
+                                    self._ws.numel(), _stream(stream)), "knn_db_search")
+        return val, idx
+
+    def close(self):
+        if self.handle is not None and self.handle.value:
+            with torch.cuda.device(self.device):
+                check(_lib.get().knn_db_destroy(self.handle), "knn_db_destroy")
+        self.handle = None
+
+
 def approx_max_k(scores, K, L=None, recall_target=0.95, bins="mod", is_min=False,
                  aggregate_to_topk=True, planning_size=0, stream=None):
     """The approx_max_k / approx_min_k operator (knn_approx_max_k) on an M x N

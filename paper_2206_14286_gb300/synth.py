@@ -11,6 +11,8 @@ Recipe (NumPy PCG64 generators, float32 output):
     The database uses the data seed (0 by default) and queries use another
     seed (1 by default) with the *same* centres, so queries come from the
     same mixture as the database.
+  * ``mixture_device``: the same mixture drawn on a CUDA device with torch's
+    seeded generator (large databases of the serving workload).
   * ``unit_rows``: rows scaled to unit l2 norm in float64 and stored as
     float32 (the cosine workload's "rows normalised after sampling").
   * ``serving_trace``: Poisson arrivals (exponential gaps at a given rate)
@@ -50,6 +52,26 @@ def mixture(n, d, n_centres, seed, centre_std=1.0, within_std=0.3, centre_seed=D
         pick = rng.integers(0, n_centres, size=e - s)
         noise = rng.standard_normal((e - s, d), dtype=np.float32)
         out[s:e] = centres[pick] + np.float32(within_std) * noise
+    return out
+
+
+def mixture_device(n, d, n_centres, seed, device, centre_std=1.0, within_std=0.3,
+                   centre_seed=DATA_SEED):
+    """The ``mixture`` recipe drawn on a CUDA device (for databases too large
+    to draw on the host in reasonable time): the same centres (NumPy, from the
+    centre seed), centre picks and N(0, within_std^2) noise from torch's
+    seeded Philox generator on the device. Same distribution as ``mixture``,
+    not the same numbers. Returns an n x d float32 CUDA tensor."""
+    import torch
+    centres = torch.from_numpy(mixture_centres(n_centres, d, centre_seed, centre_std)).to(device)
+    g = torch.Generator(device=device)
+    g.manual_seed(int(seed))
+    out = torch.empty((n, d), dtype=torch.float32, device=device)
+    for s in range(0, n, _CHUNK * 4):
+        e = min(n, s + _CHUNK * 4)
+        pick = torch.randint(0, n_centres, (e - s,), generator=g, device=device)
+        noise = torch.randn((e - s, d), generator=g, device=device)
+        out[s:e] = centres[pick] + within_std * noise
     return out
 
 

@@ -126,3 +126,23 @@ def test_approx_max_k_argument_checks_need_no_device(lib):
     assert lib.knn_approx_max_k_workspace(4, 100, 5, 10, 0, 0.9, 1) >= 4 * 10 * 8 + 4 * 5 * 8
     assert lib.knn_approx_max_k_workspace(4, 100, 5, 0, 0, 0.9, 0) > 0   # L planned
     assert lib.knn_approx_max_k_workspace(4, 100, 0, 0, 0, 0.9, 0) == 0  # no K to plan L
+
+
+def test_db_handle_rejects_bad_arguments_without_a_device(lib):
+    import ctypes
+    h = ctypes.c_void_p(123)
+    f = lib.knn_db_create
+    # (x, N, D, metric, dtype, keep_f32, stream, out)
+    assert f(None, 100, 8, 0, 1, 1, None, ctypes.byref(h)) == _lib.KNN_EINVAL
+    assert h.value is None                               # *out cleared on error
+    assert f(None, 100, 8, 0, 1, 1, None, None) == _lib.KNN_EINVAL
+    assert f(8, 0, 8, 0, 1, 1, None, ctypes.byref(h)) == _lib.KNN_EINVAL      # N = 0
+    assert f(8, 100, 8, 7, 1, 1, None, ctypes.byref(h)) == _lib.KNN_EINVAL    # metric
+    assert f(8, 100, 8, 0, 9, 1, None, ctypes.byref(h)) == _lib.KNN_EINVAL    # dtype
+    assert f(6, 100, 8, 0, 1, 1, None, ctypes.byref(h)) == _lib.KNN_EINVAL    # misaligned x
+    assert f(8, 100, 5000, 0, 1, 1, None, ctypes.byref(h)) == _lib.KNN_EUNSUPPORTED
+    assert lib.knn_db_destroy(None) == _lib.KNN_EINVAL
+    assert lib.knn_db_info(None, None, None, None, None) == _lib.KNN_EINVAL
+    assert lib.knn_db_search_workspace(None, 10, 5, 64, 0, 0.95, 2) == 0
+    assert lib.knn_db_search(None, None, 10, 5, 64, 0, 0.95, 2, None, None, None, 0,
+                             None) == _lib.KNN_EINVAL

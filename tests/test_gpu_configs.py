@@ -1,13 +1,31 @@
-"""Full-size workloads checked on sampled queries.
+"""Full-size workloads, checked element by element on sampled queries.
 
-FP8-E4M3 with per-row scales, cosine, N = 10,000,000 x D = 96 rows from a
-1024-centre mixture, M = 10,000 queries, K = 100, L from the recall law for
-0.95, FP32 re-rank of 2K candidates. The GPU runs the whole batch; the FP64
-oracle follows the same steps for a few sampled queries. The database does not
-fit the oracle in FP64 at once, so PartialReduce runs on chunks of 2^20 rows,
-a multiple of L: a row keeps its bin (j mod L) inside its chunk, and a bin's
-maximum is the maximum of its chunk maxima, ties to the smaller row, which is
-the earlier chunk. The re-rank scores the gathered candidate rows.
+The GPU runs the whole batch in the launch configuration the benchmark times;
+the FP64 oracle follows the same steps for sampled queries, and the rules of
+tests/parity.py apply to every sampled query: on a *decided* query (every
+margin that fixes the answer exceeds twice the tolerance) the indices must
+equal the oracle's bit for bit; on the others each returned value must match
+the oracle's value at its rank and its own row's score, and each row must be
+its bin's maximum, all within the tolerance. The PartialReduce output of the
+same launch shape (knn_partial_reduce) is compared bin by bin as well: the
+index bit-exact wherever the bin's best and second-best scores differ by more
+than twice the tolerance, the value within it everywhere.
+
+* BF16 / L2 / 1,000,000 x 128 Gaussian mixture, M = 1024, K = 10, L from the
+  recall law for 0.95 rounded up to the 128-row tile, FP32 re-rank of 2K: the
+  multi-part schedule of the tensor-core kernel (152 CTAs), its atomic merge
+  of bins split between CTAs, and the ragged last grid row all run here.
+  Bin-step tolerance: the FP32 accumulator the kernel keeps.
+* FP8-E4M3 with per-row scales, cosine, 10,000,000 x 96 rows from a
+  1024-centre mixture, M = 10,000, K = 100, FP32 re-rank. The database does
+  not fit the oracle in FP64 at once, so PartialReduce runs on chunks of 2^20
+  rows, a multiple of L: a row keeps its bin (j mod L) inside its chunk, and a
+  bin's maximum is the maximum of its chunk maxima, ties to the smaller row,
+  which is the earlier chunk. Bin-step tolerance: the packed 32-bit key of the
+  E4M3 kernel (its low bits hold the row's position in its bin).
+
+Score errors against FP64 (the low-precision contraction against the
+original FP32 data, and the returned values) are printed per workload.
 """
 import numpy as np
 import pytest
@@ -15,27 +33,262 @@ import torch
 
 import oracle
 from paper_2206_14286_gb300 import synth
+from tests import parity as PT
 from tests.gpu_util import db, dev, host
 
-pytestmark = pytest.mark.gpu
 CHUNK = 1 << 20
+BLOCK = 32          # sampled queries per block of full score rows
 
 
-def chunked_partial_reduce(Qs_fn, X, L, metric):
-    """PartialReduce over all rows of X, oracle per chunk, maxima merged."""
+def rng(seed):
+    return np.random.Generator(np.random.PCG64(seed))
+
+
+def scores_at(Q, X, rows, metric):
+    """FP64 larger-is-better scores of query Q (D,) against the rows X[rows],
+    by the same formula as parity.score_matrix."""
+    q = np.asarray(Q, np.float64)
+    x = np.asarray(X[rows], np.float64)
+    g = x @ q
+    if metric == "ip":
+        return g
+    if metric == "l2":
+        return -((q * q).sum() + (x * x).sum(1) - 2.0 * g)
+    return g / (np.sqrt((q * q).sum()) * np.sqrt((x * x).sum(1)))
+
+
+# ----------------------------------------------------------------------------
+# BF16 / L2 / 1M x 128 (the benchmark's workload)
+# ----------------------------------------------------------------------------
+N_SAMPLED_L2 = 128
+
+
+def l2_1m_oracle_side(bins, w=None):
+    """Everything of the headline check that needs no GPU: the sampled
+    queries, the oracle's PartialReduce / ExactRescoring / re-rank, the bin
+    statistics and the decided masks."""
+    from paper_2206_14286_gb300.search import plan_bins
+    w = w or synth.workload("mix_l2_1m")
+    X, Q, K = w["X"], w["Q"], w["K"]
+    N, M = X.shape[0], Q.shape[0]
+    L = plan_bins(N, K, 0.95, round_to=128)
+    Kp = 2 * K
+    samp = np.sort(rng(5).choice(M, size=N_SAMPLED_L2, replace=False))
+    Xs = oracle.bf16_round(X)
+    Qs = oracle.bf16_round(Q[samp])
+    Qf = Q[samp]
+    V, A = oracle.partial_reduce(Qs, Xs, L, "l2", bins=bins)
+    _, cand = oracle.topk_pairs(V, A, Kp)
+    ov, oi = oracle.rerank(Qf, X, cand, K, "l2")
+    tol_d = PT.fp32_acc_tol(Qs, Xs, "l2")
+    tol_f = 3e-5 * PT.query_scale(Qf, X, "l2")
+    best = np.empty((len(samp), L))
+    second = np.empty((len(samp), L))
+    decided = np.empty(len(samp), bool)
+    for b0 in range(0, len(samp), BLOCK):
+        b = slice(b0, b0 + BLOCK)
+        S_lp = PT.score_matrix(Qs[b], Xs, "l2")
+        best[b], second[b] = PT.bin_best_second(S_lp, L, bins)
+        del S_lp
+        S_f = PT.score_matrix(Qf[b], X, "l2")
+        cf = np.where(cand[b] >= 0, np.take_along_axis(S_f, np.maximum(cand[b], 0), 1), -np.inf)
+        del S_f
+        decided[b] = PT.decided_from_stats(best[b], second[b], Kp, cf, K, tol_d[b], tol_f[b])
+    return dict(X=X, Q=Q, K=K, L=L, Kp=Kp, samp=samp, Xs=Xs, Qs=Qs, V=V, A=A, cand=cand,
+                ov=ov, oi=oi, tol_d=tol_d, tol_f=tol_f, best=best, second=second,
+                decided=decided)
+
+
+# Decided fractions of the sampled queries under these tolerances, computed
+# from the oracle side alone (no GPU output enters them): the floors below sit
+# a little under them. Near-ties inside a bin (rows 0.3-sigma apart in 128
+# dimensions) leave most queries with at least one margin under 2 x tol.
+DECIDED_FLOOR_L2 = {"mod": 0.0, "contiguous": 0.0}
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("bins", ["mod", "contiguous"])
+def test_search_bf16_mixture_l2_1m_elementwise(bins):
+    from paper_2206_14286_gb300 import search as S
+    o = l2_1m_oracle_side(bins)
+    X, Q, K, L = o["X"], o["Q"], o["K"], o["L"]
+    N = X.shape[0]
+    samp = o["samp"]
+    d = db(X, "l2", "bf16")
+    val, idx = d.search(dev(Q), K, L=L, rerank=2, bins=bins)
+    Vg, Ag = d.partial_reduce(dev(Q), L, bins=bins)
+    gv, gi = host(val)[samp], host(idx)[samp]
+    Vg, Ag = host(Vg)[samp].astype(np.float64), host(Ag)[samp].astype(np.int64)
+    S.sync_status()
+    del d
+    torch.cuda.empty_cache()
+
+    # PartialReduce, bin by bin. The kernel's value is the relaxed score
+    # <q,x> - |x|^2/2; the oracle's is -|q-x|^2 = 2 (<q,x> - |x|^2/2) - |q|^2.
+    qn2 = (o["Qs"] ** 2).sum(1)
+    Vg_s = 2.0 * Vg - qn2[:, None]
+    owner = PT.bin_of_rows(N, L, bins)
+    assert np.all(owner[Ag] == np.arange(L)[None, :])
+    dec_bin = (o["best"] - o["second"]) > 2 * o["tol_d"][:, None]
+    np.testing.assert_array_equal(Ag[dec_bin], o["A"][dec_bin])
+    assert np.all(np.abs(Vg_s - o["V"]) <= o["tol_d"][:, None]), np.abs(Vg_s - o["V"]).max()
+    own = np.stack([scores_at(o["Qs"][k], o["Xs"], Ag[k], "l2") for k in range(len(samp))])
+    assert np.all(np.abs(Vg_s - own) <= o["tol_d"][:, None])
+    print("mix_l2_1m %s: %d sampled queries x %d bins, %.4f of bins decided"
+          % (bins, len(samp), L, dec_bin.mean()))
+
+    # the search, query by query
+    tol = np.maximum(o["tol_d"], o["tol_f"])
+    frac = PT.check_search_core(
+        gv, gi, o["ov"], o["oi"],
+        lambda i, j: scores_at(o["Qs"][i], o["Xs"], j, "l2"),
+        lambda i, j: scores_at(Q[samp[i]], X, j, "l2"),
+        o["best"], lambda j: owner[j], "l2", tol, o["decided"])
+    print("mix_l2_1m %s: decided queries %.3f (bit-exact indices there)" % (bins, frac))
+    assert frac >= DECIDED_FLOOR_L2[bins], frac
+    # decided queries: FP32 re-ranked values within the FP32 tolerance
+    dq = o["decided"]
+    np.testing.assert_allclose(gv[dq], o["ov"][dq], rtol=0, atol=float(o["tol_f"].max()))
+    # recall@10 of the sampled queries against the exact FP32 search
+    _, ei = oracle.exact_topk(Q[samp], X, K, "l2")
+    rec = np.mean([len(set(gi[k]) & set(ei[k])) / K for k in range(len(samp))])
+    orec = np.mean([len(set(o["oi"][k]) & set(ei[k])) / K for k in range(len(samp))])
+    # score error against FP64 on the original FP32 data: the BF16 bin-step
+    # score of each returned row, and the returned (FP32 re-ranked) value
+    lp_err, f_err = [], []
+    for k in range(len(samp)):
+        ex = -scores_at(Q[samp[k]], X, gi[k], "l2")
+        lp = -scores_at(o["Qs"][k], o["Xs"], gi[k], "l2")
+        lp_err.append(np.abs(lp - ex) / (np.abs(ex) + 1e-30))
+        f_err.append(np.abs(gv[k] - ex) / (np.abs(ex) + 1e-30))
+    lp_err, f_err = np.concatenate(lp_err), np.concatenate(f_err)
+    print("mix_l2_1m %s: recall@10 vs exact FP32 %.4f (oracle %.4f); relative error vs FP64 "
+          "of the BF16 distance max %.2e mean %.2e, of the returned value max %.2e mean %.2e"
+          % (bins, rec, orec, lp_err.max(), lp_err.mean(), f_err.max(), f_err.mean()))
+    assert abs(rec - orec) <= 0.02
+    assert rec >= 0.95
+    assert f_err.max() < 1e-5
+
+
+# ----------------------------------------------------------------------------
+# FP8-E4M3 / cosine / 10M x 96
+# ----------------------------------------------------------------------------
+N_SAMPLED_E4M3 = 32
+
+
+def e4m3_stored(Xc):
+    """What the GPU contracts: E4M3 codes x row scale of the unit rows."""
+    return oracle.e4m3_rows(oracle.normalize_rows(Xc))[0]
+
+
+def e4m3_10m_oracle_side(L, Kp, w=None):
+    w = w or synth.workload("mix_cos_10m")
+    X, Q, K = w["X"], w["Q"], w["K"]
+    N, M = X.shape[0], Q.shape[0]
+    assert CHUNK % L == 0
+    samp = np.sort(rng(9).choice(M, size=N_SAMPLED_E4M3, replace=False))
+    Qn = oracle.normalize_rows(Q[samp])
+    Qs, qsc = oracle.e4m3_rows(Qn)
     V = A = None
-    for c0 in range(0, X.shape[0], CHUNK):
-        assert c0 % L == 0
-        Xc = Qs_fn(X[c0:c0 + CHUNK])
-        v, a = oracle.partial_reduce(Qs_fn.q, Xc, L, metric)
+    best = second = None
+    for c0 in range(0, N, CHUNK):
+        Xc = e4m3_stored(X[c0:c0 + CHUNK])
+        v, a = oracle.partial_reduce(Qs, Xc, L, "ip")
         a = np.where(a >= 0, a + c0, -1)
         if V is None:
             V, A = v, a
         else:
             better = v > V          # equal keeps the earlier (smaller) row
-            V = np.where(better, v, V)
-            A = np.where(better, a, A)
-    return V, A
+            V, A = np.where(better, v, V), np.where(better, a, A)
+        b, s = PT.bin_best_second(Qs @ Xc.T, L)
+        if best is None:
+            best, second = b, s
+        else:
+            best, second = (np.maximum(best, b),
+                            np.maximum(np.maximum(second, s), np.minimum(best, b)))
+        del Xc
+    _, cand = oracle.topk_pairs(V, A, Kp)
+    # FP32 re-rank on the unit rows of the candidates only
+    uniq, inv = np.unique(cand[cand >= 0], return_inverse=True)
+    Xsub = oracle.normalize_rows(X[uniq])
+    csub = np.full(cand.shape, -1, np.int64)
+    csub[cand >= 0] = inv
+    ov, oi_sub = oracle.rerank(Qn, Xsub, csub, K, "ip")
+    oi = np.where(oi_sub >= 0, uniq[np.maximum(oi_sub, 0)], -1)
+    cf = np.full(cand.shape, -np.inf)
+    for k in range(len(samp)):
+        ok = csub[k] >= 0
+        cf[k, ok] = Xsub[csub[k, ok]].astype(np.float64) @ Qn[k].astype(np.float64)
+    # the E4M3 kernel's packed key keeps the top bits of each FP32 score: its
+    # values are within 2^-9 of their magnitude (scores here are below 1)
+    tol_d = 2.0 ** -9 * np.ones(len(samp)) + 3e-5
+    tol_f = 3e-5 * np.ones(len(samp))
+    decided = PT.decided_from_stats(best, second, Kp, cf, K, tol_d, tol_f)
+    return dict(X=X, Q=Q, K=K, samp=samp, Qn=Qn, Qs=Qs, qsc=qsc, V=V, A=A, cand=cand, ov=ov,
+                oi=oi, best=best, second=second, tol_d=tol_d, tol_f=tol_f, decided=decided)
+
+
+@pytest.mark.gpu
+def test_e4m3_cosine_10m_k100_elementwise():
+    from paper_2206_14286_gb300 import search as S
+    w = synth.workload("mix_cos_10m")
+    X, Q, K = w["X"], w["Q"], w["K"]
+    N, D = X.shape
+    M = Q.shape[0]
+    L = S.plan_bins(N, K, 0.95, round_to=128)
+    rr = w["rerank"]
+    Kp = min(rr * K, L)
+    assert L == 2048 and CHUNK % L == 0
+    d = db(X, "cos", "e4m3")
+    val, idx = d.search(dev(Q), K, L=L, rerank=rr)
+    Vg, Ag = d.partial_reduce(dev(Q), L)
+    gv_all, gi_all = host(val), host(idx)
+    assert gi_all.shape == (M, K) and np.all((gi_all >= 0) & (gi_all < N))
+    assert all(len(set(r)) == K for r in gi_all[:200])
+    assert np.all(np.diff(gv_all, axis=1) <= 0)
+    o = e4m3_10m_oracle_side(L, Kp, w)
+    samp = o["samp"]
+    gv, gi = gv_all[samp], gi_all[samp]
+    Vg, Ag = host(Vg)[samp].astype(np.float64), host(Ag)[samp].astype(np.int64)
+    S.sync_status()
+    del d
+    torch.cuda.empty_cache()
+
+    # PartialReduce bin by bin (the kernel leaves the per-query scale out of
+    # its values: multiply it back)
+    Vg_s = Vg * o["qsc"][:, None].astype(np.float64)
+    assert np.all(Ag % L == np.arange(L)[None, :])
+    dec_bin = (o["best"] - o["second"]) > 2 * o["tol_d"][:, None]
+    np.testing.assert_array_equal(Ag[dec_bin], o["A"][dec_bin])
+    assert np.all(np.abs(Vg_s - o["V"]) <= o["tol_d"][:, None]), np.abs(Vg_s - o["V"]).max()
+    print("mix_cos_10m: %d sampled queries x %d bins, %.4f of bins decided"
+          % (len(samp), L, dec_bin.mean()))
+
+    def lp_at(i, j):
+        return e4m3_stored(X[j]) @ o["Qs"][i]
+
+    def f_at(i, j):
+        return oracle.normalize_rows(X[j]).astype(np.float64) @ o["Qn"][i].astype(np.float64)
+
+    tol = np.maximum(o["tol_d"], o["tol_f"])
+    frac = PT.check_search_core(gv, gi, o["ov"], o["oi"], lp_at, f_at, o["best"],
+                                lambda j: j % L, "ip", tol, o["decided"])
+    agree = np.mean([len(set(gi[k]) & set(o["oi"][k])) / K for k in range(len(samp))])
+    print("mix_cos_10m: decided queries %.3f; returned rows shared with the oracle %.4f"
+          % (frac, agree))
+    # every returned value is the FP32 cosine of its own row
+    for k in range(len(samp)):
+        np.testing.assert_allclose(gv[k], f_at(k, gi[k]), rtol=0, atol=1e-5)
+    # recall@100 against the exact FP32 cosine top-100, and score errors
+    _, ei = chunked_exact(o["Qn"], X, K, "ip", oracle.normalize_rows)
+    rec = np.mean([len(set(gi[k]) & set(ei[k])) / K for k in range(len(samp))])
+    orec = np.mean([len(set(o["oi"][k]) & set(ei[k])) / K for k in range(len(samp))])
+    lp_err = np.concatenate([np.abs(lp_at(k, gi[k]) - f_at(k, gi[k])) for k in range(len(samp))])
+    print("mix_cos_10m K=%d L=%d K'=%d: recall@100 vs exact FP32 %.4f (oracle %.4f); "
+          "|E4M3 cosine - FP64 cosine| max %.2e mean %.2e"
+          % (K, L, Kp, rec, orec, lp_err.max(), lp_err.mean()))
+    assert abs(rec - orec) <= 0.03
+    assert rec >= 0.95, rec
 
 
 def chunked_exact(Q, X, K, metric, prep):
@@ -48,61 +301,3 @@ def chunked_exact(Q, X, K, metric, prep):
     i = np.concatenate(idxs, 1)
     order = np.lexsort((i, -v), axis=1)
     return np.take_along_axis(v, order, 1)[:, :K], np.take_along_axis(i, order, 1)[:, :K]
-
-
-def test_e4m3_cosine_10m_k100_sampled():
-    from paper_2206_14286_gb300 import search as S
-    w = synth.workload("mix_cos_10m")
-    X, Q, K = w["X"], w["Q"], w["K"]
-    N, D = X.shape
-    M = Q.shape[0]
-    L = S.plan_bins(N, K, 0.95, round_to=128)
-    assert L == 2048 and CHUNK % L == 0
-    d = db(X, "cos", "e4m3")
-    val, idx = d.search(dev(Q), K, L=L, rerank=2)
-    gv, gi = host(val), host(idx)
-    assert gi.shape == (M, K) and np.all((gi >= 0) & (gi < N))
-    # the GPU returns distinct rows, best first
-    assert all(len(set(r)) == K for r in gi[:200])
-    assert np.all(np.diff(gv, axis=1) <= 0)
-    del d
-    torch.cuda.empty_cache()
-
-    samp = np.random.Generator(np.random.PCG64(9)).choice(M, size=6, replace=False)
-    Qn = oracle.normalize_rows(Q[samp])
-    Qs, _ = oracle.e4m3_rows(Qn)
-
-    def stored_rows(Xc):            # what the GPU contracts: E4M3 codes x row scale
-        return oracle.e4m3_rows(oracle.normalize_rows(Xc))[0]
-    stored_rows.q = Qs
-    V, A = chunked_partial_reduce(stored_rows, X, L, "ip")
-    _, cand = oracle.topk_pairs(V, A, 2 * K)
-    # FP32 re-rank on the unit rows of the candidates only
-    uniq, inv = np.unique(cand[cand >= 0], return_inverse=True)
-    Xsub = oracle.normalize_rows(X[uniq])
-    csub = np.full(cand.shape, -1, np.int64)
-    csub[cand >= 0] = inv
-    ov, oi_sub = oracle.rerank(Qn, Xsub, csub, K, "ip")
-    oi = np.where(oi_sub >= 0, uniq[np.maximum(oi_sub, 0)], -1)
-
-    # the GPU's answer for each sampled query against the oracle's
-    agree = np.mean([len(set(gi[s]) & set(oi[k])) / K for k, s in enumerate(samp)])
-    assert agree > 0.97, agree
-    # values: FP32 cosines of the same rows
-    np.testing.assert_allclose(np.sort(gv[samp], 1), np.sort(ov, 1), rtol=0, atol=2e-3)
-    # every returned value is the FP32 cosine of its own row
-    for k, s in enumerate(samp):
-        own = oracle.normalize_rows(X[gi[s]]).astype(np.float64) @ Qn[k].astype(np.float64)
-        np.testing.assert_allclose(gv[s], own, rtol=0, atol=1e-5)
-    # recall@100 against the exact FP32 cosine top-100. Reported, with a floor:
-    # the bin step ranks by E4M3 scores (3 mantissa bits), and among the
-    # near-tied neighbours of a 1024-centre mixture that choice often differs
-    # from FP32's inside a bin, which no re-rank recovers (measured 0.755 on
-    # these six queries; the oracle's own E4M3 search agrees with the GPU above).
-    _, ei = chunked_exact(Qn, X, K, "ip", oracle.normalize_rows)
-    rec = np.mean([len(set(gi[s]) & set(ei[k])) / K for k, s in enumerate(samp)])
-    orec = np.mean([len(set(oi[k]) & set(ei[k])) / K for k in range(len(samp))])
-    print("E4M3 cosine 10M x 96, K=100, L=%d: recall@100 vs FP32 exact %.3f (oracle %.3f)"
-          % (L, rec, orec))
-    assert abs(rec - orec) <= 0.03
-    assert rec >= 0.6, rec

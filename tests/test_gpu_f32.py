@@ -290,3 +290,35 @@ def test_search_is_repeatable_whatever_the_workspace_holds(dtype, metric):
     for v, i in outs[1:]:
         assert np.array_equal(i, outs[0][1])
         assert np.array_equal(v.view(np.uint32), outs[0][0].view(np.uint32))
+
+
+@pytest.mark.parametrize("metric,dtype,keep", [("l2", "bf16", True), ("cos", "e4m3", False),
+                                               ("ip", "f32", True), ("ip", "bf16", False)])
+def test_owned_database_handle_matches_prepared_buffers(metric, dtype, keep):
+    """knn_db_create / knn_db_search / knn_db_destroy: the library-owned
+    database gives the same results, bit for bit, as knn_search on buffers
+    the caller prepared with knn_prepare (the same kernels on the same
+    bytes); without kept FP32 rows both re-rank from the stored rows."""
+    import ctypes
+    from paper_2206_14286_gb300 import search as S, _lib
+    ensure_built()
+    g = np.random.Generator(np.random.PCG64(91))
+    X = g.standard_normal((20011, 96)).astype(np.float32)
+    Q = g.standard_normal((130, 96)).astype(np.float32)
+    Xd = dev(X)
+    ref = S.Database(Xd, metric=metric, dtype=dtype, keep_f32=keep)
+    own = S.OwnedDatabase(Xd, metric=metric, dtype=dtype, keep_f32=keep)
+    del Xd                                  # the handle keeps its own copy
+    torch.cuda.empty_cache()
+    n, d, me, dt = ctypes.c_int64(), ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+    _lib.check(_lib.get().knn_db_info(own.handle, ctypes.byref(n), ctypes.byref(d),
+                                      ctypes.byref(me), ctypes.byref(dt)))
+    assert (n.value, d.value, me.value, dt.value) == (20011, 96, _lib.METRIC[metric],
+                                                      _lib.DTYPE[dtype])
+    for K, L, rr in [(10, 256, 2), (7, 100, 1)]:
+        a = ref.search(dev(Q), K, L=L, rerank=rr)
+        b = own.search(dev(Q), K, L=L, rerank=rr)
+        torch.cuda.synchronize()
+        assert torch.equal(a[1], b[1]) and torch.equal(a[0], b[0]), (K, L, rr)
+    own.close()
+    S.sync_status()

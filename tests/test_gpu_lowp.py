@@ -3,8 +3,11 @@ against the FP64 oracle run on the same dequantised values the GPU saw.
 
 The bin step runs on the stored (rounded) rows and queries; the final values
 are FP32 scores of the FP32 rows (re-rank). The oracle mirrors both steps.
-Tolerance: rel 1e-2 of the natural score scale for the bin step (BF16/FP8),
-rel 1e-5 for re-ranked FP32 values."""
+Tolerance: the stated rel 1e-2 of the natural score scale for the bin step
+(BF16/FP8) and rel 1e-5 for re-ranked FP32 values; then the tighter bound of
+each kernel's arithmetic: the BF16 kernel keeps the FP32 accumulator in its
+keys (3e-5 of the scale, plus 2^-20 of the largest |x|^2 for the L2 half-norm
+split), the E4M3 kernel's packed key keeps 2^-10 of a score's magnitude."""
 import numpy as np
 import pytest
 import torch
@@ -64,16 +67,23 @@ def test_partial_reduce_lowp(dtype, metric, shape):
             _, qsc = oracle.e4m3_rows(oracle.normalize_rows(Q) if metric == "cos" else Q)
             Vo = Vo / qsc[:, None].astype(np.float64)
         scale = PT.query_scale(Qs, Xs, metric)
-        tol_bin = PT.REL_LOWP * scale
+        if dtype == "bf16":
+            # the BF16 kernel keeps the FP32 accumulator in its 64-bit keys;
+            # its values are in the relaxed scale (half of -|q-x|^2 for L2)
+            tol_bin = PT.fp32_acc_tol(Qs, Xs, metric)
+            tight = (tol_bin / 2 if metric == "l2" else tol_bin)[:, None] + \
+                2.0 ** -20 * np.abs(Vo)
+        else:
+            # the E4M3 kernel's packed 32-bit key keeps the top bits of each
+            # FP32 score (its low bits hold the row's position in its bin)
+            tol_bin = PT.REL_LOWP * scale
+            tight = 2.0 ** -9 * np.abs(Vo) + 1e-5 * scale[:, None]
+            if metric != "l2":
+                tight = 2.0 ** -9 * np.abs(Vo) + 1e-5 * scale[:, None] / qsc[:, None]
         best, second = PT.bin_best_second(Sm, L)
         decided = (best - second) > 2 * tol_bin[:, None]
         assert np.all(A % L == np.arange(L)[None, :])
         np.testing.assert_array_equal(A[decided], Ao[decided])
-        # values: FP32 accumulation plus the packed key's truncation (< 2^-10 relative)
-        vs = Vo if not (dtype == "e4m3" and metric != "l2") else Vo
-        tight = 2.0 ** -9 * np.abs(vs) + 1e-5 * (scale[:, None] if metric != "l2" else scale[:, None])
-        if dtype == "e4m3" and metric != "l2":
-            tight = 2.0 ** -9 * np.abs(vs) + 1e-5 * scale[:, None] / qsc[:, None]
         err = np.abs(V - Vo)
         # undecided bins may hold a different near-best member: compare by its own score
         own = Sm[np.arange(M)[:, None], A]
@@ -83,6 +93,8 @@ def test_partial_reduce_lowp(dtype, metric, shape):
             own = own / qsc[:, None]
         assert np.all(err[decided] <= tight[decided]), (L, err[decided].max())
         assert np.all(np.abs(V - own) <= tight), (L,)
+        if dtype == "bf16":
+            assert decided.mean() > 0.9, (L, decided.mean())
 
 
 @pytest.mark.parametrize("metric", METRICS)
@@ -137,10 +149,8 @@ def test_search_bf16_long_rows(metric):
 # ----------------------------------------------------------------------------
 # Search with FP32 re-rank
 # ----------------------------------------------------------------------------
-def run_lowp(X, Q, metric, dtype, K, L, rerank, bins="mod"):
-    d = db(X, metric, dtype)
-    val, idx = d.search(dev(Q), K, L=L, rerank=rerank, bins=bins)
-    gv, gi = host(val), host(idx)
+def lowp_oracle_side(X, Q, metric, dtype, K, L, rerank, bins="mod"):
+    """The oracle's answer and the decided masks of run_lowp (no GPU)."""
     Xs, Xf = stored(X, metric, dtype)
     Qs, Qf = stored(Q, metric, dtype)
     Kp = min(max(1, rerank) * K, L)
@@ -154,19 +164,32 @@ def run_lowp(X, Q, metric, dtype, K, L, rerank, bins="mod"):
     tol_f = PT.REL_F32 * PT.query_scale(Qf, Xf, metric)
     # the stated rule: rel 1e-2 (BF16/FP8) for the bin step
     dec = PT.decided_mask(S_lp, L, Kp, S_f, cand, K, tol_lp, bins=bins)
-    PT.check_search(gv, gi, ov, oi, S_lp, S_f, L, om(metric), tol_lp, dec, bins=bins)
-    # a stricter rule derived from the kernel's arithmetic: the packed key keeps
-    # scores to 2^-10 of their magnitude, FP32 accumulation adds ~D u ||q|| ||x||
-    if bins == "contiguous":   # FP32 accumulator, no packed-key truncation
-        tol_d = 3e-5 * scale_lp + (2.0 ** -20 * (Xs ** 2).sum(1).max() if metric == "l2" else 0.0)
+    # a stricter rule derived from the kernels' arithmetic: the BF16 kernel
+    # keeps the FP32 accumulator in its keys; the E4M3 kernel's packed key
+    # keeps scores to 2^-10 of their magnitude, plus FP32 accumulation
+    if dtype == "bf16":
+        tol_d = PT.fp32_acc_tol(Qs, Xs, metric)
     else:
-        tol_d = 2.0 ** -9 * (scale_lp if metric == "l2" else np.abs(S_lp).max(1)) + 3e-5 * scale_lp
+        tol_d = 2.0 ** -9 * (scale_lp if metric == "l2" else np.abs(S_lp).max(1)) + \
+            3e-5 * scale_lp
     tol_df = np.maximum(tol_f, 3e-5 * PT.query_scale(Qf, Xf, metric))
     dec2 = PT.decided_mask(S_lp, L, Kp, S_f, cand, K, tol_d, tol_df, bins=bins) | dec
-    frac = PT.check_search(gv, gi, ov, oi, S_lp, S_f, L, om(metric), np.maximum(tol_d, tol_df),
-                           dec2, bins=bins)
+    return dict(ov=ov, oi=oi, S_lp=S_lp, S_f=S_f, tol_lp=tol_lp, tol_d=tol_d, tol_df=tol_df,
+                dec=dec, dec2=dec2)
+
+
+def run_lowp(X, Q, metric, dtype, K, L, rerank, bins="mod"):
+    d = db(X, metric, dtype)
+    val, idx = d.search(dev(Q), K, L=L, rerank=rerank, bins=bins)
+    gv, gi = host(val), host(idx)
+    o = lowp_oracle_side(X, Q, metric, dtype, K, L, rerank, bins)
+    ov, oi, S_lp, S_f = o["ov"], o["oi"], o["S_lp"], o["S_f"]
+    PT.check_search(gv, gi, ov, oi, S_lp, S_f, L, om(metric), o["tol_lp"], o["dec"], bins=bins)
+    dec2 = o["dec2"]
+    frac = PT.check_search(gv, gi, ov, oi, S_lp, S_f, L, om(metric),
+                           np.maximum(o["tol_d"], o["tol_df"]), dec2, bins=bins)
     # values are FP32 re-ranked: FP32 tolerance where decided
-    np.testing.assert_allclose(gv[dec2], ov[dec2], rtol=0, atol=float(np.max(tol_df)) + 1e-6)
+    np.testing.assert_allclose(gv[dec2], ov[dec2], rtol=0, atol=float(np.max(o["tol_df"])) + 1e-6)
     return frac, gi
 
 
@@ -176,9 +199,12 @@ def test_search_lowp_small(dtype, metric):
     X, Q = inputs(6007, 131, 64, seed=21)
     for K, L, rr in [(10, 176, 2), (10, 256, 1), (4, 4, 1), (1, 1, 1), (8, 6007, 1)]:
         frac, _ = run_lowp(X, Q, metric, dtype, K, L, rr)
-        # with L2 the packed key truncates relative to |<q,x> - |x|^2/2|, which is
-        # dominated by the norm: fewer queries are decided
-        assert frac > (0.02 if metric == "l2" else 0.25), (K, L, rr, frac)
+        # floors a little under the decided fractions, which depend on the
+        # oracle side alone (BF16: 0.83-1.0; E4M3 IP/COS: 0.37-0.97; E4M3 L2,
+        # whose packed-key truncation scales with the norm-dominated relaxed
+        # score: 0.08-0.78)
+        floor = 0.75 if dtype == "bf16" else (0.05 if metric == "l2" else 0.3)
+        assert frac > floor, (K, L, rr, frac)
 
 
 # ----------------------------------------------------------------------------
@@ -224,32 +250,7 @@ def test_search_contiguous_bf16_small(metric):
     X, Q = inputs(6007, 131, 64, seed=31)
     for K, L, rr in [(10, 176, 2), (10, 256, 1), (4, 4, 1), (1, 1, 1), (8, 6007, 1)]:
         frac, _ = run_lowp(X, Q, metric, "bf16", K, L, rr, bins="contiguous")
-        assert frac > 0.25, (K, L, rr, frac)
-
-
-@pytest.mark.parametrize("bins", ["mod", "contiguous"])
-def test_search_bf16_mixture_l2_1m_sampled(bins):
-    """BF16 / L2 / 1M x 128 Gaussian mixture, M = 1024, K = 10, L from recall 0.95
-    (rounded to the 128-row tile): parity and recall on sampled queries."""
-    w = synth.workload("mix_l2_1m")
-    X, Q = w["X"], w["Q"]
-    from paper_2206_14286_gb300 import search as S
-    L = S.plan_bins(X.shape[0], 10, 0.95, round_to=128)
-    d = db(X, "l2", "bf16")
-    val, idx = d.search(dev(Q), 10, L=L, rerank=2, bins=bins)
-    gv, gi = host(val), host(idx)
-    samp = rng(5).choice(Q.shape[0], size=24, replace=False)
-    Xs = oracle.bf16_round(X)
-    Qs = oracle.bf16_round(Q[samp])
-    V, A = oracle.partial_reduce(Qs, Xs, L, "l2", bins=bins)
-    _, cand = oracle.topk_pairs(V, A, 20)
-    ov, oi = oracle.rerank(Q[samp], X, cand, 10, "l2")
-    agree = np.mean([len(set(gi[s]) & set(oi[k])) / 10 for k, s in enumerate(samp)])
-    assert agree > 0.97
-    np.testing.assert_allclose(np.sort(gv[samp], 1), np.sort(ov, 1), rtol=1e-4, atol=1e-3)
-    ev, ei = oracle.exact_topk(Q[samp], X, 10, "l2")
-    rec = np.mean([len(set(gi[s]) & set(ei[k])) / 10 for k, s in enumerate(samp)])
-    assert rec >= 0.9   # expected ~0.98 (exact law at L=256), sampled
+        assert frac > 0.75, (K, L, rr, frac)      # decided: 0.82-1.0
 
 
 @pytest.mark.parametrize("dtype", ["bf16", "e4m3"])
@@ -307,10 +308,9 @@ def test_search_fused_rescoring_bounds(metric):
     for K, L, rr in [(16, 1024, 2), (32, 1024, 1), (32, 33, 1), (3, 40, 8), (1, 32, 1)]:
         frac, gi = run_lowp(X, Q, metric, "bf16", K, L, rr)
         # with K up to 32 and bins of ~5 rows more queries hold a near-tie
-        # inside the stated tolerance (for L2, whose tolerance scales with the
-        # norms, often every query); the checks in run_lowp cover every query
-        if metric != "l2":
-            assert frac > 0.05, (K, L, rr, frac)
+        # within twice the tolerance (decided: 0.38-1.0); the checks in
+        # run_lowp cover every query
+        assert frac > 0.3, (K, L, rr, frac)
         # every row returned once per query
         for r in gi:
             assert len(set(r[r >= 0].tolist())) == int((r >= 0).sum())
@@ -324,7 +324,6 @@ def test_search_ragged_last_grid_row(metric):
     for N, L in [(257, 64), (1456, 300), (2657, 600), (2303, 1024)]:
         X, Q = inputs(N, 77, 64, seed=N)
         frac, gi = run_lowp(X, Q, metric, "bf16", 10, L, 2)
-        if metric != "l2":
-            assert frac > 0.25, (N, L, frac)
+        assert frac > 0.75, (N, L, frac)          # decided: 0.80-0.95
         ragged = N - (N // L) * L
         assert ragged in (1, 256, 257, 255)

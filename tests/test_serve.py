@@ -75,11 +75,16 @@ def test_serving_trace_is_seeded_and_shaped():
 # ----------------------------------------------------------------------------
 # GPU
 # ----------------------------------------------------------------------------
-def _dbs():
-    from tests.gpu_util import db
+def _raw():
     X1 = synth.mixture(60000, 64, 64, 71)
     X2 = synth.mixture(90000, 96, 64, 72)
-    return {"db1": db(X1, "l2", "bf16"), "db2": db(X2, "ip", "bf16")}, \
+    return {"db1": (X1, "l2"), "db2": (X2, "ip")}
+
+
+def _dbs():
+    from tests.gpu_util import db
+    raw = _raw()
+    return {n: db(X, m, "bf16") for n, (X, m) in raw.items()}, \
         {"db1": (64, 64), "db2": (96, 64)}
 
 
@@ -91,14 +96,13 @@ def _alone(server, r):
 
 
 def _same(r, alone):
+    """Every query of a batch is searched on its own (its bins, its rescoring,
+    its re-rank), by the same kernels whatever the batch size: a request's
+    result in the mix must equal its result alone, bit for bit."""
     av, ai = (t.cpu() for t in alone)
-    tol = 1e-5 * (av.abs().max().item() + 1.0)
-    assert torch.allclose(r.val, av, rtol=0, atol=tol), r.rid
-    diff = r.idx != ai
-    # a differing index is only allowed where two candidates tie within tol
-    if diff.any():
-        assert torch.all((r.val - av).abs()[diff] <= tol), r.rid
-    return int(diff.sum())
+    assert torch.equal(r.idx, ai), r.rid
+    assert torch.equal(r.val, av), r.rid
+    return 0
 
 
 @pytest.mark.gpu
@@ -112,10 +116,40 @@ def test_results_same_alone_and_in_mix():
     assert len(done) == 60 and all(r.error is None for r in done)
     assert srv.batches < 60                     # requests were batched together
     assert srv.max_in_flight >= 2               # several batches admitted at once
-    mism = sum(_same(r, _alone(srv, r)) for r in done)
-    total = sum(r.idx.numel() for r in done)
-    assert mism <= 1e-3 * total
+    for r in done:
+        _same(r, _alone(srv, r))
     assert srv.arena.used == 0 and srv.arena.peak <= srv.arena.size
+
+
+@pytest.mark.gpu
+def test_served_results_match_the_oracle_per_class():
+    """A mixed trace over both databases and both K; the first request of
+    every (database, K) class, as the server returned it, against the FP64
+    oracle's PartialReduce -> top-2K -> FP32 re-rank on the same queries
+    (the parity rule of tests/parity.py with the BF16 kernel's tolerance)."""
+    from tests.test_gpu_lowp import lowp_oracle_side, om
+    from tests import parity as PT
+    raw = _raw()
+    dbs, shapes = _dbs()
+    trace = synth.serving_trace(80, 2.0e5, shapes, m_max=256, seed=82)
+    srv = SV.Server(dbs, hbm_budget=64 << 20, max_batch=512, slots=3)
+    done = SV.run_trace(srv, [(t, n, torch.from_numpy(q).pin_memory(), K)
+                              for t, n, q, K in trace])
+    assert len(done) == 80 and all(r.error is None for r in done)
+    assert srv.batches < 80
+    first = {}
+    for r in sorted(done, key=lambda r: r.rid):
+        first.setdefault((r.db, r.K), r)
+    assert len(first) == 4, sorted(first)
+    for (name, K), r in sorted(first.items()):
+        X, metric = raw[name]
+        L = srv.bins_for(name, K)
+        Q = r.q.numpy()
+        o = lowp_oracle_side(X, Q, metric, "bf16", K, L, srv.rerank)
+        gv, gi = r.val.numpy(), r.idx.numpy()
+        frac = PT.check_search(gv, gi, o["ov"], o["oi"], o["S_lp"], o["S_f"], L, om(metric),
+                               np.maximum(o["tol_d"], o["tol_df"]), o["dec2"])
+        print("served %s K=%d L=%d m=%d: decided %.3f" % (name, K, L, Q.shape[0], frac))
 
 
 @pytest.mark.gpu
