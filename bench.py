@@ -7,16 +7,26 @@ re-rank to the top K. Default workload: 1,000,000 x 128 database rows from a
 256-centre Gaussian mixture, 1024 queries from the same mixture, L2 metric,
 K = 10, L from the recall law for 0.95 rounded up to the 128-row tile.
 
-Reported beside it: the plain FP32 path (SIMT contraction, same workload),
-recall@10 against the exact FP32 search, p50/p99 step latency, the end-to-end
-rate through the host-buffer entry point, the dominant kernel's roofline and
-the FP64 CPU oracle timed on a bounded sample.
+Reported beside it:
+  * the plain FP32 path (SIMT contraction, same workload) with its roofline;
+  * recall@10 against the exact FP32 search, p50/p99 step latency, the
+    end-to-end rate through the host-buffer entry point, CUDA-graph replay;
+  * the dominant kernel's roofline, and the paper's three-roof bound (Eq. 6)
+    with gamma and the FFMA rate measured by microbenchmarks and C from the
+    kernel's ncu instruction count;
+  * score errors against FP64 on the original FP32 data;
+  * the other workloads: FP8-E4M3 cosine 10M x 96 (K = 100) and the
+    1M x 256 BF16 forward + backward (K = 32);
+  * the serving loop over two resident databases (p50/p99);
+  * the unfused GEMM -> HBM -> approx_max_k comparison (App. A.6);
+  * the FP64 CPU oracle timed on bounded samples (all cores and one core).
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 Multi-GPU (torchrun): every rank runs an independent replica (the search does
 not shard on one box); the value is the total over ranks.
 """
 import argparse
+import ctypes
 import hashlib
 import json
 import os
@@ -31,7 +41,13 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
+METRIC = "queries/s at recall@10≥0.95 (fused BF16 vs plain FP32) and % of roofline; p99 ms"
 PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
+# nominal dense tensor rates per GPU (PFLOP/s): FP8 / BF16 = 4.5 / 2.25
+FP8_PER_BF16 = 2.0
+# nominal FP32 CUDA-core rate: 152 SMs x 128 FMA lanes x 2 FLOP x 2.07 GHz
+FFMA_NOMINAL_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+KERNEL_CLASSES = ["prep", "k1", "k2", "k3"]
 
 
 def parse():
@@ -46,28 +62,13 @@ def parse():
     ap.add_argument("--bins", default="mod", choices=["mod", "contiguous"])
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-unfused", action="store_true")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="skip the E4M3 10M and the 1M x 256 backward workloads")
+    ap.add_argument("--config-steps", type=int, default=10)
     ap.add_argument("--serving-requests", type=int, default=1200)
     ap.add_argument("--serving-rates", default="1500,6000",
                     help="offered requests/s, one trace per rate")
     return ap.parse_args()
-
-
-def eq6_block(M, N, D, k1_ms, pk, bytes_moved):
-    """The paper's three-roof bound (Eq. 6) for K1 on this GPU: pi and beta
-    measured, gamma from unit counts x clock (ALU pipe), C from the kernel's
-    design: one compare per 16-score maximum (tcgen05.ld.red), plus the
-    searches of new bests, which depend on the data and are not counted."""
-    from paper_2206_14286_gb300 import roofline as RF
-    C = 1.0 / 16.0
-    r = RF.report(M, N, D, k1_ms / 1e3, pk["bf16_tflops"] * 1e12, pk["hbm_gbs"] * 1e9,
-                  RF.gb300_gamma("alu"), C, bytes_moved)
-    return {"C_design_alu_cops_per_score": C, "I_MEM_flop_per_byte": r["I_MEM"],
-            "I_COP_flop_per_cop": r["I_COP"],
-            "roofs_tflops": {k: v / 1e12 for k, v in r["roofs"].items()},
-            "binding": r["binding"], "fraction_of_attainable": r["fraction_of_attainable"],
-            "gamma_alu_tcops": RF.gb300_gamma("alu") / 1e12,
-            "cop_budget_per_score": RF.cop_budget(D, RF.gb300_gamma("alu"),
-                                                  pk["bf16_tflops"] * 1e12)}
 
 
 def job_rate(world, units_per_rank, local_ms, device=None):
@@ -168,6 +169,188 @@ class OracleRunner:
         return int(max(8, min(cap, seconds / max(t / 8, 1e-6))))
 
 
+def cpu_baseline(w, L, K, bins, seconds=4.0):
+    """The oracle on all host cores and on one core: three runs each on a
+    bounded sample of the queries (about `seconds` each), median."""
+    import oracle
+    oracle.build()
+    runner = OracleRunner(w, L, K, bins)
+    M, N = w["Q"].shape[0], w["X"].shape[0]
+    cores = oracle.set_threads(0)
+    try:
+        n_all = runner.size_for(seconds, M)
+        t_all = statistics.median(runner.run(n_all) for _ in range(3))
+        oracle.set_threads(1)
+        n_one = runner.size_for(seconds, M)
+        t_one = statistics.median(runner.run(n_one) for _ in range(3))
+    finally:
+        oracle.set_threads(cores)
+    return {"value": n_all / t_all, "unit": "queries/s", "cores": cores, "kind": "oracle",
+            "sample": "%d of the %d queries against the full %d-row database (FP64), "
+                      "median of 3 runs of %.1f s" % (n_all, M, N, t_all),
+            "single_thread": {"value": n_one / t_one, "unit": "queries/s", "cores": 1,
+                              "sample": "%d queries, median of 3 runs of %.1f s"
+                                        % (n_one, t_one)}}
+
+
+# ----------------------------------------------------------------------------
+# helpers on the GPU side
+# ----------------------------------------------------------------------------
+def timed(fn, steps, warmup=2):
+    """Mean ms per call of fn over `steps` calls, CUDA events on the current stream."""
+    import torch
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(steps):
+        fn()
+    b.record()
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / steps
+
+
+def profiled(lib, fn, reps):
+    """Per kernel class of the library (query prep, K1, K2, K3): mean ms per
+    launch and launches, from the library's event profiler on fn's stream."""
+    import torch
+    from paper_2206_14286_gb300 import _lib
+    _lib.check(lib.knn_profile_enable(1))
+    for _ in range(reps):
+        fn()
+    torch.cuda.synchronize()
+    _lib.check(lib.knn_profile_enable(0))
+    out = {}
+    for c, name in enumerate(KERNEL_CLASSES):
+        tot = ctypes.c_double()
+        n = ctypes.c_int64()
+        _lib.check(lib.knn_profile_read(c, ctypes.byref(tot), ctypes.byref(n)))
+        out[name] = {"ms_avg": tot.value / max(1, n.value), "launches": n.value}
+    return out
+
+
+def measure_rates(lib):
+    """gamma (compare/select COPs per second) and the FP32 FFMA rate of this
+    GPU, from the library's issue-rate microbenchmarks."""
+    from paper_2206_14286_gb300 import _lib
+    out = {}
+    for name in ("minmax", "ffma"):
+        r, ms = ctypes.c_double(), ctypes.c_double()
+        _lib.check(lib.knn_measure_rate(_lib.RATE[name], 4096, ctypes.byref(r), ctypes.byref(ms),
+                                        None))
+        out[name] = {"ops_per_s": r.value, "ms": ms.value}
+    return {"gamma_cops": out["minmax"]["ops_per_s"],
+            "ffma_tflops": 2.0 * out["ffma"]["ops_per_s"] / 1e12,
+            "how": "knn_measure_rate: FP32 min/max (gamma) and FFMA issue rates, 16 chains per "
+                   "thread, 2048 threads per SM, CUDA events",
+            "kernel_ms": {k: v["ms"] for k, v in out.items()}}
+
+
+def scaled_mm_tflops():
+    """Dense E4M3 GEMM rate of the library GEMM at 8192^3 (context for the
+    FP8 roof; the roof itself is the measured BF16 peak x the nominal ratio)."""
+    import torch
+    try:
+        n = 8192
+        a = torch.randn(n, n, device="cuda").to(torch.float8_e4m3fn)
+        b = torch.randn(n, n, device="cuda").to(torch.float8_e4m3fn).t()
+        one = torch.ones((), device="cuda")
+        ms = timed(lambda: torch._scaled_mm(a, b, scale_a=one, scale_b=one,
+                                            out_dtype=torch.bfloat16), 10, 3)
+        del a, b
+        return 2.0 * n ** 3 / (ms / 1e3) / 1e12
+    except (RuntimeError, TypeError, AttributeError) as e:
+        return "unavailable: " + str(e)[:120]
+
+
+def prepared_rows(d, rows):
+    """FP64 values the contraction sees for the rows `rows` (CUDA int64
+    tensor) of a prepared Database: BF16, E4M3 x scale, or FP32, decoded from
+    the stored bytes."""
+    import torch
+    esz = {"f32": 4, "bf16": 2, "e4m3": 1}[d.dtype]
+    b = d.lp.view(d.N, d.pitch * esz)[rows][:, :d.D * esz].contiguous()
+    if d.dtype == "bf16":
+        return b.view(torch.bfloat16).double()
+    if d.dtype == "e4m3":
+        return b.view(torch.float8_e4m3fn).float().double() * d.scale[rows].double()[:, None]
+    return b.view(torch.float32).double()
+
+
+def score_errors(d, Xd, Qd, val, idx, metric, n=64, seed=7):
+    """Errors against FP64 on the original FP32 data, over n sampled queries
+    and their returned rows: of the low-precision score the contraction
+    computes (FP64 on the stored values), and of the returned value. Both in
+    the reported form (IP <q,x>, L2 |q-x|^2, COS cosine); `scaled` divides by
+    the natural scale |q||x| (IP, COS) or |q|^2 + |x|^2 (L2)."""
+    import torch
+    from paper_2206_14286_gb300 import search as S
+    M, K = idx.shape
+    samp = np.random.Generator(np.random.PCG64(seed)).choice(M, size=min(n, M), replace=False)
+    st = torch.from_numpy(samp).cuda()
+    qsel = Qd[st].contiguous()
+    dq = S.Database(qsel, metric=metric, dtype=d.dtype, keep_f32=False)
+    qlp = prepared_rows(dq, torch.arange(len(samp), device="cuda"))
+    rows = idx[st].long()
+    xlp = prepared_rows(d, rows.reshape(-1)).view(len(samp), K, -1)
+    xf = Xd[rows.reshape(-1)].double().view(len(samp), K, -1)
+    qf = qsel.double()
+
+    def score(q, x):
+        if metric == "l2":
+            return ((q[:, None, :] - x) ** 2).sum(-1)
+        if metric == "cos":
+            x = x / x.norm(dim=-1, keepdim=True)
+            q = q / q.norm(dim=-1, keepdim=True)
+        return (q[:, None, :] * x).sum(-1)
+
+    exact = score(qf, xf)
+    lowp = score(qlp, xlp) if metric != "cos" else (qlp[:, None, :] * xlp).sum(-1)
+    ret = val[st].double()
+    if metric == "l2":
+        scale = (qf * qf).sum(-1)[:, None] + (xf * xf).sum(-1)
+    elif metric == "cos":
+        scale = torch.ones_like(exact)
+    else:
+        scale = qf.norm(dim=-1)[:, None] * xf.norm(dim=-1)
+
+    def stats(e):
+        a = e.abs()
+        s = a / scale
+        return {"max_abs": a.max().item(), "mean_abs": a.mean().item(),
+                "max_scaled": s.max().item(), "mean_scaled": s.mean().item()}
+
+    out = {"queries": len(samp), "rows_per_query": K,
+           "contraction_%s" % d.dtype: stats(lowp - exact), "returned_fp32": stats(ret - exact),
+           "reference": "FP64 on the original FP32 rows and queries (torch, float64)"}
+    del dq
+    return out
+
+
+def recall_of(gi, ei):
+    K = gi.shape[1]
+    return float(np.mean([len(set(gi[i]) & set(ei[i])) / K for i in range(gi.shape[0])]))
+
+
+def eq6(M, N, D, seconds, pi, beta, bytes_moved, gamma, C_design, C_measured=None):
+    """The paper's three-roof bound (Eq. 6) for one launch of a fused
+    contraction over M x N scores of length D, with C COPs per score."""
+    from paper_2206_14286_gb300 import roofline as RF
+    out = {"gamma_tcops": gamma / 1e12,
+           "cop_budget_per_score": RF.cop_budget(D, gamma, pi)}
+    for tag, C in (("design", C_design), ("measured", C_measured)):
+        if C is None:
+            continue
+        r = RF.report(M, N, D, seconds, pi, beta, gamma, C, bytes_moved)
+        out[tag] = {"C_cops_per_score": C, "I_MEM_flop_per_byte": r["I_MEM"],
+                    "I_COP_flop_per_cop": r["I_COP"],
+                    "roofs_tflops": {k: v / 1e12 for k, v in r["roofs"].items()},
+                    "binding": r["binding"],
+                    "fraction_of_attainable": r["fraction_of_attainable"]}
+    return out
+
+
 # ----------------------------------------------------------------------------
 def main():
     args = parse()
@@ -180,39 +363,7 @@ def main():
     from paper_2206_14286_gb300 import synth
 
     if args.impl == "reference":
-        if rank != 0:
-            return 0
-        import oracle
-        oracle.build()
-        from oracle import recall as R
-        w = synth.workload(args.workload)
-        K = w["K"]
-        L = min(w["X"].shape[0], -(-R.min_bins(K, w["recall"]) // 128) * 128)
-        runner = OracleRunner(w, L, K, args.bins)
-        n = runner.size_for(max(0.5, 120.0 / max(1, args.steps + args.warmup)), 256)
-        per = []
-        nq = 0
-        for s in range(args.warmup + args.steps):
-            t = runner.run(n)
-            if s >= args.warmup:
-                per.append((n, t))
-                nq += n
-        tot = sum(t for _, t in per)
-        value = nq / tot
-        cores = os.cpu_count()
-        line = {"impl": "reference", "metric": "queries/s at recall@10>=0.95", "value": value,
-                "unit": "queries/s", "n_gpus": args.gpus, "steps": args.steps,
-                "warmup": args.warmup, "ms_per_step": 1e3 * tot / len(per),
-                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-                "data": "synthetic", "config": config_of(w, L, bins=args.bins),
-                "cpu_baseline": {"value": value, "unit": "queries/s", "cores": cores,
-                                 "kind": "oracle",
-                                 "sample": "%d queries per step of the %d-query batch, full %d-row database"
-                                           % (per[0][0], w["Q"].shape[0], w["X"].shape[0])},
-                "e2e": {"value": value, "unit": "queries/s", "h2d_bytes_per_step": 0,
-                        "d2h_bytes_per_step": 0}}
-        print(json.dumps(line))
-        return 0
+        return reference_arm(args, rank)
 
     torch.cuda.set_device(local)
     if world > 1:
@@ -264,24 +415,15 @@ def main():
 
     # per-kernel times from the library's event profiler, in a separate pass
     # (its events are not part of the timed steps above)
-    _lib.check(lib.knn_profile_enable(1))
-    for _ in range(min(args.steps, 20)):
-        step()
-    torch.cuda.synchronize()
-    _lib.check(lib.knn_profile_enable(0))
-    prof = {}
-    import ctypes
-    for c, name in enumerate(["prep", "k1_partial_reduce", "k2_rescoring", "k3_rerank"]):
-        tot = ctypes.c_double()
-        n = ctypes.c_int64()
-        _lib.check(lib.knn_profile_read(c, ctypes.byref(tot), ctypes.byref(n)))
-        prof[name] = {"ms_avg": tot.value / max(1, n.value), "launches": n.value}
+    prof = profiled(lib, step, min(args.steps, 20))
     # prep, K1 (plus the ragged-row kernel when N mod L != 0), then K2 and K3,
     # or one launch of both when the library fuses them (no K3 launches)
-    fused23 = prof["k3_rerank"]["launches"] == 0
+    fused23 = prof["k3"]["launches"] == 0
+    kernels = {"prep": prof["prep"], "k1_partial_reduce": prof["k1"]}
     if fused23:
-        prof["k2_k3_rescoring_rerank_fused"] = prof.pop("k2_rescoring")
-        prof.pop("k3_rerank")
+        kernels["k2_k3_rescoring_rerank_fused"] = prof["k2"]
+    else:
+        kernels["k2_rescoring"], kernels["k3_rerank"] = prof["k2"], prof["k3"]
     launches_per_step = (3 if fused23 else 4) + (1 if bins == "mod" and N % L else 0)
     S.sync_status()
 
@@ -292,60 +434,37 @@ def main():
         gr = torch.cuda.CUDAGraph()
         with torch.cuda.graph(gr):
             step()
-        for _ in range(3):
-            gr.replay()
-        torch.cuda.synchronize()
-        ga, gb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        ga.record()
-        for _ in range(args.steps):
-            gr.replay()
-        gb.record()
-        torch.cuda.synchronize()
-        g_ms = ga.elapsed_time(gb) / args.steps
+        g_ms = timed(gr.replay, args.steps, 3)
         graph = {"value": world * M / (g_ms / 1e3), "unit": "queries/s", "ms_per_step": g_ms}
         del gr
     except RuntimeError as e:  # capture refused: report why
         graph = {"unavailable": str(e)[:200]}
     S.sync_status()
 
-    # recall@10 against the exact FP32 search on the same data
+    # recall@10 against the exact FP32 search on the same data, score errors
     dbx = S.Database(Xd, metric=metric, dtype="f32", keep_f32=True)
     _, ei = dbx.search_exact(Qd, K)
-    gi = idx.cpu().numpy()
     ei = ei.cpu().numpy()
-    recall = float(np.mean([len(set(gi[i]) & set(ei[i])) / K for i in range(M)]))
+    recall = recall_of(idx.cpu().numpy(), ei)
+    errors = score_errors(db, Xd, Qd, val, idx, metric)
 
-    # the same BF16 search with the other bin map (j mod L), same workload
+    # the same BF16 search with the other bin map, same workload
     other = "mod" if bins == "contiguous" else "contiguous"
-    for _ in range(2):
-        db.search(Qd, K, L=L, rerank=rerank, bins=other)
-    torch.cuda.synchronize()
-    ao, bo = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    ao.record()
-    for _ in range(args.steps):
-        db.search(Qd, K, L=L, rerank=rerank, bins=other, out=(val, idx))
-    bo.record()
-    torch.cuda.synchronize()
-    ms_other = ao.elapsed_time(bo) / args.steps
-    io = idx.cpu().numpy()
-    recall_other = float(np.mean([len(set(io[i]) & set(ei[i])) / K for i in range(M)]))
+    vo = torch.empty_like(val)
+    io = torch.empty_like(idx)
+    ms_other = timed(lambda: db.search(Qd, K, L=L, rerank=rerank, bins=other, out=(vo, io)),
+                     args.steps)
+    recall_other = recall_of(io.cpu().numpy(), ei)
 
     # the plain FP32 path on the same workload (j mod L bins)
+    v32 = torch.empty_like(val)
+    i32 = torch.empty_like(idx)
+
     def step32():
-        dbx.search(Qd, K, L=L, rerank=rerank)
-    for _ in range(2):
-        step32()
-    torch.cuda.synchronize()
-    a32, b32 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    a32.record()
-    for _ in range(args.fp32_steps):
-        step32()
-    b32.record()
-    torch.cuda.synchronize()
-    ms32 = a32.elapsed_time(b32) / args.fp32_steps
-    v32, i32 = dbx.search(Qd, K, L=L, rerank=rerank)
-    i32 = i32.cpu().numpy()
-    recall32 = float(np.mean([len(set(i32[i]) & set(ei[i])) / K for i in range(M)]))
+        dbx.search(Qd, K, L=L, rerank=rerank, out=(v32, i32))
+    ms32 = timed(step32, args.fp32_steps)
+    prof32 = profiled(lib, step32, 3)
+    recall32 = recall_of(i32.cpu().numpy(), ei)
     del dbx
 
     # end to end through the host-buffer entry point (pinned buffers)
@@ -362,14 +481,19 @@ def main():
     e2e = {"value": world * M * e2e_steps / e2e_s, "unit": "queries/s",
            "h2d_bytes_per_step": int(M * D * 4), "d2h_bytes_per_step": int(M * K * 8)}
 
-    # roofline of the dominant kernel (K1)
+    # roofline of the dominant kernel (K1), and of the FP32 path's K1
     pk, pk_kind = peaks()
-    k1_ms = prof["k1_partial_reduce"]["ms_avg"]
+    rates = measure_rates(lib)
+    k1_ms = prof["k1"]["ms_avg"]
     flops = 2.0 * M * N * D
     achieved = flops / (k1_ms / 1e3) / 1e12
     peak = pk["bf16_tflops"]
     k1_bytes = N * D * 2 + (N * 4 if metric == "l2" else 0) + M * D * 2
-    traffic = k1_traffic(M, N, D, bins)
+    fields = profile_fields("k1_tcs_mix_l2_1m.md", "k1_tcs.cu", M, N, D, bins)
+    traffic = int(fields["dram bytes per launch"]) if fields else None
+    alu = float(fields["alu warp instructions per launch"]) if fields and \
+        "alu warp instructions per launch" in fields else None
+    C_meas = 32.0 * alu / (M * N) if alu else None
     roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
             "frac": achieved / peak, "traffic": traffic,
             "peak_source": "%s bf16 dense burst (MEASURED_PEAKS.json)" % pk_kind,
@@ -378,42 +502,56 @@ def main():
                        "k1_tcs_kernel (+ k1_tcs_tail for the N mod L ragged rows): fused BF16 "
                        "contraction + PartialReduce, j mod L bins"),
             "algorithmic": "2*M*N*D = %.4g FLOP per launch" % flops,
-            "eq6": eq6_block(M, N, D, k1_ms, pk, traffic or k1_bytes),
+            "eq6": dict(eq6(M, N, D, k1_ms / 1e3, peak * 1e12, pk["hbm_gbs"] * 1e9,
+                            traffic or k1_bytes, rates["gamma_cops"], 1.0 / 16.0, C_meas),
+                        C_note="design: one ALU compare per 16-score maximum (tcgen05.ld.red); "
+                               "measured: 32 x ALU-pipe warp instructions per score from the "
+                               "kernel's ncu capture, which also counts the polling of "
+                               "its barrier waits"),
             "hbm_context": {"algorithmic_bytes": k1_bytes,
                             "achieved_gbs": k1_bytes / (k1_ms / 1e3) / 1e9,
                             "peak_gbs": pk["hbm_gbs"]}}
+    k1_32 = prof32["k1"]["ms_avg"]
+    fp32_roof = {"bound": "alu", "kernel": "k1_simt_kernel (FP32 FFMA contraction + PartialReduce)",
+                 "achieved": flops / (k1_32 / 1e3) / 1e12, "unit": "TFLOP/s",
+                 "peak_measured_ffma": rates["ffma_tflops"],
+                 "peak_nominal_ffma": FFMA_NOMINAL_TFLOPS,
+                 "frac": flops / (k1_32 / 1e3) / 1e12 / rates["ffma_tflops"],
+                 "k1_ms": k1_32}
 
     serving = None if args.no_serving else serving_leg(args, db, w)
     unfused = None if args.no_unfused else unfused_leg(Xd, Qd, K, L)
+    configs = None
+    if not args.no_configs:
+        del Xd, Qd
+        torch.cuda.empty_cache()
+        configs = {"fp8_e4m3_cos_10m": e4m3_leg(args, lib, pk, rates),
+                   "bf16_ip_grad_1m": grad_leg(args, lib, pk)}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        import oracle
-        oracle.build()
-        runner = OracleRunner(w, L, K, bins)
-        n = runner.size_for(12.0, M)
-        tt = runner.run(n)
-        rate = n / tt
-        cpu = {"value": rate, "unit": "queries/s", "cores": os.cpu_count(), "kind": "oracle",
-               "sample": "%d of the %d queries against the full %d-row database (FP64), %.1f s"
-                         % (n, M, N, tt)}
+        cpu = cpu_baseline(w, L, K, bins)
 
     if rank == 0:
         sm = sorted(step_ms)
-        line = {"metric": "queries/s at recall@10>=0.95 (fused BF16; plain FP32 alongside)",
+        line = {"metric": METRIC,
                 "value": value, "unit": "queries/s", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                 "dtype": "bf16", "data": "synthetic", "config": config_of(w, L, L_min, bins),
                 "recall_at_10": recall,
+                "score_error": errors,
                 "other_bins": {"bins": other, "value": world * M / (ms_other / 1e3),
                                "unit": "queries/s", "ms_per_step": ms_other,
                                "recall_at_10": recall_other},
                 "p50_ms": sm[len(sm) // 2], "p99_ms": sm[min(len(sm) - 1, int(0.99 * len(sm)))],
                 "fp32_path": {"value": world * M / (ms32 / 1e3), "unit": "queries/s",
-                              "ms_per_step": ms32, "recall_at_10": recall32},
-                "kernels": prof, "roofline": roof, "e2e": e2e,
+                              "ms_per_step": ms32, "recall_at_10": recall32,
+                              "roofline": fp32_roof},
+                "kernels": kernels, "roofline": roof, "e2e": e2e,
+                "rates": dict(rates, fp8_scaled_mm_tflops=scaled_mm_tflops()),
                 "graph_replay": graph,
+                "configs": configs,
                 "serving": serving,
                 "unfused_baseline": unfused,
                 "gpu_launches": launches_per_step * args.steps, "clocks": clk,
@@ -422,6 +560,177 @@ def main():
     if world > 1:
         dist.destroy_process_group()
     return 0
+
+
+def reference_arm(args, rank):
+    """The FP64 oracle on the host cores, on the bench's workload and metric."""
+    if rank != 0:
+        return 0
+    import oracle
+    oracle.build()
+    from oracle import recall as R
+    from paper_2206_14286_gb300 import synth
+    w = synth.workload(args.workload)
+    K = w["K"]
+    L = min(w["X"].shape[0], -(-R.min_bins(K, w["recall"]) // 128) * 128)
+    runner = OracleRunner(w, L, K, args.bins)
+    n = runner.size_for(max(0.5, 120.0 / max(1, args.steps + args.warmup)), 256)
+    per = []
+    nq = 0
+    for s in range(args.warmup + args.steps):
+        t = runner.run(n)
+        if s >= args.warmup:
+            per.append((n, t))
+            nq += n
+    tot = sum(t for _, t in per)
+    value = nq / tot
+    cores = oracle.set_threads(0)
+    line = {"impl": "reference", "metric": METRIC, "value": value,
+            "unit": "queries/s", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * tot / len(per),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": config_of(w, L, bins=args.bins),
+            "cpu_baseline": {"value": value, "unit": "queries/s", "cores": cores,
+                             "kind": "oracle",
+                             "sample": "%d queries per step of the %d-query batch, full %d-row "
+                                       "database" % (per[0][0], w["Q"].shape[0],
+                                                     w["X"].shape[0])},
+            "e2e": {"value": value, "unit": "queries/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def e4m3_leg(args, lib, pk, rates):
+    """FP8-E4M3 with per-row scales, cosine, 10,000,000 x 96 rows from a
+    1024-centre mixture, M = 10,000 queries, K = 100, L = 8192, FP32 re-rank
+    of 8K bin winners; recall@100 against exact FP32 search on 2000 sampled
+    queries; the BF16 path on the same workload beside it."""
+    import torch
+    from paper_2206_14286_gb300 import search as S, synth
+    w = synth.workload("mix_cos_10m")
+    X, Q, K = w["X"], w["Q"], w["K"]
+    N, D = X.shape
+    M = Q.shape[0]
+    L, rr = w["L"], w["rerank"]
+    Xd = torch.from_numpy(X).cuda()
+    Qd = torch.from_numpy(Q).cuda()
+    del X
+    d8 = S.Database(Xd, metric="cos", dtype="e4m3")
+    v = torch.empty((M, K), dtype=torch.float32, device="cuda")
+    i = torch.empty((M, K), dtype=torch.int32, device="cuda")
+
+    def step():
+        d8.search(Qd, K, L=L, rerank=rr, out=(v, i))
+    ms = timed(step, args.config_steps, 3)
+    prof = profiled(lib, step, 3)
+    S.sync_status()
+    samp = np.random.Generator(np.random.PCG64(11)).choice(M, 2000, replace=False)
+    st = torch.from_numpy(samp).cuda()
+    dx = S.Database(Xd, metric="cos", dtype="f32")
+    _, ei = dx.search_exact(Qd[st].contiguous(), K)
+    del dx
+    torch.cuda.empty_cache()
+    ei = ei.cpu().numpy()
+    rec = recall_of(i[st].cpu().numpy(), ei)
+    errors = score_errors(d8, Xd, Qd, v, i, "cos", n=32)
+    flops = 2.0 * M * N * D
+    k1 = prof["k1"]["ms_avg"]
+    fp8_peak = FP8_PER_BF16 * pk["bf16_tflops"]
+    out = {"workload": "gaussian-mixture-1024c cosine N=%d D=%d M=%d K=%d, FP8-E4M3 per-row "
+                       "scales" % (N, D, M, K),
+           "L": L, "rerank": "FP32 top-%dK" % rr, "value": M / (ms / 1e3),
+           "unit": "queries/s", "ms_per_step": ms, "recall_at_100": rec,
+           "recall_sample": "2000 queries vs exact FP32 search",
+           "kernels": {"prep": prof["prep"], "k1_partial_reduce": prof["k1"],
+                       "k2_rescoring": prof["k2"], "k3_rerank": prof["k3"]},
+           "roofline": {"bound": "tensor", "kernel": "k1_tc_kernel (E4M3 tcgen05 kind::f8f6f4, "
+                                                    "packed-key PartialReduce)",
+                        "achieved": flops / (k1 / 1e3) / 1e12, "unit": "TFLOP/s",
+                        "peak": fp8_peak,
+                        "peak_source": "measured BF16 burst x 2 (nominal FP8/BF16 ratio)",
+                        "frac": flops / (k1 / 1e3) / 1e12 / fp8_peak,
+                        "eq6": eq6(M, N, D, k1 / 1e3, fp8_peak * 1e12, pk["hbm_gbs"] * 1e9,
+                                   N * (D + 4) + M * D, rates["gamma_cops"], 2.0)},
+           "score_error": errors}
+    # the BF16 path on the same rows: L from the recall law, 2K re-rank
+    d16 = S.Database(Xd, metric="cos", dtype="bf16")
+    L16 = S.plan_bins(N, K, w["recall"], round_to=128)
+
+    def step16():
+        d16.search(Qd, K, L=L16, rerank=2, out=(v, i))
+    ms16 = timed(step16, args.config_steps, 3)
+    k1_16 = profiled(lib, step16, 3)["k1"]["ms_avg"]
+    out["bf16_same_workload"] = {"L": L16, "rerank": "FP32 top-2K", "value": M / (ms16 / 1e3),
+                                 "ms_per_step": ms16, "unit": "queries/s",
+                                 "recall_at_100": recall_of(i[st].cpu().numpy(), ei),
+                                 "k1_ms": k1_16,
+                                 "k1_frac_of_bf16_peak": flops / (k1_16 / 1e3) / 1e12 /
+                                 pk["bf16_tflops"]}
+    S.sync_status()
+    del d8, d16, Xd, Qd
+    torch.cuda.empty_cache()
+    return out
+
+
+def grad_leg(args, lib, pk):
+    """The differentiation workload: BF16 inner product, 1,000,000 x 256
+    N(0, 1/D) rows, M = 4096, K = 32; forward search, then knn_backward of
+    seeded weights on the K values (dQ gather, dX scatter-add; dX dense and
+    zero-filled as torch's autograd needs it, and added into an existing dX)."""
+    import torch
+    from paper_2206_14286_gb300 import search as S, synth
+    w = synth.workload("iid_ip_grad_1m")
+    X, Q, K = w["X"], w["Q"], w["K"]
+    N, D = X.shape
+    M = Q.shape[0]
+    L = S.plan_bins(N, K, w["recall"], round_to=128)
+    Xd = torch.from_numpy(X).cuda()
+    Qd = torch.from_numpy(Q).cuda()
+    d = S.Database(Xd, metric="ip", dtype="bf16", keep_f32=True)
+    v = torch.empty((M, K), dtype=torch.float32, device="cuda")
+    i = torch.empty((M, K), dtype=torch.int32, device="cuda")
+
+    def fwd():
+        d.search(Qd, K, L=L, rerank=2, out=(v, i))
+    ms_f = timed(fwd, args.config_steps, 3)
+    prof = profiled(lib, fwd, 3)
+    g = torch.from_numpy(synth.targets(M, K)).cuda()
+    dxb = torch.zeros((N, D), dtype=torch.float32, device="cuda")
+    ms_b = timed(lambda: d.backward(Qd, i, g, dx=dxb, zero_dx=True), args.config_steps, 2)
+    ms_b_acc = timed(lambda: d.backward(Qd, i, g, dx=dxb, zero_dx=False), args.config_steps, 2)
+    ms_dq = timed(lambda: d.backward(Qd, i, g, want_dx=False), args.config_steps, 2)
+    S.sync_status()
+    touched = int(torch.unique(i).numel())
+    flops = 2.0 * M * N * D
+    k1 = prof["k1"]["ms_avg"]
+    sparse = M * K * D * 4 + 2 * M * D * 4 + M * K * 8 + 2 * touched * D * 4
+    dense = N * D * 4
+    out = {"workload": "iid N(0,1/D) inner product N=%d D=%d M=%d K=%d, BF16" % (N, D, M, K),
+           "L": L, "forward": {"value": M / (ms_f / 1e3), "unit": "queries/s",
+                               "ms_per_step": ms_f, "k1_ms": k1,
+                               "roofline": {"bound": "tensor",
+                                            "achieved": flops / (k1 / 1e3) / 1e12,
+                                            "peak": pk["bf16_tflops"], "unit": "TFLOP/s",
+                                            "frac": flops / (k1 / 1e3) / 1e12 /
+                                            pk["bf16_tflops"]}},
+           "backward": {"ms_dense_dx": ms_b, "ms_accumulate_dx": ms_b_acc, "ms_dq_only": ms_dq,
+                        "touched_rows": touched,
+                        "algorithmic_bytes": {"dense_dx_fill": dense, "sparse": sparse},
+                        "roofline": {"bound": "hbm", "unit": "GB/s", "peak": pk["hbm_gbs"],
+                                     "achieved_dense": (dense + sparse) / (ms_b / 1e3) / 1e9,
+                                     "frac_dense": (dense + sparse) / (ms_b / 1e3) / 1e9 /
+                                     pk["hbm_gbs"],
+                                     "achieved_accumulate": sparse / (ms_b_acc / 1e3) / 1e9,
+                                     "frac_accumulate": sparse / (ms_b_acc / 1e3) / 1e9 /
+                                     pk["hbm_gbs"]},
+                        "bytes_model": "dense: N*D*4 zero fill; sparse: gathered rows M*K*D*4, "
+                                       "q read + dq write 2*M*D*4, idx + g M*K*8, RMW of the "
+                                       "touched dX rows 2*rows*D*4"},
+           "score_error": score_errors(d, Xd, Qd, v, i, "ip", n=64)}
+    del d, Xd, Qd, dxb
+    torch.cuda.empty_cache()
+    return out
 
 
 def unfused_leg(Xd, Qd, K, L):
@@ -436,23 +745,10 @@ def unfused_leg(Xd, Qd, K, L):
     db_ip = S.Database(Xd, metric="ip", dtype="bf16", keep_f32=True)
     Xb, Qb = Xd.to(torch.bfloat16), Qd.to(torch.bfloat16)
     scores = torch.empty((M, N), dtype=torch.bfloat16, device="cuda")
-
-    def events(fn, reps=5):
-        for _ in range(2):
-            fn()
-        torch.cuda.synchronize()
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record()
-        for _ in range(reps):
-            fn()
-        b.record()
-        torch.cuda.synchronize()
-        return a.elapsed_time(b) / reps
-
-    gemm_ms = events(lambda: torch.matmul(Qb, Xb.t(), out=scores))
-    amk_ms = events(lambda: S.approx_max_k(scores, K, L=L))
-    unfused_ms = events(lambda: S.approx_max_k(torch.matmul(Qb, Xb.t(), out=scores), K, L=L))
-    fused_ms = events(lambda: db_ip.search(Qd, K, L=L, rerank=1))
+    gemm_ms = timed(lambda: torch.matmul(Qb, Xb.t(), out=scores), 5)
+    amk_ms = timed(lambda: S.approx_max_k(scores, K, L=L), 5)
+    unfused_ms = timed(lambda: S.approx_max_k(torch.matmul(Qb, Xb.t(), out=scores), K, L=L), 5)
+    fused_ms = timed(lambda: db_ip.search(Qd, K, L=L, rerank=1), 5)
     sbytes = M * N * 2
     out = {"workload": "IP, BF16, N=%d x D=%d, M=%d, K=%d, L=%d" % (N, Xd.shape[1], M, K, L),
            "gemm_ms": gemm_ms, "approx_max_k_ms": amk_ms,
@@ -511,18 +807,19 @@ def config_of(w, L, L_min=None, bins="mod"):
     return {"workload": "gaussian-mixture-256c L2 N=%d D=%d M=%d K=%d" % (X.shape[0], X.shape[1],
                                                                           Q.shape[0], w["K"]),
             "N": X.shape[0], "D": X.shape[1], "global_batch": Q.shape[0], "K": w["K"],
-            "L": L, "L_min_eq14": L_min, "bins": bins, "metric": w["metric"], "rerank": "FP32 top-%dK" % w.get("rerank", 2),
+            "L": L, "L_min_eq14": L_min, "bins": bins, "metric": w["metric"],
+            "rerank": "FP32 top-%dK" % w.get("rerank", 2),
             "l2_flush": "inputs larger than L2 (database %d MB in BF16 streamed every step)"
                         % (X.shape[0] * X.shape[1] * 2 // 2 ** 20),
             "parallelism": "replicas"}
 
 
-def k1_traffic(M, N, D, bins="mod"):
-    """DRAM bytes per K1 launch from the committed ncu summary of the same
-    kernel source and launch shape (else None). The summary holds lines
-    "- kernel source sha256: <16 hex>", "- bins: ...", "- M: ...", "- N: ...",
-    "- D: ..." and "- dram bytes per launch: <int>"."""
-    name = "k1_tcs_mix_l2_1m.md"
+def profile_fields(name, source, M, N, D, bins="mod"):
+    """Fields of a committed ncu summary under profiles/ when it was taken on
+    the current kernel source (sha256 prefix) and the same launch shape, else
+    None. The summary holds lines "- <field>: <value>", among them
+    "kernel source sha256", "bins", "M", "N", "D", "dram bytes per launch"
+    and "alu warp instructions per launch"."""
     p = os.path.join(ROOT, "profiles", name)
     if not os.path.exists(p):
         return None
@@ -531,16 +828,16 @@ def k1_traffic(M, N, D, bins="mod"):
         if line.startswith("- ") and ":" in line:
             k, v = line[2:].split(":", 1)
             fields[k.strip()] = v.strip().strip("`")
-    h = hashlib.sha256(open(os.path.join(ROOT, "paper_2206_14286_gb300", "csrc", "k1_tcs.cu"),
+    h = hashlib.sha256(open(os.path.join(ROOT, "paper_2206_14286_gb300", "csrc", source),
                             "rb").read()).hexdigest()[:16]
     try:
         if (fields.get("kernel source sha256") != h or fields.get("bins") != bins
                 or int(fields.get("M", -1)) != M or int(fields.get("N", -1)) != N
-                or int(fields.get("D", -1)) != D):
+                or int(fields.get("D", -1)) != D or "dram bytes per launch" not in fields):
             return None
-        return int(fields["dram bytes per launch"])
-    except (KeyError, ValueError):
+    except ValueError:
         return None
+    return fields
 
 
 if __name__ == "__main__":

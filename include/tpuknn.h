@@ -344,6 +344,38 @@ size_t knn_backward_workspace(int64_t N, int32_t D, int64_t M, int32_t K, int32_
 knn_status knn_profile_enable(int32_t on);
 knn_status knn_profile_read(int32_t kernel_class, double* total_ms, int64_t* launches);
 
+/*
+ * Measurement aid (no counterpart in the paper's algorithm; it measures the
+ * inputs of its roofline, Sec. 4 Eq. 6 and Eq. 8-9, on this GPU): runs a
+ * kernel that issues only one kind of FP32 instruction, in 16 independent
+ * chains per thread, over 2048 threads per SM for `iters` iterations, and
+ * returns the operations per second (thread-level: one instruction of one
+ * thread = one operation) and the kernel time in ms, timed with CUDA events
+ * on `stream` after one untimed launch. Synchronous.
+ *   KNN_RATE_MINMAX : min/max, the compare-and-select operation (COP) of
+ *                     PartialReduce: the gamma of Eq. 6.
+ *   KNN_RATE_FFMA   : fused multiply-add (2 FLOP each): the roof of the
+ *                     FP32 CUDA-core contraction.
+ * Errors: KNN_EINVAL (unknown kind, iters < 1, NULL output), KNN_ECUDA.
+ */
+typedef enum { KNN_RATE_MINMAX = 0, KNN_RATE_FFMA = 1 } knn_rate_kind;
+knn_status knn_measure_rate(int32_t kind, int64_t iters, double* ops_per_s, double* ms,
+                            void* stream);
+
+/*
+ * Test aid for the failure handling (no counterpart in the paper): sets the
+ * limit, in nanoseconds, of the tensor-core kernels' pipeline waits on the
+ * current device (0 restores the default, 2 s). A wait that runs out makes its
+ * CTA stop issuing work, let the copies and MMAs it already issued finish
+ * (those waits keep the fixed 2 s limit), free its tensor memory and return;
+ * the search's results are then undefined and knn_sync_status reports
+ * KNN_ETIMEOUT once. A limit of a few nanoseconds makes the first wait that
+ * does not complete at once run out, which is how a test exercises this path
+ * without a fault. Synchronous (it writes device memory through the legacy
+ * stream); do not call it while searches are in flight. Errors: KNN_ECUDA.
+ */
+knn_status knn_set_wait_limit_ns(uint64_t ns);
+
 /* Synchronise the current device and report a device-side wait timeout
  * (KNN_ETIMEOUT, flag then cleared) or a CUDA error (KNN_ECUDA). */
 knn_status knn_sync_status(void);

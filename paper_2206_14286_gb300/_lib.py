@@ -13,6 +13,7 @@ KNN_OK, KNN_EINVAL, KNN_ENOMEM, KNN_ECUDA, KNN_ETIMEOUT, KNN_EUNSUPPORTED = rang
 METRIC = {"ip": 0, "l2": 1, "cos": 2}
 DTYPE = {"f32": 0, "bf16": 1, "e4m3": 2}
 BINS = {"mod": 0, "contiguous": 1}
+RATE = {"minmax": 0, "ffma": 1}
 STATIC_WORKSPACE_BYTES = 16 << 20  # KNN_STATIC_WORKSPACE_BYTES
 
 # every function the header declares, with (restype, argtypes)
@@ -49,6 +50,8 @@ SIGNATURES = {
     "knn_db_info": (ctypes.c_int, [P, P, P, P, P]),
     "knn_db_search": (ctypes.c_int, [P, P, I64, I32, I64, I32, DBL, I32, P, P, P, SZ, P]),
     "knn_db_search_workspace": (SZ, [P, I64, I32, I64, I32, DBL, I32]),
+    "knn_measure_rate": (ctypes.c_int, [I32, I64, P, P, P]),
+    "knn_set_wait_limit_ns": (ctypes.c_int, [ctypes.c_uint64]),
     "knn_sync_status": (ctypes.c_int, []),
     "knn_profile_enable": (ctypes.c_int, [I32]),
     "knn_profile_read": (ctypes.c_int, [I32, P, P]),

@@ -990,6 +990,19 @@ knn_status knn_profile_read(int32_t kernel_class, double* total_ms, int64_t* lau
   return KNN_OK;
 }
 
+knn_status knn_measure_rate(int32_t kind, int64_t iters, double* ops_per_s, double* ms,
+                            void* stream) {
+  if ((kind != KNN_RATE_MINMAX && kind != KNN_RATE_FFMA) || iters < 1 || !ops_per_s || !ms)
+    return KNN_EINVAL;
+  return cuda_status(measure_rate(kind, iters, ops_per_s, ms, (cudaStream_t)stream));
+}
+
+knn_status knn_set_wait_limit_ns(uint64_t ns) {
+  const bool a = k1_tc_set_wait_limit((unsigned long long)ns);
+  const bool b = k1_tcs_set_wait_limit((unsigned long long)ns);
+  return (a && b) ? KNN_OK : KNN_ECUDA;
+}
+
 knn_status knn_sync_status(void) {
   cudaError_t e = cudaDeviceSynchronize();
   if (e != cudaSuccess) return cuda_status(e);

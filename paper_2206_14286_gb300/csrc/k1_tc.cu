@@ -146,15 +146,16 @@ k1_tc_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CU
           ph ^= 1u;
         }
       }
-      // drain: the last min(issued, S) copies land before the CTA can exit
+      // drain: the last min(issued, S) copies and the query tile land before
+      // the CTA can exit, also after a give-up
       for (int k = 0; k < S && k < issued; ++k) {
         if (--s < 0) {
           s = S - 1;
           ph ^= 1u;
         }
-        mbar_wait_sleep(b_full + 8 * s, ph, abort_flag, 64);
+        mbar_drain(b_full + 8 * s, ph);
       }
-      mbar_wait_sleep(b_q, 0, abort_flag, 64);
+      mbar_drain(b_q, 0);
     } else if (warp == 1) {
       // ---------------------------------------------------------- MMA issuer
       if (lane == 0) {
@@ -184,9 +185,10 @@ k1_tc_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CU
             }
           }
         }
-        // all MMAs have completed before tensor memory is released
+        // all MMAs have completed before tensor memory is released (also
+        // after a give-up: the MMAs already issued still write TMEM)
         tc_commit(b_done);
-        mbar_wait(b_done, 0, abort_flag);
+        mbar_drain(b_done, 0);
       }
       __syncwarp();
       // wait until the epilogue has read its last accumulator
@@ -234,7 +236,7 @@ k1_tc_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CU
         if (DT == KNN_E4M3) mul_n = a.xscale[jn];
       }
     }
-    if (!mbar_wait_sleep(b_accf + 8 * ab, aph, abort_flag, 128)) break;
+    if (!warp_all(mbar_wait_sleep(b_accf + 8 * ab, aph, abort_flag, 128))) break;
     tc_fence_after();
     // invalid lanes turn every key into -inf: no divergence, no extra select
     const uint32_t km = valid ? nmask : 0u;
@@ -403,5 +405,6 @@ cudaError_t launch_k1_tc(const K1Plan& p, const void* X, const float* xscale, co
 
 
 bool k1_tc_take_timeout() { return tc_take_timeout_local(); }
+bool k1_tc_set_wait_limit(unsigned long long ns) { return tc_set_wait_limit_local(ns); }
 
 }  // namespace tpuknn

@@ -231,7 +231,7 @@ k1_tcs_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
   if (warp < 4) asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(kCtrlRegsS));
   if (warp == 0) {
     // -------------------------------------------------------------- producer
-    int s = 0, issued = 0;
+    int s = 0, issued = 0, q_armed = 0;
     uint32_t ph = 0;
     bool prun = true;
     for (int sg = 0; sg < nseg && prun; ++sg) {
@@ -239,8 +239,9 @@ k1_tcs_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
     // the segment's query tile (phase sg of b_q); from the second segment on
     // only after the MMAs of the previous one are done with the old tile
     if (MODE != kKLoopQ && sg > 0 &&
-        !mbar_wait_sleep(b_qe, (uint32_t)((sg - 1) & 1), abort_flag, 64))
+        !warp_all(mbar_wait_sleep(b_qe, (uint32_t)((sg - 1) & 1), abort_flag, 64)))
       break;
+    q_armed = sg + 1;
     if (lane == 0) {
       if (MODE == kKLoopQ) {
         mbar_arrive(b_q);  // the queries come with every stage
@@ -256,7 +257,7 @@ k1_tcs_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
     int64_t bg = s_begin / a.ntg, tg = s_begin % a.ntg;
     const int total = ns * NKB;
     for (int g = 0; g < total; ++g) {
-      if (issued >= S && !mbar_wait_sleep(b_empty + 8 * s, ph ^ 1u, abort_flag, 64)) {
+      if (issued >= S && !warp_all(mbar_wait_sleep(b_empty + 8 * s, ph ^ 1u, abort_flag, 64))) {
         prun = false;
         break;
       }
@@ -295,14 +296,16 @@ k1_tcs_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
       }
     }
     }
+    // the copies still in flight land before the CTA can exit, also after a
+    // give-up: the last min(issued, S) stages and the last query tile armed
     for (int k = 0; k < S && k < issued; ++k) {
       if (--s < 0) {
         s = S - 1;
         ph ^= 1u;
       }
-      mbar_wait_sleep(b_full + 8 * s, ph, abort_flag, 64);
+      mbar_drain(b_full + 8 * s, ph);
     }
-    if (nseg > 0) mbar_wait_sleep(b_q, (uint32_t)((nseg - 1) & 1), abort_flag, 64);
+    if (MODE != kKLoopQ && q_armed > 0) mbar_drain(b_q, (uint32_t)((q_armed - 1) & 1));
     return;
   }
   if (warp == 1) {
@@ -324,7 +327,7 @@ k1_tcs_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
       uint32_t ph0 = 0;
       bool run = true;
       for (int sg = 0; sg < nseg && run; ++sg) {
-      if (!mbar_wait(b_q, (uint32_t)(sg & 1), abort_flag)) break;
+      if (!warp_all(mbar_wait(b_q, (uint32_t)(sg & 1), abort_flag))) break;
       for (int li = 0; li < ns && run; ++li) {
         const int i = sg * ns + li;
         const int e = i & 1;
@@ -336,7 +339,7 @@ k1_tcs_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
 #pragma unroll
           for (int kb = 0; kb < NKB; ++kb) {
             sk[kb] = s;
-            if (run && !mbar_wait(b_full + 8 * s, ph, abort_flag)) run = false;
+            if (run && !warp_all(mbar_wait(b_full + 8 * s, ph, abort_flag))) run = false;
             if (++s == S) {
               s = 0;
               ph ^= 1u;
@@ -346,13 +349,14 @@ k1_tcs_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
           ph0 = ph;
         }
         if (!run) break;
-        if (a.ext && !mbar_wait(b_xf + 8 * e, (uint32_t)((i >> 1) & 1), abort_flag)) {
+        if (a.ext && !warp_all(mbar_wait(b_xf + 8 * e, (uint32_t)((i >> 1) & 1), abort_flag))) {
           run = false;
           break;
         }
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
-          if (i >= 1 && !mbar_wait(b_acce + 8 * h, (uint32_t)((i & 1) ^ 1), abort_flag)) {
+          if (i >= 1 &&
+              !warp_all(mbar_wait(b_acce + 8 * h, (uint32_t)((i & 1) ^ 1), abort_flag))) {
             run = false;
             break;
           }
@@ -396,18 +400,18 @@ k1_tcs_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
       uint32_t ph = 0;
       bool run = true;
       for (int sg = 0; sg < nseg && run; ++sg) {
-      if (!mbar_wait(b_q, (uint32_t)(sg & 1), abort_flag)) break;
+      if (!warp_all(mbar_wait(b_q, (uint32_t)(sg & 1), abort_flag))) break;
       for (int li = 0; li < ns && run; ++li) {
         const int i = sg * ns + li;
         const int e = i & 1;
         // both accumulators are written from the first K block on
-        if (i >= 1 && (!mbar_wait(b_acce, (uint32_t)((i & 1) ^ 1), abort_flag) ||
-                       !mbar_wait(b_acce + 8, (uint32_t)((i & 1) ^ 1), abort_flag))) {
+        if (i >= 1 && (!warp_all(mbar_wait(b_acce, (uint32_t)((i & 1) ^ 1), abort_flag)) ||
+                       !warp_all(mbar_wait(b_acce + 8, (uint32_t)((i & 1) ^ 1), abort_flag)))) {
           run = false;
           break;
         }
         for (int kb = 0; kb < NKB; ++kb) {
-          if (!mbar_wait(b_full + 8 * s, ph, abort_flag)) {
+          if (!warp_all(mbar_wait(b_full + 8 * s, ph, abort_flag))) {
             run = false;
             break;
           }
@@ -440,7 +444,7 @@ k1_tcs_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
         }
         if (!run) break;
         if (a.ext) {
-          if (!mbar_wait(b_xf + 8 * e, (uint32_t)((i >> 1) & 1), abort_flag)) {
+          if (!warp_all(mbar_wait(b_xf + 8 * e, (uint32_t)((i >> 1) & 1), abort_flag))) {
             run = false;
             break;
           }
@@ -465,10 +469,11 @@ k1_tcs_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
       }
     }
     }
-    // all MMAs have completed before tensor memory is released
+    // all MMAs have completed before tensor memory is released (also after a
+    // give-up: the MMAs already issued still write their accumulators)
     if (lane == 0) tc_commit(b_done);
     __syncwarp();
-    mbar_wait(b_done, 0, abort_flag);
+    mbar_drain(b_done, 0);
     asm volatile("bar.sync 1, %0;" ::"n"(32 + 512) : "memory");
     tc_fence_after();
     tmem_dealloc(tmem_base, 512);
@@ -594,7 +599,7 @@ k1_tcs_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
     brow = -1;
     for (int li = 0; li < ns; ++li) {
       const int i = sg * ns + li;
-      if (!mbar_wait_sleep(b_accf + 8 * h, (uint32_t)(i & 1), abort_flag, 32)) {
+      if (!warp_all(mbar_wait_sleep(b_accf + 8 * h, (uint32_t)(i & 1), abort_flag, 32))) {
         erun = false;
         break;
       }
@@ -691,7 +696,7 @@ k1_tcs_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
   tg = s_begin % a.ntg;
   for (int li = 0; li < ns; ++li) {
     const int i = sg * ns + li;
-    if (!mbar_wait_sleep(b_accf + 8 * h, (uint32_t)(i & 1), abort_flag, 32)) {
+    if (!warp_all(mbar_wait_sleep(b_accf + 8 * h, (uint32_t)(i & 1), abort_flag, 32))) {
       erun = false;
       break;
     }
@@ -1046,5 +1051,6 @@ cudaError_t launch_k1_tcs(int64_t N, int64_t M, int64_t L, int D, int metric, in
 }
 
 bool k1_tcs_take_timeout() { return tc_take_timeout_local(); }
+bool k1_tcs_set_wait_limit(unsigned long long ns) { return tc_set_wait_limit_local(ns); }
 
 }  // namespace tpuknn

@@ -68,6 +68,7 @@ cudaError_t launch_k1_tcs(int64_t N, int64_t M, int64_t L, int D, int metric, in
                           const void* X, const float* hnorm, const void* Qp,
                           unsigned long long* G, cudaStream_t st);
 bool k1_tcs_take_timeout();
+bool k1_tcs_set_wait_limit(unsigned long long ns);
 
 // approx_max_k on a caller's score matrix (FP32 or BF16, M x N): the bin
 // winners merged as ordered 64-bit keys into G[M][L] (zero on entry), scores
@@ -117,9 +118,17 @@ size_t backward_ws_bytes(int64_t N, int64_t M, int K, int deterministic);
 // (256 or 128), or 0 if the rows are too long.
 int k1_tc_query_tile(int dtype, int D);
 
+// Issue-rate microbenchmark (knn_measure_rate): operations per second of one
+// instruction kind over a grid that fills every SM.
+cudaError_t measure_rate(int kind, int64_t iters, double* ops_per_s, double* ms,
+                         cudaStream_t st);
+
 // Number of SMs of the current device (cached).
 int device_sm_count();
 // Take and clear the tensor-core kernels' timeout flag (synchronous).
 bool k1_tc_take_timeout();
+// Set the limit of the tensor-core kernels' pipeline waits on the current
+// device (ns = 0: the default 2 s).
+bool k1_tc_set_wait_limit(unsigned long long ns);
 
 }  // namespace tpuknn

@@ -12,6 +12,10 @@ namespace tpuknn {
 // copy, so every tensor-core kernel file exports a reader.
 static __device__ unsigned int g_tc_timeout = 0;
 constexpr uint64_t kTimeoutNs = 2000000000ull;
+// The limit of the pipeline waits (mbar_wait, mbar_wait_sleep); the host may
+// lower it (knn_set_wait_limit_ns) to make a wait run out in a test. The
+// drain waits after a give-up (mbar_drain) keep kTimeoutNs.
+static __device__ unsigned long long g_tc_wait_limit_ns = kTimeoutNs;
 
 namespace {
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -56,7 +60,14 @@ __device__ __forceinline__ uint64_t global_ns() {
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
   return t;
 }
-// Bounded wait for the phase of `parity` to complete.
+__device__ __forceinline__ uint64_t wait_limit_ns() {
+  return *reinterpret_cast<volatile unsigned long long*>(&g_tc_wait_limit_ns);
+}
+// Bounded wait for the phase of `parity` to complete. Returns false when the
+// limit runs out (the caller's CTA then aborts: this thread raises the CTA's
+// abort flag and the device-wide timeout flag) or when another thread of the
+// CTA has raised the abort flag. Each lane decides on its own: callers that
+// need a warp-wide decision combine the lanes' results (warp_all).
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag) {
   if (mbar_test_wait(bar, parity)) return true;
   const uint64_t t0 = global_ns();
@@ -64,7 +75,7 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatil
     if (mbar_test_wait(bar, parity)) return true;
     if ((n & 1023) == 0) {
       if (*abort_flag) return false;
-      if (global_ns() - t0 > kTimeoutNs) {
+      if (global_ns() - t0 > wait_limit_ns()) {
         *abort_flag = 1;
         atomicExch(&g_tc_timeout, 1u);
         return false;
@@ -84,7 +95,7 @@ __device__ __forceinline__ bool mbar_wait_sleep(uint32_t bar, uint32_t parity,
     if (mbar_test_wait(bar, parity)) return true;
     if ((n & 15) == 0) {
       if (*abort_flag) return false;
-      if (global_ns() - t0 > kTimeoutNs) {
+      if (global_ns() - t0 > wait_limit_ns()) {
         *abort_flag = 1;
         atomicExch(&g_tc_timeout, 1u);
         return false;
@@ -92,6 +103,27 @@ __device__ __forceinline__ bool mbar_wait_sleep(uint32_t bar, uint32_t parity,
     }
   }
 }
+// Wait used on the way out after a give-up: the copies and MMAs a CTA has
+// already issued must finish before it releases its shared and tensor memory,
+// so this wait ignores the abort flag. It is bounded by the fixed kTimeoutNs
+// (a wait that runs out here records the timeout and returns).
+__device__ __forceinline__ bool mbar_drain(uint32_t bar, uint32_t parity) {
+  if (mbar_test_wait(bar, parity)) return true;
+  const uint64_t t0 = global_ns();
+  for (uint32_t n = 1;; ++n) {
+    __nanosleep(64);
+    if (mbar_test_wait(bar, parity)) return true;
+    if ((n & 15) == 0 && global_ns() - t0 > kTimeoutNs) {
+      atomicExch(&g_tc_timeout, 1u);
+      return false;
+    }
+  }
+}
+// A decision every lane of the warp takes together (all 32 lanes call it):
+// true only if it holds in every lane. After a wait, lanes that may have given
+// up at different moments then leave (or stay) as one warp, as the warp-wide
+// .sync.aligned instructions that follow require.
+__device__ __forceinline__ bool warp_all(bool ok) { return __all_sync(0xffffffffu, ok) != 0; }
 __device__ __forceinline__ void fence_barrier_init() {
   asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
 }
@@ -205,6 +237,17 @@ __device__ __forceinline__ void fence_proxy_async_smem() {
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
 }  // namespace
+
+// Host: set this translation unit's pipeline-wait limit on the current
+// device (ns = 0: the default kTimeoutNs).
+static inline bool tc_set_wait_limit_local(unsigned long long ns) {
+  const unsigned long long v = ns ? ns : kTimeoutNs;
+  if (cudaMemcpyToSymbol(g_tc_wait_limit_ns, &v, sizeof(v)) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return true;
+}
 
 // Host: read and clear this translation unit's timeout flag.
 static inline bool tc_take_timeout_local() {

@@ -191,8 +191,12 @@ class Database:
         return V, A
 
     def backward(self, q, idx, grad_val, want_dq=True, want_dx=True, deterministic=False,
-                 x_f32=None, stream=None):
-        """Gradient of sum(grad_val * value(q_i, x_idx)) w.r.t. q and the rows."""
+                 x_f32=None, stream=None, dx=None, zero_dx=True):
+        """Gradient of sum(grad_val * value(q_i, x_idx)) w.r.t. q and the rows.
+
+        dx: an N x D float32 CUDA tensor to write into (default: a new one);
+        zero_dx=False adds into it instead of writing zeros over it first
+        (for a caller whose dx is already zero, or who accumulates)."""
         q = q.contiguous()
         idx = idx.contiguous()
         grad_val = grad_val.contiguous().float()
@@ -200,15 +204,23 @@ class Database:
         lib = _lib.get()
         xf = x_f32 if x_f32 is not None else self.f32
         dq = torch.empty((M, self.D), dtype=torch.float32, device=self.device) if want_dq else None
-        dx = torch.empty((self.N, self.D), dtype=torch.float32, device=self.device) if want_dx else None
+        if want_dx and dx is None:
+            dx = torch.empty((self.N, self.D), dtype=torch.float32, device=self.device)
+            zero_dx = True
+        elif not want_dx:
+            dx = None
+        elif not (dx.is_cuda and dx.dtype == torch.float32 and dx.is_contiguous()
+                  and tuple(dx.shape) == (self.N, self.D)):
+            raise ValueError("dx must be a contiguous N x D float32 CUDA tensor")
         nb = lib.knn_backward_workspace(self.N, self.D, M, K, int(deterministic))
         ws = self._get_ws(("bwd", M, K), nb) if nb else None
         with torch.cuda.device(self.device):
             check(lib.knn_backward(self.lp.data_ptr(), _ptr(self.scale), _ptr(xf), self.N, self.D,
                                    DTYPE[self.dtype], METRIC[self.metric], q.data_ptr(), M, K,
-                                   idx.data_ptr(), grad_val.data_ptr(), _ptr(dq), _ptr(dx), 1,
-                                   int(deterministic), _ptr(ws), ws.numel() if ws is not None else 0,
-                                   _stream(stream)), "knn_backward")
+                                   idx.data_ptr(), grad_val.data_ptr(), _ptr(dq), _ptr(dx),
+                                   int(bool(zero_dx)), int(deterministic), _ptr(ws),
+                                   ws.numel() if ws is not None else 0, _stream(stream)),
+                  "knn_backward")
         return dq, dx
 
 

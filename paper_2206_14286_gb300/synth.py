@@ -129,10 +129,13 @@ def workload(name, scale=1.0):
         Q = mixture(M, D, 256, QUERY_SEED)
         return dict(X=X, Q=Q, metric="l2", K=10, recall=0.95, dtype="bf16", rerank=2)
     if name == "mix_cos_10m":         # E4M3, cosine, K=100, recall 0.95
+        # L and the re-rank multiple reach recall@100 >= 0.95 against exact
+        # FP32 search (measured: 0.968); with E4M3 scores the recall law's L
+        # (2048) and a 2K re-rank give 0.75
         N, D, M = n_of(10_000_000), 96, n_of(10_000)
         X = unit_rows(mixture(N, D, 1024, DATA_SEED))
         Q = unit_rows(mixture(M, D, 1024, QUERY_SEED))
-        return dict(X=X, Q=Q, metric="cos", K=100, recall=0.95, dtype="e4m3", rerank=2)
+        return dict(X=X, Q=Q, metric="cos", K=100, recall=0.95, dtype="e4m3", L=8192, rerank=8)
     if name == "iid_ip_grad_1m":      # BF16, IP, K=32, backward
         N, D, M = n_of(1_000_000), 256, n_of(4096)
         X = iid_normal(N, D, DATA_SEED, std=1.0 / np.sqrt(D))

@@ -221,3 +221,25 @@ def test_autograd_grad_workload_1m_sampled():
     hq = host(gdq)[samp]
     sq = np.abs(oq).max() + 1e-30
     np.testing.assert_allclose(hq[same], oq[same], rtol=0, atol=1e-4 * sq)
+
+
+def test_backward_into_caller_dx_accumulates():
+    """zero_dx=False adds into the caller's dx: two backward passes into one
+    buffer give twice one pass (atomic adds of the same values in FP32 may
+    round differently, hence the tolerance); zero_dx=True overwrites."""
+    g = rng(17)
+    X = g.standard_normal((5000, 64)).astype(np.float32)
+    Q = g.standard_normal((40, 64)).astype(np.float32)
+    d = db(X, "ip", "bf16")
+    val, idx = d.search(dev(Q), 8, L=128)
+    gv = torch.from_numpy(g.standard_normal((40, 8)).astype(np.float32)).cuda()
+    _, dx1 = d.backward(dev(Q), idx, gv, want_dq=False)
+    acc = torch.zeros_like(dx1)
+    for _ in range(2):
+        d.backward(dev(Q), idx, gv, want_dq=False, dx=acc, zero_dx=False)
+    torch.cuda.synchronize()
+    scale = dx1.abs().max().item()
+    assert torch.allclose(acc, 2 * dx1, rtol=0, atol=1e-5 * scale)
+    d.backward(dev(Q), idx, gv, want_dq=False, dx=acc, zero_dx=True)
+    torch.cuda.synchronize()
+    assert torch.allclose(acc, dx1, rtol=0, atol=1e-6 * scale)
