@@ -65,6 +65,9 @@ def parse():
     ap.add_argument("--no-configs", action="store_true",
                     help="skip the E4M3 10M and the 1M x 256 backward workloads")
     ap.add_argument("--config-steps", type=int, default=10)
+    ap.add_argument("--shard", action="store_true",
+                    help="N-sharded search: the rows split over the ranks, two all-reduce MAX "
+                         "exchanges per step (strong scaling); default: independent replicas")
     ap.add_argument("--serving-requests", type=int, default=1200)
     ap.add_argument("--serving-rates", default="1500,6000",
                     help="offered requests/s, one trace per rate")
@@ -373,6 +376,8 @@ def main():
     from paper_2206_14286_gb300 import search as S
     from paper_2206_14286_gb300 import _lib
     lib = _lib.get()
+    if args.shard:
+        return shard_main(args, world, rank, local)
 
     w = synth.workload(args.workload)
     X, Q, K, metric = w["X"], w["Q"], w["K"], w["metric"]
@@ -557,6 +562,78 @@ def main():
                 "gpu_launches": launches_per_step * args.steps, "clocks": clk,
                 "cpu_baseline": cpu}
         print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def shard_main(args, world, rank, local):
+    """The N-sharded search (knn_shard_*): rank r holds rows
+    shard_bounds(N, world, L)[r] of the workload's database, every rank takes
+    the whole query batch, and a step is PartialReduce on the shard, an
+    all-reduce MAX of the M x L keys, rescoring of the candidates the shard
+    holds, an all-reduce MAX of the M x Kp keys and the top K. Total work is
+    fixed as the ranks grow (strong scaling); value = queries / step time
+    (max over ranks)."""
+    import torch
+    import torch.distributed as dist
+    from paper_2206_14286_gb300 import search as S, shard as SH, synth
+    w = synth.workload(args.workload)
+    X, Q, K, metric = w["X"], w["Q"], w["K"], w["metric"]
+    N, D = X.shape
+    M = Q.shape[0]
+    L = S.plan_bins(N, K, w["recall"], round_to=128)
+    rerank = w.get("rerank", 2)
+    row0, n = SH.shard_bounds(N, world, L)[rank]
+    part = SH.DatabaseShard(torch.from_numpy(X[row0:row0 + n]).cuda(), row0, N, metric,
+                            w["dtype"])
+    Qd = torch.from_numpy(Q).cuda()
+    ar = SH.dist_allreduce_max()
+    out = {}
+
+    def step():
+        out["r"] = SH.sharded_search(part, Qd, K, L, rerank, ar)
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+    S.sync_status()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = Clocks(local)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(args.steps):
+        step()
+    b.record()
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    if world > 1:
+        dist.barrier()
+    t = torch.tensor([a.elapsed_time(b)], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    job_ms = float(t.item())
+    value = M * args.steps / (job_ms / 1e3)
+    recall = None
+    if world == 1:
+        dbx = S.Database(torch.from_numpy(X).cuda(), metric=metric, dtype="f32")
+        _, ei = dbx.search_exact(Qd, K)
+        recall = recall_of(out["r"][1].cpu().numpy(), ei.cpu().numpy())
+    if rank == 0:
+        cfg = config_of(w, L, bins="mod")
+        cfg["parallelism"] = "shard%d" % world
+        cfg["shard_rows"] = n
+        print(json.dumps({"metric": METRIC, "value": value, "unit": "queries/s", "n_gpus": world,
+                          "steps": args.steps, "warmup": args.warmup,
+                          "ms_per_step": job_ms / args.steps, "higher_is_better": True,
+                          "scaling": "strong", "vs_baseline": None, "dtype": w["dtype"],
+                          "data": "synthetic", "config": cfg, "recall_at_10": recall,
+                          # per step: prep, K1 (+ ragged rows), bin merge, key conversion;
+                          # key conversion, K2, FP32 scoring; key conversion, K2, pairs
+                          "gpu_launches": args.steps * (10 + (1 if n % L else 0) +
+                                                        (1 if metric == "cos" else 0)),
+                          "clocks": clk}))
     if world > 1:
         dist.destroy_process_group()
     return 0

@@ -205,6 +205,64 @@ knn_status knn_search_static(const void* db_lp, const float* db_scale, const flo
                              float* out_val, int32_t* out_idx, void* stream);
 
 /*
+ * N-sharded search (Sec. 7: the search runs on pods of chips that each hold
+ * part of the database; App. A.1: reduction_input_size_override plans the
+ * bins for the whole input when an operand holds one shard). A database of
+ * N_global rows is split by rows; a shard holds the global rows
+ * [row0, row0 + n_local), prepared as knn_prepare does. Bins are j mod L of
+ * the GLOBAL row index j, L planned for N_global (knn_plan_bins); row0 must be
+ * a multiple of L, so every shard's rows keep their global bins, and
+ * L <= n_local. Only the j mod L bin map is supported.
+ *
+ * The shards exchange two arrays between three calls, each merged by an
+ * element-wise maximum over the shards (e.g. an all-reduce MAX over int64):
+ *   1. knn_shard_partial_reduce: PartialReduce (Alg. 1) of the shard's rows,
+ *      keys[M x L] (int64, device): per query and bin the best (score, global
+ *      row) as a signed-order key, or INT64_MIN for a bin with no row here.
+ *      Workspace: knn_shard_partial_reduce_workspace bytes (0 = invalid).
+ *   2. knn_shard_rescore: on the merged keys, ExactRescoring's top
+ *      Kp = knn_rescore_count(K, rerank_mult, L) bin winners per query
+ *      (every shard gets the same ones), and for those whose row this shard
+ *      holds the FP32 score from x_f32 (n_local x D, the shard's FP32 rows;
+ *      for COS its unit rows) against the FP32 queries q (M x D); the others
+ *      stay INT64_MIN. Output cand_keys[M x Kp] (int64, device).
+ *      Workspace: knn_shard_rescore_workspace bytes.
+ *   3. knn_shard_finish: on the merged cand_keys, the best K per query, best
+ *      first, in the reported form (as knn_search's outputs).
+ *      Workspace: knn_shard_finish_workspace bytes.
+ * A key orders (score, row) like the library's 64-bit keys (larger score
+ * first, then the smaller row), XOR 2^63 so that signed int64 comparison
+ * gives that order; a MAX reduction therefore keeps, per bin, the best row of
+ * all shards (ties to the smaller global row), exactly PartialReduce over
+ * the whole database. With one shard (row0 = 0, n_local = N_global) the three
+ * calls are the search.
+ * Errors: KNN_EINVAL (sizes, row0 not a multiple of L, L > n_local, NULL,
+ * alignment), KNN_ENOMEM (workspace), KNN_EUNSUPPORTED, KNN_ECUDA.
+ */
+size_t knn_shard_partial_reduce_workspace(int64_t n_local, int64_t row0, int64_t N_global,
+                                          int32_t D, int32_t dtype, int32_t metric, int64_t M,
+                                          int64_t L);
+knn_status knn_shard_partial_reduce(const void* db_lp, const float* db_scale,
+                                    const float* db_hnorm, int64_t n_local, int64_t row0,
+                                    int64_t N_global, int32_t D, int32_t dtype, int32_t metric,
+                                    const float* q, int64_t M, int64_t L, int64_t* keys,
+                                    void* workspace, size_t ws_bytes, void* stream);
+/* Kp = min(max(1, rerank_mult) * K, L, 4096), at least K; -1 if K < 1, L < 1,
+ * K > L or K > 4096. */
+int32_t knn_rescore_count(int32_t K, int32_t rerank_mult, int64_t L);
+size_t knn_shard_rescore_workspace(int64_t M, int64_t L, int32_t D, int32_t metric, int32_t K,
+                                   int32_t rerank_mult);
+knn_status knn_shard_rescore(const int64_t* keys, int64_t M, int64_t L, int32_t K,
+                             int32_t rerank_mult, const float* q, int32_t D, int32_t metric,
+                             const float* x_f32, int64_t n_local, int64_t row0,
+                             int64_t* cand_keys, void* workspace, size_t ws_bytes,
+                             void* stream);
+size_t knn_shard_finish_workspace(int64_t M, int32_t Kp, int32_t K);
+knn_status knn_shard_finish(const int64_t* cand_keys, int64_t M, int32_t Kp, int32_t K,
+                            int32_t metric, float* out_val, int32_t* out_idx, void* workspace,
+                            size_t ws_bytes, void* stream);
+
+/*
  * A database held by the library (the problem statement's fixed set of N
  * reference vectors, Sec. 2, prepared once for the contraction as
  * knn_prepare does). knn_db_create allocates device memory with cudaMalloc on
@@ -369,9 +427,10 @@ knn_status knn_measure_rate(int32_t kind, int64_t iters, double* ops_per_s, doub
  * CTA stop issuing work, let the copies and MMAs it already issued finish
  * (those waits keep the fixed 2 s limit), free its tensor memory and return;
  * the search's results are then undefined and knn_sync_status reports
- * KNN_ETIMEOUT once. A limit of a few nanoseconds makes the first wait that
- * does not complete at once run out, which is how a test exercises this path
- * without a fault. Synchronous (it writes device memory through the legacy
+ * KNN_ETIMEOUT once. A limit under 1000 ns (below the device timer's
+ * resolution) makes every wait give up at its first check, i.e. the first
+ * wait that does not complete at once runs out: that is how a test exercises
+ * this path without a fault. Synchronous (it writes device memory through the legacy
  * stream); do not call it while searches are in flight. Errors: KNN_ECUDA.
  */
 knn_status knn_set_wait_limit_ns(uint64_t ns);

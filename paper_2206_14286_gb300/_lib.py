@@ -45,6 +45,15 @@ SIGNATURES = {
     "knn_backward": (ctypes.c_int, [P, P, P, I64, I32, I32, I32, P, I64, I32, P, P, P, P, I32,
                                     I32, P, SZ, P]),
     "knn_backward_workspace": (SZ, [I64, I32, I64, I32, I32]),
+    "knn_shard_partial_reduce_workspace": (SZ, [I64, I64, I64, I32, I32, I32, I64, I64]),
+    "knn_shard_partial_reduce": (ctypes.c_int, [P, P, P, I64, I64, I64, I32, I32, I32, P, I64, I64,
+                                                P, P, SZ, P]),
+    "knn_rescore_count": (I32, [I32, I32, I64]),
+    "knn_shard_rescore_workspace": (SZ, [I64, I64, I32, I32, I32, I32]),
+    "knn_shard_rescore": (ctypes.c_int, [P, I64, I64, I32, I32, P, I32, I32, P, I64, I64, P, P, SZ,
+                                         P]),
+    "knn_shard_finish_workspace": (SZ, [I64, I32, I32]),
+    "knn_shard_finish": (ctypes.c_int, [P, I64, I32, I32, I32, P, P, P, SZ, P]),
     "knn_db_create": (ctypes.c_int, [P, I64, I32, I32, I32, I32, P, P]),
     "knn_db_destroy": (ctypes.c_int, [P]),
     "knn_db_info": (ctypes.c_int, [P, P, P, P, P]),

@@ -854,6 +854,171 @@ knn_status knn_backward(const void* db_lp, const float* db_scale, const float* x
 }
 
 // ---------------------------------------------------------------------------
+// N-sharded search (knn_shard_*): the shard's rows are global rows
+// [row0, row0 + n_local) of an N_global-row database; bins are j mod L of the
+// global index, which the local grid view keeps when row0 is a multiple of L.
+// ---------------------------------------------------------------------------
+static knn_status shard_layout(int64_t n_local, int64_t row0, int64_t N_global, int32_t D,
+                               int32_t dtype, int32_t metric, int64_t M, int64_t L,
+                               SearchLayout* s, size_t* total) {
+  if (N_global < 1 || N_global >= ((int64_t)1 << 31) - 1 || M < 0) return KNN_EINVAL;
+  if (n_local < 1 || row0 < 0 || row0 + n_local > N_global) return KNN_EINVAL;
+  if (L < 1 || L > n_local || row0 % L != 0) return KNN_EINVAL;
+  SearchArgs a{nullptr, nullptr, nullptr, nullptr, n_local, D, dtype, metric, nullptr, M, 1, L,
+               0.5, 1, KNN_BINS_MOD};
+  knn_status st = layout_search(a, s);
+  if (st != KNN_OK) return st;
+  *total = al(s->total) + 2 * al((size_t)M * L * 4);
+  return KNN_OK;
+}
+
+size_t knn_shard_partial_reduce_workspace(int64_t n_local, int64_t row0, int64_t N_global,
+                                          int32_t D, int32_t dtype, int32_t metric, int64_t M,
+                                          int64_t L) {
+  SearchLayout s;
+  size_t t = 0;
+  if (shard_layout(n_local, row0, N_global, D, dtype, metric, M, L, &s, &t) != KNN_OK) return 0;
+  return t;
+}
+
+knn_status knn_shard_partial_reduce(const void* db_lp, const float* db_scale,
+                                    const float* db_hnorm, int64_t n_local, int64_t row0,
+                                    int64_t N_global, int32_t D, int32_t dtype, int32_t metric,
+                                    const float* q, int64_t M, int64_t L, int64_t* keys,
+                                    void* workspace, size_t ws_bytes, void* stream) {
+  SearchLayout s;
+  size_t total = 0;
+  knn_status rc = shard_layout(n_local, row0, N_global, D, dtype, metric, M, L, &s, &total);
+  if (rc != KNN_OK) return rc;
+  if (M == 0) return KNN_OK;
+  SearchArgs a{db_lp, db_scale, db_hnorm, nullptr, n_local, D, dtype, metric, q, M, 1, L, 0.5, 1,
+               KNN_BINS_MOD};
+  if (!keys || !aligned(keys, 8)) return KNN_EINVAL;
+  if ((rc = check_pointers(a, reinterpret_cast<float*>(keys), reinterpret_cast<int32_t*>(keys))) !=
+      KNN_OK)
+    return rc;
+  if (!workspace || !aligned(workspace, kAlign)) return KNN_EINVAL;
+  if (ws_bytes < total) return KNN_ENOMEM;
+  cudaStream_t st = (cudaStream_t)stream;
+  char* ws = reinterpret_cast<char*>(workspace);
+  const float* qf32;
+  int64_t q_stride;
+  cudaError_t e = prep_queries(a, s, ws, &qf32, &q_stride, st);
+  if (e != cudaSuccess) return cuda_status(e);
+  const bool k64 = s.keys64;
+  // pair and packed partials decode their rows with the shard's offset; the
+  // 64-bit keys hold local rows, offset when they become signed keys
+  Partials parts{reinterpret_cast<float*>(ws + s.off_part_v),
+                 (dtype == KNN_F32 && !k64) ? reinterpret_cast<int32_t*>(ws + s.off_part_a)
+                                            : nullptr,
+                 k64 ? 0 : row0, s.plan.atomic_merge, k64};
+  const float* qscale = s.qb.scale ? reinterpret_cast<const float*>(ws + s.off_qscale) : nullptr;
+  e = run_k1(s.plan, a, db_lp, db_scale, db_hnorm, ws + s.off_qlp, qscale, parts, st);
+  if (e == cudaErrorNotSupported) return KNN_EUNSUPPORTED;
+  if (e != cudaSuccess) return cuda_status(e);
+  float* V = reinterpret_cast<float*>(ws + al(s.total));
+  int32_t* A = reinterpret_cast<int32_t*>(ws + al(s.total) + al((size_t)M * L * 4));
+  e = launch_merge_bins(s.plan, parts, V, A, st);
+  if (e == cudaSuccess) e = launch_pairs_to_signed_keys(V, A, M * L, k64 ? row0 : 0, keys, st);
+  return cuda_status(e);
+}
+
+int32_t knn_rescore_count(int32_t K, int32_t rerank_mult, int64_t L) {
+  if (K < 1 || L < 1 || K > L || K > kMaxK) return -1;
+  return kprime(K, rerank_mult, L);
+}
+
+size_t knn_shard_rescore_workspace(int64_t M, int64_t L, int32_t D, int32_t metric, int32_t K,
+                                   int32_t rerank_mult) {
+  if (M < 0 || D < 1 || D > kMaxD || !valid_metric(metric)) return 0;
+  const int32_t Kp = knn_rescore_count(K, rerank_mult, L);
+  if (Kp < 1) return 0;
+  size_t t = al((size_t)M * L * 8) + al((size_t)M * Kp * 8);
+  if (metric == KNN_COS) t += al((size_t)M * knn_row_pitch(D) * 4);
+  return t > kAlign ? t : kAlign;
+}
+
+knn_status knn_shard_rescore(const int64_t* keys, int64_t M, int64_t L, int32_t K,
+                             int32_t rerank_mult, const float* q, int32_t D, int32_t metric,
+                             const float* x_f32, int64_t n_local, int64_t row0,
+                             int64_t* cand_keys, void* workspace, size_t ws_bytes,
+                             void* stream) {
+  const size_t need = knn_shard_rescore_workspace(M, L, D, metric, K, rerank_mult);
+  if (need == 0 || n_local < 1 || row0 < 0 || row0 + n_local >= ((int64_t)1 << 31))
+    return KNN_EINVAL;
+  if (M == 0) return KNN_OK;
+  if (!keys || !q || !x_f32 || !cand_keys || !aligned(keys, 8) || !aligned(cand_keys, 8) ||
+      !aligned(q, 4) || !aligned(x_f32, 4))
+    return KNN_EINVAL;
+  if (!workspace || !aligned(workspace, kAlign)) return KNN_EINVAL;
+  if (ws_bytes < need) return KNN_ENOMEM;
+  const int32_t Kp = knn_rescore_count(K, rerank_mult, L);
+  cudaStream_t st = (cudaStream_t)stream;
+  char* ws = reinterpret_cast<char*>(workspace);
+  uint64_t* G = reinterpret_cast<uint64_t*>(ws);
+  uint64_t* cand = reinterpret_cast<uint64_t*>(ws + al((size_t)M * L * 8));
+  cudaError_t e = launch_signed_to_keys(keys, M * L, G, st);
+  K1Plan p{};
+  p.M = M;
+  p.L = L;
+  p.Lk = L;
+  p.g = 1;
+  p.nsplits = 1;
+  Partials parts{reinterpret_cast<float*>(G), nullptr, 0, false, true};
+  if (e == cudaSuccess) e = launch_k2(p, parts, Kp, nullptr, cand, st);
+  const float* qf = q;
+  int64_t q_stride = D;
+  if (e == cudaSuccess && metric == KNN_COS) {
+    // cosine: the candidates' unit rows against the unit queries
+    float* qn = reinterpret_cast<float*>(ws + al((size_t)M * L * 8) + al((size_t)M * Kp * 8));
+    const int pitch = knn_row_pitch(D);
+    e = launch_prep(q, M, D, pitch, KNN_COS, KNN_F32, qn, nullptr, nullptr, nullptr, st);
+    qf = qn;
+    q_stride = pitch;
+  }
+  if (e == cudaSuccess)
+    e = launch_score_owned(cand, M, Kp, qf, q_stride, x_f32, n_local, row0, D, metric, cand_keys,
+                           st);
+  return cuda_status(e);
+}
+
+size_t knn_shard_finish_workspace(int64_t M, int32_t Kp, int32_t K) {
+  if (M < 0 || K < 1 || Kp < K || Kp > kMaxK) return 0;
+  const size_t t = al((size_t)M * Kp * 8) + al((size_t)M * K * 8);
+  return t > kAlign ? t : kAlign;
+}
+
+knn_status knn_shard_finish(const int64_t* cand_keys, int64_t M, int32_t Kp, int32_t K,
+                            int32_t metric, float* out_val, int32_t* out_idx, void* workspace,
+                            size_t ws_bytes, void* stream) {
+  const size_t need = knn_shard_finish_workspace(M, Kp, K);
+  if (need == 0 || !valid_metric(metric)) return KNN_EINVAL;
+  if (M == 0) return KNN_OK;
+  if (!cand_keys || !out_val || !out_idx || !aligned(cand_keys, 8) || !aligned(out_val, 4) ||
+      !aligned(out_idx, 4))
+    return KNN_EINVAL;
+  if (!workspace || !aligned(workspace, kAlign)) return KNN_EINVAL;
+  if (ws_bytes < need) return KNN_ENOMEM;
+  cudaStream_t st = (cudaStream_t)stream;
+  char* ws = reinterpret_cast<char*>(workspace);
+  uint64_t* C = reinterpret_cast<uint64_t*>(ws);
+  uint64_t* top = reinterpret_cast<uint64_t*>(ws + al((size_t)M * Kp * 8));
+  cudaError_t e = launch_signed_to_keys(cand_keys, M * Kp, C, st);
+  K1Plan p{};
+  p.M = M;
+  p.L = Kp;
+  p.Lk = Kp;
+  p.g = 1;
+  p.nsplits = 1;
+  Partials parts{reinterpret_cast<float*>(C), nullptr, 0, false, true};
+  if (e == cudaSuccess) e = launch_k2(p, parts, K, nullptr, top, st);
+  // internal scores are larger-is-better: L2 reports the squared distance
+  if (e == cudaSuccess)
+    e = launch_keys_to_pairs(top, M * K, metric == KNN_L2 ? 1 : 0, out_val, out_idx, st);
+  return cuda_status(e);
+}
+
+// ---------------------------------------------------------------------------
 // Library-owned database (knn_db_*): the prepared rows and their side arrays
 // in device memory the handle allocates and frees.
 // ---------------------------------------------------------------------------

@@ -133,7 +133,7 @@ k1_tc_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CU
       int issued = 0, s = 0;
       uint32_t ph = 0;
       for (int it = 0; it < nt; ++it) {
-        if (it >= S && !mbar_wait_sleep(b_empty + 8 * s, ph ^ 1u, abort_flag, 64)) break;
+        if (it >= S && !mbar_wait_sleep(b_empty + 8 * s, ph ^ 1u, abort_flag)) break;
         mbar_expect_tx(b_full + 8 * s, a.stage_bytes);
         const int row0 = (int)((t_begin + it) * a.Lk + strip * kRows);
         uint8_t* dst = sA + (size_t)s * a.stage_bytes;
@@ -236,7 +236,7 @@ k1_tc_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CU
         if (DT == KNN_E4M3) mul_n = a.xscale[jn];
       }
     }
-    if (!warp_all(mbar_wait_sleep(b_accf + 8 * ab, aph, abort_flag, 128))) break;
+    if (!warp_all(mbar_wait_sleep(b_accf + 8 * ab, aph, abort_flag))) break;
     tc_fence_after();
     // invalid lanes turn every key into -inf: no divergence, no extra select
     const uint32_t km = valid ? nmask : 0u;

@@ -239,7 +239,7 @@ k1_tcs_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
     // the segment's query tile (phase sg of b_q); from the second segment on
     // only after the MMAs of the previous one are done with the old tile
     if (MODE != kKLoopQ && sg > 0 &&
-        !warp_all(mbar_wait_sleep(b_qe, (uint32_t)((sg - 1) & 1), abort_flag, 64)))
+        !warp_all(mbar_wait_sleep(b_qe, (uint32_t)((sg - 1) & 1), abort_flag)))
       break;
     q_armed = sg + 1;
     if (lane == 0) {
@@ -257,7 +257,7 @@ k1_tcs_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
     int64_t bg = s_begin / a.ntg, tg = s_begin % a.ntg;
     const int total = ns * NKB;
     for (int g = 0; g < total; ++g) {
-      if (issued >= S && !warp_all(mbar_wait_sleep(b_empty + 8 * s, ph ^ 1u, abort_flag, 64))) {
+      if (issued >= S && !warp_all(mbar_wait_sleep(b_empty + 8 * s, ph ^ 1u, abort_flag))) {
         prun = false;
         break;
       }
@@ -531,7 +531,7 @@ k1_tcs_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
         const int e = i & 1;
         int ok = 1;
         if (lane == 0 && i >= kExtSlotsS)
-          ok = mbar_wait_sleep(b_xe + 8 * e, (uint32_t)(((i >> 1) & 1) ^ 1), abort_flag, 64) ? 1
+          ok = mbar_wait_sleep(b_xe + 8 * e, (uint32_t)(((i >> 1) & 1) ^ 1), abort_flag) ? 1
                                                                                            : 0;
         ok = __shfl_sync(0xffffffffu, ok, 0);
         if (!ok) {
@@ -599,7 +599,7 @@ k1_tcs_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
     brow = -1;
     for (int li = 0; li < ns; ++li) {
       const int i = sg * ns + li;
-      if (!warp_all(mbar_wait_sleep(b_accf + 8 * h, (uint32_t)(i & 1), abort_flag, 32))) {
+      if (!warp_all(mbar_wait_sleep(b_accf + 8 * h, (uint32_t)(i & 1), abort_flag))) {
         erun = false;
         break;
       }
@@ -696,7 +696,7 @@ k1_tcs_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
   tg = s_begin % a.ntg;
   for (int li = 0; li < ns; ++li) {
     const int i = sg * ns + li;
-    if (!warp_all(mbar_wait_sleep(b_accf + 8 * h, (uint32_t)(i & 1), abort_flag, 32))) {
+    if (!warp_all(mbar_wait_sleep(b_accf + 8 * h, (uint32_t)(i & 1), abort_flag))) {
       erun = false;
       break;
     }

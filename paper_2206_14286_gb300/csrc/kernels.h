@@ -118,6 +118,16 @@ size_t backward_ws_bytes(int64_t N, int64_t M, int K, int deterministic);
 // (256 or 128), or 0 if the rows are too long.
 int k1_tc_query_tile(int dtype, int D);
 
+// N-sharded search (shard.cu): PartialReduce pairs -> signed-order keys with
+// global indices; signed keys -> keys; FP32 scores of the candidates a shard
+// holds, as signed keys (empty for the others).
+cudaError_t launch_pairs_to_signed_keys(const float* v, const int32_t* a, int64_t n, int64_t add,
+                                        int64_t* out, cudaStream_t st);
+cudaError_t launch_signed_to_keys(const int64_t* in, int64_t n, uint64_t* out, cudaStream_t st);
+cudaError_t launch_score_owned(const uint64_t* cand, int64_t M, int Kp, const float* q,
+                               int64_t q_stride, const float* x, int64_t n_local, int64_t row0,
+                               int D, int metric, int64_t* out, cudaStream_t st);
+
 // Issue-rate microbenchmark (knn_measure_rate): operations per second of one
 // instruction kind over a grid that fills every SM.
 cudaError_t measure_rate(int kind, int64_t iters, double* ops_per_s, double* ms,

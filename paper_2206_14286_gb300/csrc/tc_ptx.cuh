@@ -16,6 +16,11 @@ constexpr uint64_t kTimeoutNs = 2000000000ull;
 // lower it (knn_set_wait_limit_ns) to make a wait run out in a test. The
 // drain waits after a give-up (mbar_drain) keep kTimeoutNs.
 static __device__ unsigned long long g_tc_wait_limit_ns = kTimeoutNs;
+// Limits below this (under the global timer's resolution) make a pipeline wait
+// give up at its first check instead of comparing times.
+constexpr uint64_t kImmediateNs = 1000;
+// Suspend-time hint of one mbarrier.try_wait probe in the sleeping waits.
+constexpr uint32_t kSuspendHintNs = 20000;
 
 namespace {
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -55,6 +60,21 @@ __device__ __forceinline__ bool mbar_test_wait(uint32_t bar, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
+// Potentially suspending probe: if the phase is not complete the thread may
+// be suspended until it completes or about `hint_ns` pass (the hardware's
+// time limit may be shorter), so a waiting warp issues almost nothing.
+__device__ __forceinline__ bool mbar_try_wait_hint(uint32_t bar, uint32_t parity,
+                                                   uint32_t hint_ns) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity), "r"(hint_ns)
+      : "memory");
+  return ok != 0;
+}
 __device__ __forceinline__ uint64_t global_ns() {
   uint64_t t;
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
@@ -71,11 +91,12 @@ __device__ __forceinline__ uint64_t wait_limit_ns() {
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag) {
   if (mbar_test_wait(bar, parity)) return true;
   const uint64_t t0 = global_ns();
+  const uint64_t lim = wait_limit_ns();
   for (uint32_t n = 1;; ++n) {
     if (mbar_test_wait(bar, parity)) return true;
-    if ((n & 1023) == 0) {
+    if (n == 1 || (n & 1023) == 0) {
       if (*abort_flag) return false;
-      if (global_ns() - t0 > wait_limit_ns()) {
+      if (lim < kImmediateNs || global_ns() - t0 > lim) {
         *abort_flag = 1;
         atomicExch(&g_tc_timeout, 1u);
         return false;
@@ -83,24 +104,22 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatil
     }
   }
 }
-// Bounded wait for roles with slack (producer, epilogue, ...): between polls
-// the warp sleeps for about `ns` nanoseconds, so that its polling does not
-// compete with the tensor core for shared-memory bandwidth.
+// Bounded wait for roles with slack (producer, epilogue, ...): the warp
+// waits suspended in mbarrier.try_wait (woken when the phase completes), so
+// its polling does not take issue slots from the roles that work.
 __device__ __forceinline__ bool mbar_wait_sleep(uint32_t bar, uint32_t parity,
-                                                volatile int* abort_flag, uint32_t ns) {
+                                                volatile int* abort_flag) {
   if (mbar_test_wait(bar, parity)) return true;
   const uint64_t t0 = global_ns();
-  for (uint32_t n = 1;; ++n) {
-    __nanosleep(ns);
-    if (mbar_test_wait(bar, parity)) return true;
-    if ((n & 15) == 0) {
-      if (*abort_flag) return false;
-      if (global_ns() - t0 > wait_limit_ns()) {
-        *abort_flag = 1;
-        atomicExch(&g_tc_timeout, 1u);
-        return false;
-      }
+  const uint64_t lim = wait_limit_ns();
+  for (;;) {
+    if (*abort_flag) return false;
+    if (lim < kImmediateNs || global_ns() - t0 > lim) {
+      *abort_flag = 1;
+      atomicExch(&g_tc_timeout, 1u);
+      return false;
     }
+    if (mbar_try_wait_hint(bar, parity, kSuspendHintNs)) return true;
   }
 }
 // Wait used on the way out after a give-up: the copies and MMAs a CTA has

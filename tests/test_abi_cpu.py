@@ -146,3 +146,16 @@ def test_db_handle_rejects_bad_arguments_without_a_device(lib):
     assert lib.knn_db_search_workspace(None, 10, 5, 64, 0, 0.95, 2) == 0
     assert lib.knn_db_search(None, None, 10, 5, 64, 0, 0.95, 2, None, None, None, 0,
                              None) == _lib.KNN_EINVAL
+
+
+def test_shard_calls_reject_bad_layouts(lib):
+    """Host-side checks of the sharded calls' layout rules (no launch)."""
+    f = lib.knn_shard_partial_reduce_workspace
+    # (n_local, row0, N_global, D, dtype, metric, M, L)
+    assert f(1000, 0, 3000, 64, 1, 1, 10, 128) > 0
+    assert f(1000, 100, 3000, 64, 1, 1, 10, 128) == 0       # row0 not a multiple of L
+    assert f(100, 0, 3000, 64, 1, 1, 10, 128) == 0          # L > n_local
+    assert f(1000, 2560, 3000, 64, 1, 1, 10, 128) == 0      # past N_global
+    assert lib.knn_rescore_count(10, 2, 128) == 20
+    assert lib.knn_rescore_count(10, 2, 15) == 15
+    assert lib.knn_rescore_count(11, 1, 10) == -1
