@@ -103,7 +103,7 @@ int64_t plan_bins(int64_t N, int K, double r, int round_to) {
 void k1_tile(int dtype, int D, int64_t M, int* BW, int* BQ) {
   if (dtype == KNN_F32) {
     *BW = 64;
-    *BQ = 64;
+    *BQ = 128;
   } else {
     *BW = 128;
     const int maxq = k1_tc_query_tile(dtype, D);

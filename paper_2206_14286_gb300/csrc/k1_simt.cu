@@ -1,30 +1,35 @@
 // k1_simt.cu -- PartialReduce (Alg. 1) fused with an FP32 SIMT contraction.
 //
 // The plain FP32 path: no tensor cores, exact FP32 scores and exact indices.
-// Tiling follows Alg. 2 (App. A.3): a block of BQ = 64 queries stays fixed
+// Tiling follows Alg. 2 (App. A.3): a block of BQ = 128 queries stays fixed
 // while the CTA walks tiles of BW = 64 database rows; the D loop runs in
-// chunks of 16 through shared memory with FFMA on a 4 x 4 register tile per
-// thread; after each tile the compare/select of Alg. 1 (strict '>' while the
-// row index grows, so ties keep the smaller index) updates the running best
-// of each (query, bin) the thread owns. A thread owns 4 queries x 4 bins and
-// the bins never change across tiles (tile t covers rows t*Lk + strip*64 +
-// [0, 64)), so the running state lives in registers and only M x L partials
-// per split reach memory (Eq. 20's 2*4*M*L output bytes per split).
+// chunks of BD = 16 through double-buffered shared memory (the next chunk's
+// global loads are in registers while the current chunk is multiplied), with
+// FFMA on an 8 x 4 register tile per thread; after each tile the
+// compare/select of Alg. 1 (strict '>' while the row index grows, so ties
+// keep the smaller index) updates the running best of each (query, bin) the
+// thread owns. A thread owns 8 queries x 4 bins and the bins never change
+// across tiles (tile t covers rows t*Lk + strip*64 + [0, 64)), so the running
+// state lives in registers and only M x L partials per split reach memory
+// (Eq. 20's 2*4*M*L output bytes per split).
 #include "common.cuh"
 #include "kernels.h"
 
 namespace tpuknn {
 
 namespace {
-constexpr int BQ = 64, BW = 64, BD = 16, PADW = 68;
+constexpr int BQ = 128, BW = 64, BD = 16;
+constexpr int PADQ = BQ + 4, PADW = BW + 4;  // row padding of the transposed tiles
+constexpr int TQ = 8, TB = 4;                // queries x bins per thread
+constexpr int kSimtThreads = 256;            // (BQ / TQ) x (BW / TB) threads
 
 template <int METRIC>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(kSimtThreads, 2)
 k1_simt_kernel(const float* __restrict__ X, const float* __restrict__ hnorm,
                const float* __restrict__ Qp, K1Plan p, float* __restrict__ part_v,
                int32_t* __restrict__ part_a) {
-  __shared__ __align__(16) float Qs[BD][PADW];
-  __shared__ __align__(16) float Xs[BD][PADW];
+  __shared__ __align__(16) float Qs[2][BD][PADQ];
+  __shared__ __align__(16) float Xs[2][BD][PADW];
   const int tid = threadIdx.x, tq = tid >> 4, tb = tid & 15;
   int64_t cta = blockIdx.x;
   const int64_t qtile = cta % p.nqtiles;
@@ -35,67 +40,94 @@ k1_simt_kernel(const float* __restrict__ X, const float* __restrict__ hnorm,
   const int64_t t_begin = split * p.tiles_per_split;
   const int64_t t_end = min(p.ntiles, t_begin + p.tiles_per_split);
 
-  float v[4][4];
-  int32_t a[4][4];
+  float v[TQ][TB];
+  int32_t a[TQ][TB];
 #pragma unroll
-  for (int r = 0; r < 4; ++r)
+  for (int r = 0; r < TQ; ++r)
 #pragma unroll
-    for (int c = 0; c < 4; ++c) {
+    for (int c = 0; c < TB; ++c) {
       v[r][c] = neg_inf();
       a[r][c] = -1;
     }
 
-  // loader mapping: 64 rows x 16 columns, one float4 per thread
+  // loader mapping: a chunk is BQ query rows and BW database rows of BD
+  // floats; thread tid loads the float4 at column lcol of rows lrow (and
+  // lrow + 64 for the queries)
   const int lrow = tid >> 2, lcol = (tid & 3) * 4;
-  const int64_t qrow = i0 + lrow;
-  const bool qvalid = qrow < p.M;
+  const bool qv0 = i0 + lrow < p.M, qv1 = i0 + lrow + 64 < p.M;
+  const float* qp0 = Qp + (qv0 ? (i0 + lrow) * p.pitch + lcol : 0);
+  const float* qp1 = Qp + (qv1 ? (i0 + lrow + 64) * p.pitch + lcol : 0);
+  const int nchunks = p.pitch / BD;
 
   for (int64_t t = t_begin; t < t_end; ++t) {
     const int64_t row0 = t * p.Lk + b0;
     const int64_t xrow = row0 + lrow;
     const bool xvalid = (b0 + lrow < p.Lk) && (xrow < p.N);
-    float acc[4][4];
+    const float* xp = X + (xvalid ? xrow * p.pitch + lcol : 0);
+    float acc[TQ][TB];
 #pragma unroll
-    for (int r = 0; r < 4; ++r)
+    for (int r = 0; r < TQ; ++r)
 #pragma unroll
-      for (int c = 0; c < 4; ++c) acc[r][c] = 0.0f;
+      for (int c = 0; c < TB; ++c) acc[r][c] = 0.0f;
 
-    for (int d0 = 0; d0 < p.pitch; d0 += BD) {
-      float4 qv = qvalid ? *reinterpret_cast<const float4*>(Qp + qrow * p.pitch + d0 + lcol)
-                         : make_float4(0.f, 0.f, 0.f, 0.f);
-      float4 xv = xvalid ? *reinterpret_cast<const float4*>(X + xrow * p.pitch + d0 + lcol)
-                         : make_float4(0.f, 0.f, 0.f, 0.f);
-      __syncthreads();
-      Qs[lcol + 0][lrow] = qv.x;
-      Qs[lcol + 1][lrow] = qv.y;
-      Qs[lcol + 2][lrow] = qv.z;
-      Qs[lcol + 3][lrow] = qv.w;
-      Xs[lcol + 0][lrow] = xv.x;
-      Xs[lcol + 1][lrow] = xv.y;
-      Xs[lcol + 2][lrow] = xv.z;
-      Xs[lcol + 3][lrow] = xv.w;
-      __syncthreads();
+    auto fetch = [&](int d0, float4& q0, float4& q1, float4& x0) {
+      const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+      q0 = qv0 ? __ldg(reinterpret_cast<const float4*>(qp0 + d0)) : z;
+      q1 = qv1 ? __ldg(reinterpret_cast<const float4*>(qp1 + d0)) : z;
+      x0 = xvalid ? __ldg(reinterpret_cast<const float4*>(xp + d0)) : z;
+    };
+    auto stash = [&](int buf, const float4& q0, const float4& q1, const float4& x0) {
+      Qs[buf][lcol + 0][lrow] = q0.x;
+      Qs[buf][lcol + 1][lrow] = q0.y;
+      Qs[buf][lcol + 2][lrow] = q0.z;
+      Qs[buf][lcol + 3][lrow] = q0.w;
+      Qs[buf][lcol + 0][lrow + 64] = q1.x;
+      Qs[buf][lcol + 1][lrow + 64] = q1.y;
+      Qs[buf][lcol + 2][lrow + 64] = q1.z;
+      Qs[buf][lcol + 3][lrow + 64] = q1.w;
+      Xs[buf][lcol + 0][lrow] = x0.x;
+      Xs[buf][lcol + 1][lrow] = x0.y;
+      Xs[buf][lcol + 2][lrow] = x0.z;
+      Xs[buf][lcol + 3][lrow] = x0.w;
+    };
+    float4 nq0, nq1, nx0;
+    fetch(0, nq0, nq1, nx0);
+    // the previous tile's last chunk may still be read from buffer 0 or 1:
+    // every thread has passed its compare/select before buffers are refilled
+    __syncthreads();
+    stash(0, nq0, nq1, nx0);
+    __syncthreads();
+    for (int ch = 0; ch < nchunks; ++ch) {
+      const int buf = ch & 1;
+      if (ch + 1 < nchunks) fetch((ch + 1) * BD, nq0, nq1, nx0);
 #pragma unroll
       for (int dd = 0; dd < BD; ++dd) {
-        float4 q4 = *reinterpret_cast<const float4*>(&Qs[dd][tq * 4]);
-        float4 x4 = *reinterpret_cast<const float4*>(&Xs[dd][tb * 4]);
-        float qa[4] = {q4.x, q4.y, q4.z, q4.w};
-        float xa[4] = {x4.x, x4.y, x4.z, x4.w};
+        const float4 qa4 = *reinterpret_cast<const float4*>(&Qs[buf][dd][tq * TQ]);
+        const float4 qb4 = *reinterpret_cast<const float4*>(&Qs[buf][dd][tq * TQ + 4]);
+        const float4 x4 = *reinterpret_cast<const float4*>(&Xs[buf][dd][tb * TB]);
+        const float qa[TQ] = {qa4.x, qa4.y, qa4.z, qa4.w, qb4.x, qb4.y, qb4.z, qb4.w};
+        const float xa[TB] = {x4.x, x4.y, x4.z, x4.w};
 #pragma unroll
-        for (int r = 0; r < 4; ++r)
+        for (int r = 0; r < TQ; ++r)
 #pragma unroll
-          for (int c = 0; c < 4; ++c) acc[r][c] = fmaf(qa[r], xa[c], acc[r][c]);
+          for (int c = 0; c < TB; ++c) acc[r][c] = fmaf(qa[r], xa[c], acc[r][c]);
+      }
+      if (ch + 1 < nchunks) {
+        // the other buffer was last read in chunk ch - 1, before the barrier
+        // that ended it
+        stash(buf ^ 1, nq0, nq1, nx0);
+        __syncthreads();
       }
     }
     // Alg. 1 compare/select per (query, bin)
 #pragma unroll
-    for (int c = 0; c < 4; ++c) {
-      const int64_t b = b0 + tb * 4 + c;
-      const int64_t j = row0 + tb * 4 + c;
+    for (int c = 0; c < TB; ++c) {
+      const int64_t b = b0 + tb * TB + c;
+      const int64_t j = row0 + tb * TB + c;
       const bool valid = (b < p.Lk) && (j < p.N);
       const float hb = (METRIC == KNN_L2 && valid) ? hnorm[j] : 0.0f;
 #pragma unroll
-      for (int r = 0; r < 4; ++r) {
+      for (int r = 0; r < TQ; ++r) {
         const float s = acc[r][c] - hb;
         if (valid && s > v[r][c]) {
           v[r][c] = s;
@@ -106,12 +138,12 @@ k1_simt_kernel(const float* __restrict__ X, const float* __restrict__ hnorm,
   }
   // partials of this split
 #pragma unroll
-  for (int r = 0; r < 4; ++r) {
-    const int64_t i = i0 + tq * 4 + r;
+  for (int r = 0; r < TQ; ++r) {
+    const int64_t i = i0 + tq * TQ + r;
     if (i >= p.M) continue;
 #pragma unroll
-    for (int c = 0; c < 4; ++c) {
-      const int64_t b = b0 + tb * 4 + c;
+    for (int c = 0; c < TB; ++c) {
+      const int64_t b = b0 + tb * TB + c;
       if (b >= p.Lk) continue;
       const int64_t o = (split * p.M + i) * p.Lk + b;
       part_v[o] = v[r][c];
@@ -128,9 +160,11 @@ cudaError_t launch_k1_simt(const K1Plan& p, const float* X, const float* hnorm, 
   if (blocks <= 0) return cudaSuccess;
   if (blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
   if (p.metric == KNN_L2)
-    k1_simt_kernel<KNN_L2><<<(unsigned)blocks, 256, 0, st>>>(X, hnorm, Qp, p, out.v, out.a);
+    k1_simt_kernel<KNN_L2><<<(unsigned)blocks, kSimtThreads, 0, st>>>(X, hnorm, Qp, p, out.v,
+                                                                       out.a);
   else
-    k1_simt_kernel<KNN_IP><<<(unsigned)blocks, 256, 0, st>>>(X, hnorm, Qp, p, out.v, out.a);
+    k1_simt_kernel<KNN_IP><<<(unsigned)blocks, kSimtThreads, 0, st>>>(X, hnorm, Qp, p, out.v,
+                                                                       out.a);
   return cudaGetLastError();
 }
 

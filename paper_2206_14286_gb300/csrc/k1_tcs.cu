@@ -57,14 +57,26 @@ namespace {
 constexpr int kThreadsS = 640;   // 4 control warps + 4 epilogue warpgroups
 constexpr int kQH = 128;         // queries per half: MMA M, TMEM lanes
 constexpr int kQT = 256;         // queries per CTA
-constexpr int kBinsStep = 16;    // bins per step
 constexpr int kRowsBin = 16;     // grid rows per bin per step
-constexpr int kCols = kBinsStep * kRowsBin;  // 256 = MMA N
 constexpr int kSpanS = 128;      // bytes of one 128-byte swizzle span (one K block)
-constexpr int kStageS = kCols * kSpanS;      // 32 KB: one K block of a step
 constexpr int kExtAS = kQH * 32;             // ones block (K = 16 BF16)
-constexpr int kExtBS = kCols * 32;           // half-norm block of a step
-constexpr int kExtSlotsS = 2;
+
+// Step layouts: BS bins x 16 grid rows (or BS * 16 consecutive rows) per step.
+//   BS = 16: MMA N = 256, one accumulator per query half, 32 KB stages; the
+//            layout of the K-loop modes (rows longer than 128 elements).
+//   BS = 8 : MMA N = 128, two accumulators per query half (a step's MMAs
+//            write the buffer the step before last used, so they never wait
+//            for the previous step's drain), 16 KB stages: twice as many steps
+//            fit in the ring, which hides more of the load latency.
+template <int BS>
+struct StepT {
+  static constexpr int kCols = BS * kRowsBin;   // MMA N, accumulator columns
+  static constexpr int kStage = kCols * kSpanS; // one K block of a step
+  static constexpr int kExtB = kCols * 32;      // half-norm block of a step
+  static constexpr int kNB = BS == 8 ? 2 : 1;   // accumulators per query half
+  static constexpr int kXS = BS == 8 ? 4 : 2;   // half-norm block slots
+  static constexpr int kBPW = BS / 2;           // bins per epilogue warpgroup
+};
 // Register split (setmaxnreg): the control warpgroup gives up registers so
 // the epilogue can keep four 16-column runs in flight. 128*64 + 512*104 =
 // 61440 = 640*96, the registers the kernel is launched with (checked on the
@@ -145,10 +157,13 @@ __device__ __forceinline__ int64_t run_bin_end(int64_t b, int64_t q, int64_t r) 
   return (b + 1) * q + min(b + 1, r);
 }
 
-template <int NKS, int MODE, int BM>
+template <int NKS, int MODE, int BM, int BS>
 __global__ void __launch_bounds__(kThreadsS, 1)
 k1_tcs_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmQ,
               const TcsArgs a) {
+  using T = StepT<BS>;
+  constexpr int kCols = T::kCols, NB = T::kNB, XS = T::kXS, BPW = T::kBPW;
+  static_assert(MODE == kFused || BS == 16, "the K-loop modes use 16-bin steps");
   // 128-byte K blocks per step
   const int NKB = MODE == kFused ? (NKS + 3) / 4 : a.nkb;
   extern __shared__ uint8_t smem_raw[];
@@ -158,16 +173,19 @@ k1_tcs_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
   uint8_t* sA = smem;                                      // queries, SW128, [kb][256][128 B]
   uint8_t* sB = sA + a.a_bytes;                            // S stages of one K block
   uint8_t* sAext = sB + (size_t)S * a.stage_bytes;         // ones block (L2)
-  uint8_t* sBext = sAext + (a.ext ? kExtAS : 0);           // 2 half-norm blocks (L2)
-  uint64_t* bars = reinterpret_cast<uint64_t*>(sBext + (a.ext ? kExtSlotsS * kExtBS : 0));
+  uint8_t* sBext = sAext + (a.ext ? kExtAS : 0);           // XS half-norm blocks (L2)
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sBext + (a.ext ? XS * T::kExtB : 0));
+  // accumulator (h, buf) of query half h: barriers b_accf / b_acce + 8 (h NB + buf),
+  // TMEM columns (h NB + buf) kCols
+  constexpr int NACC = 2 * NB;
   const uint32_t b_full = smem_u32(bars), b_empty = smem_u32(bars + S);
-  const uint32_t b_accf = smem_u32(bars + 2 * S), b_acce = smem_u32(bars + 2 * S + 2);
-  const uint32_t b_xf = smem_u32(bars + 2 * S + 4);
-  const uint32_t b_xe = smem_u32(bars + 2 * S + 4 + kExtSlotsS);
-  const uint32_t b_q = smem_u32(bars + 2 * S + 4 + 2 * kExtSlotsS);
-  const uint32_t b_done = smem_u32(bars + 2 * S + 5 + 2 * kExtSlotsS);
-  const uint32_t b_qe = smem_u32(bars + 2 * S + 6 + 2 * kExtSlotsS);
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * S + 7 + 2 * kExtSlotsS);
+  const uint32_t b_accf = smem_u32(bars + 2 * S), b_acce = smem_u32(bars + 2 * S + NACC);
+  const uint32_t b_xf = smem_u32(bars + 2 * S + 2 * NACC);
+  const uint32_t b_xe = smem_u32(bars + 2 * S + 2 * NACC + XS);
+  const uint32_t b_q = smem_u32(bars + 2 * S + 2 * NACC + 2 * XS);
+  const uint32_t b_done = smem_u32(bars + 2 * S + 2 * NACC + 2 * XS + 1);
+  const uint32_t b_qe = smem_u32(bars + 2 * S + 2 * NACC + 2 * XS + 2);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * S + 2 * NACC + 2 * XS + 3);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -190,11 +208,11 @@ k1_tcs_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
       mbar_init(b_full + 8 * s, 1);
       mbar_init(b_empty + 8 * s, 1);
     }
-    for (int h = 0; h < 2; ++h) {
-      mbar_init(b_accf + 8 * h, 1);
-      mbar_init(b_acce + 8 * h, 8);
+    for (int c = 0; c < NACC; ++c) {
+      mbar_init(b_accf + 8 * c, 1);
+      mbar_init(b_acce + 8 * c, 8);  // the 8 warps of the two warpgroups of a half
     }
-    for (int e = 0; e < kExtSlotsS; ++e) {
+    for (int e = 0; e < XS; ++e) {
       mbar_init(b_xf + 8 * e, 1);
       mbar_init(b_xe + 8 * e, 1);
     }
@@ -213,8 +231,8 @@ k1_tcs_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
       *reinterpret_cast<uint4*>(sAext + ext_off_s(r, 0)) = *reinterpret_cast<uint4*>(v);
       *reinterpret_cast<uint4*>(sAext + ext_off_s(r, 1)) = make_uint4(0, 0, 0, 0);
     }
-    for (int t = threadIdx.x; t < kExtSlotsS * kCols; t += kThreadsS)
-      *reinterpret_cast<uint4*>(sBext + (size_t)(t / kCols) * kExtBS + ext_off_s(t % kCols, 1)) =
+    for (int t = threadIdx.x; t < XS * kCols; t += kThreadsS)
+      *reinterpret_cast<uint4*>(sBext + (size_t)(t / kCols) * T::kExtB + ext_off_s(t % kCols, 1)) =
           make_uint4(0, 0, 0, 0);
     fence_proxy_async_smem();
   }
@@ -267,18 +285,18 @@ k1_tcs_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
         if (MODE == kKLoopQ) {
           // the queries' K block first: [256 queries][128 B]
           tma_load_2d(dst, &tmQ, b_full + 8 * s, kb * (kSpanS / 2), (int)(qtile * kQT));
-          dst += kStageS;
+          dst += kQT * kSpanS;
         }
         if constexpr (BM == kBinsRun) {
-          // 256 consecutive rows; rows past N read the fill value (zero)
+          // kCols consecutive rows; rows past N read the fill value (zero)
           tma_load_2d(dst, &tmX, b_full + 8 * s, kb * (kSpanS / 2),
                       (int)((s_begin + g / NKB) * kCols));
         } else {
           // one box: K block kb (64 elements), grid rows tg*16 .. +15, bins
-          // bg*16 .. +15, landing as [bin][grid row][128 B]; bins past L, rows
-          // past T and elements past the row read the fill value (zero)
+          // bg*BS .. +BS-1, landing as [bin][grid row][128 B]; bins past L,
+          // rows past T and elements past the row read the fill value (zero)
           tma_load_3d(dst, &tmX, b_full + 8 * s, kb * (kSpanS / 2), (int)(tg * kRowsBin),
-                      (int)(bg * kBinsStep));
+                      (int)(bg * BS));
         }
       }
       __syncwarp();
@@ -330,7 +348,8 @@ k1_tcs_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
       if (!warp_all(mbar_wait(b_q, (uint32_t)(sg & 1), abort_flag))) break;
       for (int li = 0; li < ns && run; ++li) {
         const int i = sg * ns + li;
-        const int e = i & 1;
+        const int e = i % XS;
+        const int buf = NB == 2 ? (i & 1) : 0;
         // the stages of this step (NKB consecutive ring slots)
         int sk[(NKS + 3) / 4];
         {
@@ -349,33 +368,35 @@ k1_tcs_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
           ph0 = ph;
         }
         if (!run) break;
-        if (a.ext && !warp_all(mbar_wait(b_xf + 8 * e, (uint32_t)((i >> 1) & 1), abort_flag))) {
+        if (a.ext && !warp_all(mbar_wait(b_xf + 8 * e, (uint32_t)((i / XS) & 1), abort_flag))) {
           run = false;
           break;
         }
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
-          if (i >= 1 &&
-              !warp_all(mbar_wait(b_acce + 8 * h, (uint32_t)((i & 1) ^ 1), abort_flag))) {
+          // the accumulator's previous use (step i - NB) has been drained
+          const int c = h * NB + buf;
+          if (i >= NB &&
+              !warp_all(mbar_wait(b_acce + 8 * c, (uint32_t)(((i / NB) & 1) ^ 1), abort_flag))) {
             run = false;
             break;
           }
           tc_fence_after();
           if (lane == 0) {
-            const uint32_t d_tmem = tmem_base + (uint32_t)(h * kCols);
+            const uint32_t d_tmem = tmem_base + (uint32_t)(c * kCols);
             const uint64_t ah = a_desc + (uint64_t)((h * kQH * kSpanS) >> 4);
 #pragma unroll
             for (int ks = 0; ks < NKS; ++ks) {
               // descriptors advance by (bytes >> 4) in their address field
               const uint64_t ad = ah + (uint64_t)(((ks >> 2) * kQT * kSpanS + (ks & 3) * 32) >> 4);
               const uint64_t bd =
-                  b_desc + (uint64_t)((sk[ks >> 2] * kStageS + (ks & 3) * 32) >> 4);
+                  b_desc + (uint64_t)((sk[ks >> 2] * T::kStage + (ks & 3) * 32) >> 4);
               tc_mma<KNN_BF16>(d_tmem, ad, bd, a.idesc, ks > 0 ? 1u : 0u);
             }
             if (a.ext)
-              tc_mma<KNN_BF16>(d_tmem, ax_desc, bx_desc + (uint64_t)((e * kExtBS) >> 4), a.idesc,
-                               1u);
-            tc_commit(b_accf + 8 * h);
+              tc_mma<KNN_BF16>(d_tmem, ax_desc, bx_desc + (uint64_t)((e * T::kExtB) >> 4),
+                               a.idesc, 1u);
+            tc_commit(b_accf + 8 * c);
             if (h == 1) {
 #pragma unroll
               for (int kb = 0; kb < NKB; ++kb) tc_commit(b_empty + 8 * sk[kb]);
@@ -403,7 +424,7 @@ k1_tcs_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
       if (!warp_all(mbar_wait(b_q, (uint32_t)(sg & 1), abort_flag))) break;
       for (int li = 0; li < ns && run; ++li) {
         const int i = sg * ns + li;
-        const int e = i & 1;
+        const int e = i % XS;
         // both accumulators are written from the first K block on
         if (i >= 1 && (!warp_all(mbar_wait(b_acce, (uint32_t)((i & 1) ^ 1), abort_flag)) ||
                        !warp_all(mbar_wait(b_acce + 8, (uint32_t)((i & 1) ^ 1), abort_flag)))) {
@@ -418,7 +439,7 @@ k1_tcs_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
           tc_fence_after();
           if (lane == 0) {
             const uint32_t st = smem_u32(sB + (size_t)s * a.stage_bytes);
-            const uint64_t bd = smem_desc_sw128(MODE == kKLoopQ ? st + kStageS : st);
+            const uint64_t bd = smem_desc_sw128(MODE == kKLoopQ ? st + kQT * kSpanS : st);
             const int steps = min(4, a.nksteps - kb * 4);
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
@@ -444,7 +465,7 @@ k1_tcs_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
         }
         if (!run) break;
         if (a.ext) {
-          if (!warp_all(mbar_wait(b_xf + 8 * e, (uint32_t)((i >> 1) & 1), abort_flag))) {
+          if (!warp_all(mbar_wait(b_xf + 8 * e, (uint32_t)((i / XS) & 1), abort_flag))) {
             run = false;
             break;
           }
@@ -455,7 +476,7 @@ k1_tcs_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
 #pragma unroll
             for (int h = 0; h < 2; ++h)
               tc_mma<KNN_BF16>(tmem_base + (uint32_t)(h * kCols), ax_desc,
-                               bx_desc + (uint64_t)((e * kExtBS) >> 4), a.idesc, 1u);
+                               bx_desc + (uint64_t)((e * T::kExtB) >> 4), a.idesc, 1u);
             tc_commit(b_xe + 8 * e);
           }
           tc_commit(b_accf);
@@ -483,23 +504,26 @@ k1_tcs_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
     // ---------------------------------------------------------- L2 half norms
     if (!a.ext) return;
     // column n = j*16 + u of a step is bin b0 + j, grid row t0 + u. Lane l
-    // writes columns c = l + 32 k (k < 8), i.e. j = c & 15, u = c >> 4, so
-    // that lanes 0..15 read 16 consecutive floats of one grid row. The loads
-    // of the next step are in flight while a step is written.
-    float hb[2][8];
+    // writes columns c = l + 32 k (k < HK), i.e. j = c % BS, u = c / BS, so
+    // that lanes 0..BS-1 read BS consecutive floats of one grid row. The loads
+    // run PD - 1 steps ahead of the step being written (registers hb[PD]), so
+    // their latency hides behind that many steps.
+    constexpr int HK = kCols / 32;
+    constexpr int PD = BS == 8 ? 4 : 2;
+    float hb[PD][HK];
     int64_t bg = s_begin / a.ntg, tg = s_begin % a.ntg;
-    // (with contiguous bins: column n is row step*256 + n)
+    // (with contiguous bins: column n is row step*kCols + n)
     int64_t rstep = s_begin;  // contiguous bins: the step being loaded
-    auto load = [&](int64_t bgx, int64_t tgx, bool live, float (&h)[8]) {
+    auto load = [&](int64_t bgx, int64_t tgx, bool live, float (&h)[HK]) {
 #pragma unroll
-      for (int k = 0; k < 8; ++k) {
+      for (int k = 0; k < HK; ++k) {
         const int c = lane + 32 * k;
         if constexpr (BM == kBinsRun) {
           const int64_t p = rstep * kCols + c;
           h[k] = (live && p < a.N) ? a.hnorm[p] : 0.0f;
         } else {
-          const int64_t b = bgx * kBinsStep + (c & 15);
-          const int64_t t = tgx * kRowsBin + (c >> 4);
+          const int64_t b = bgx * BS + (c % BS);
+          const int64_t t = tgx * kRowsBin + (c / BS);
           h[k] = (live && b < a.L && t < a.T) ? a.hnorm[t * a.L + b] : 0.0f;
         }
       }
@@ -518,32 +542,34 @@ k1_tcs_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
         t = s_begin % a.ntg;
       }
     };
-    load(bgn, tgn, nt > 0, hb[0]);
-    advance(bgn, tgn);
-    bool run = true;
-    for (int i0 = 0; i0 < nt && run; i0 += 2) {
 #pragma unroll
-      for (int cur = 0; cur < 2; ++cur) {
+    for (int k = 0; k < PD - 1; ++k) {
+      load(bgn, tgn, k < nt, hb[k]);
+      advance(bgn, tgn);
+    }
+    bool run = true;
+    for (int i0 = 0; i0 < nt && run; i0 += PD) {
+#pragma unroll
+      for (int cur = 0; cur < PD; ++cur) {
         const int i = i0 + cur;
         if (i >= nt) break;
-        load(bgn, tgn, i + 1 < nt, hb[cur ^ 1]);
+        load(bgn, tgn, i + PD - 1 < nt, hb[(cur + PD - 1) % PD]);
         advance(bgn, tgn);
-        const int e = i & 1;
+        const int e = i % XS;
         int ok = 1;
-        if (lane == 0 && i >= kExtSlotsS)
-          ok = mbar_wait_sleep(b_xe + 8 * e, (uint32_t)(((i >> 1) & 1) ^ 1), abort_flag) ? 1
-                                                                                           : 0;
+        if (lane == 0 && i >= XS)
+          ok = mbar_wait_sleep(b_xe + 8 * e, (uint32_t)(((i / XS) & 1) ^ 1), abort_flag) ? 1 : 0;
         ok = __shfl_sync(0xffffffffu, ok, 0);
         if (!ok) {
           run = false;
           break;
         }
-        uint8_t* ext = sBext + (size_t)e * kExtBS;
+        uint8_t* ext = sBext + (size_t)e * T::kExtB;
 #pragma unroll
-        for (int k = 0; k < 8; ++k) {
+        for (int k = 0; k < HK; ++k) {
           const int c = lane + 32 * k;
-          const int n = BM == kBinsRun ? c : (c & 15) * kRowsBin + (c >> 4);
-          const float hv = hb[cur][k];
+          const int n = BM == kBinsRun ? c : (c % BS) * kRowsBin + (c / BS);
+          const float hv = hb[cur][k];  // loaded PD - 1 steps ago
           const __nv_bfloat16 hi = __float2bfloat16_rn(hv);
           const float rem1 = hv - __bfloat162float(hi);
           const __nv_bfloat16 mid = __float2bfloat16_rn(rem1);
@@ -565,8 +591,9 @@ k1_tcs_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
   asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(kEpiRegsS));
   const int quad = warp & 3;
   const int egrp = (warp - 4) >> 2;  // 0..3
-  const int h = egrp >> 1;           // query half = accumulator
-  const int cq = egrp & 1;           // bins cq*8 .. cq*8+7 of each step
+  const int h = egrp >> 1;           // query half
+  const int cq = egrp & 1;           // bins cq*BPW .. cq*BPW+BPW-1 of each step
+  constexpr int NLD = BPW / 4;       // 64-column loads per step and thread
   // this thread's query in the current segment
   bool q_ok = false;
   unsigned long long* gq = a.G;
@@ -575,14 +602,15 @@ k1_tcs_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
     q_ok = qi < a.M;
     gq = a.G + (q_ok ? qi : 0) * a.L;
   };
-  const uint32_t tbase =
-      tmem_base + ((uint32_t)(quad * 32) << 16) + (uint32_t)(h * kCols + cq * 128);
+  // TMEM lanes of this warp and this warpgroup's columns of an accumulator
+  const uint32_t tlane = tmem_base + ((uint32_t)(quad * 32) << 16) + (uint32_t)(cq * BPW * 16);
+  auto acc_cols = [&](int buf) { return tlane + (uint32_t)((h * NB + buf) * kCols); };
   if constexpr (BM == kBinsRun) {
-    // Contiguous bins: this warpgroup sees rows s*256 + cq*128 .. +127 of
-    // every step s, in increasing order. A thread follows the current bin
+    // Contiguous bins: this warpgroup sees rows s*kCols + cq*kCols/2 .. + kCols/2 - 1
+    // of every step s, in increasing order. A thread follows the current bin
     // (the same for every lane: bins depend on rows only) with its best score
     // and row, and merges it into G when the rows leave the bin.
-    const int64_t first = min((s_begin * kCols + cq * 128), a.N - 1);
+    const int64_t first = min((s_begin * kCols + cq * (kCols / 2)), a.N - 1);
     int64_t cur = 0, seg_end = 0, brow = -1;
     float bv = __uint_as_float(kNegInfBits);
     auto flush_run = [&]() {
@@ -599,22 +627,25 @@ k1_tcs_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
     brow = -1;
     for (int li = 0; li < ns; ++li) {
       const int i = sg * ns + li;
-      if (!warp_all(mbar_wait_sleep(b_accf + 8 * h, (uint32_t)(i & 1), abort_flag))) {
+      const int buf = NB == 2 ? (i & 1) : 0;
+      if (!warp_all(mbar_wait_sleep(b_accf + 8 * (h * NB + buf), (uint32_t)((i / NB) & 1),
+                                    abort_flag))) {
         erun = false;
         break;
       }
       tc_fence_after();
-      const int64_t p0 = (s_begin + li) * kCols + cq * 128;
+      const int64_t p0 = (s_begin + li) * kCols + cq * (kCols / 2);
+      const uint32_t tb = acc_cols(buf);
 #pragma unroll
-      for (int half64 = 0; half64 < 2; ++half64) {
+      for (int half64 = 0; half64 < NLD; ++half64) {
         float r[4][16], m[4];
         __syncwarp();
-        tmem_ld4x16_max_s(tbase + (uint32_t)(half64 * 64), r, m);
-        if (half64 == 1) {
+        tmem_ld4x16_max_s(tb + (uint32_t)(half64 * 64), r, m);
+        if (half64 == NLD - 1) {
           // everything of this accumulator is in registers: release it
           tc_fence_before();
           __syncwarp();
-          if (lane == 0) mbar_arrive(b_acce + 8 * h);
+          if (lane == 0) mbar_arrive(b_acce + 8 * (h * NB + buf));
         }
 #pragma unroll
         for (int g = 0; g < 4; ++g) {
@@ -658,17 +689,17 @@ k1_tcs_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
     return;
   }
   int64_t bg = 0, tg = 0;
-  float best[8];
-  int32_t bt[8];
+  float best[BPW];
+  int32_t bt[BPW];
 #pragma unroll
-  for (int g = 0; g < 8; ++g) {
+  for (int g = 0; g < BPW; ++g) {
     best[g] = __uint_as_float(kNegInfBits);
     bt[g] = -1;
   }
   auto flush = [&](int64_t bgx) {
 #pragma unroll
-    for (int g = 0; g < 8; ++g) {
-      const int64_t b = bgx * kBinsStep + cq * 8 + g;
+    for (int g = 0; g < BPW; ++g) {
+      const int64_t b = bgx * BS + cq * BPW + g;
       if (q_ok && bt[g] >= 0 && b < a.L)
         atomicMax(&gq[b], (unsigned long long)make_key(best[g], (int32_t)(bt[g] * a.L + b)));
       best[g] = __uint_as_float(kNegInfBits);
@@ -696,33 +727,38 @@ k1_tcs_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
   tg = s_begin % a.ntg;
   for (int li = 0; li < ns; ++li) {
     const int i = sg * ns + li;
-    if (!warp_all(mbar_wait_sleep(b_accf + 8 * h, (uint32_t)(i & 1), abort_flag))) {
+    const int buf = NB == 2 ? (i & 1) : 0;
+    if (!warp_all(mbar_wait_sleep(b_accf + 8 * (h * NB + buf), (uint32_t)((i / NB) & 1),
+                                  abort_flag))) {
       erun = false;
       break;
     }
     tc_fence_after();
+    const uint32_t tb = acc_cols(buf);
     const int32_t t0 = (int32_t)(tg * kRowsBin);
-    const int64_t bw = bg * kBinsStep + cq * 8;  // first bin of this warpgroup
-    if (t0 + kRowsBin <= a.T && bw + 8 <= a.L) {
+    const int64_t bw = bg * BS + cq * BPW;  // first bin of this warpgroup
+    if (t0 + kRowsBin <= a.T && bw + BPW <= a.L) {
       // every column valid (warp-uniform): one compare per 16 scores. The
       // accumulator is released as soon as the last run is in registers.
       float r[4][16], m[4];
-      __syncwarp();
-      tmem_ld4x16_max_s(tbase, r, m);
-      record(r, m, 0, t0);
-      __syncwarp();
-      tmem_ld4x16_max_s(tbase + 64u, r, m);
-      tc_fence_before();
-      __syncwarp();
-      if (lane == 0) mbar_arrive(b_acce + 8 * h);
-      record(r, m, 4, t0);
+#pragma unroll
+      for (int ld = 0; ld < NLD; ++ld) {
+        __syncwarp();
+        tmem_ld4x16_max_s(tb + (uint32_t)(ld * 64), r, m);
+        if (ld == NLD - 1) {
+          tc_fence_before();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(b_acce + 8 * (h * NB + buf));
+        }
+        record(r, m, 4 * ld, t0);
+      }
     } else {
       // past the last full grid row or the last bin: column by column
 #pragma unroll
-      for (int g = 0; g < 8; ++g) {
+      for (int g = 0; g < BPW; ++g) {
         float r[16];
         __syncwarp();
-        tmem_ld16s(tbase + (uint32_t)(g * 16), r);
+        tmem_ld16s(tb + (uint32_t)(g * 16), r);
         if (bw + g < a.L) {
 #pragma unroll
           for (int k = 0; k < 16; ++k) {
@@ -735,7 +771,7 @@ k1_tcs_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
       }
       tc_fence_before();
       __syncwarp();
-      if (lane == 0) mbar_arrive(b_acce + 8 * h);
+      if (lane == 0) mbar_arrive(b_acce + 8 * (h * NB + buf));
     }
     if (++tg == a.ntg) {
       flush(bg);
@@ -846,14 +882,14 @@ bool make_map_s(CUtensorMap* m, const void* base, int64_t inner, int64_t rows, i
 
 // 3-D BF16 view of the database for the step boxes: element d of grid row t,
 // bin b is row t*L + b. Dimensions (d, t, b) with the bin outermost, so a
-// box of (64, 16, 16) lands as [bin][grid row][128 B]: each bin's 16 rows are
+// box of (64, 16, bs) lands as [bin][grid row][128 B]: each bin's 16 rows are
 // consecutive accumulator columns.
-bool make_map_grid(CUtensorMap* m, const void* base, int64_t pitch, int64_t L, int64_t T) {
+bool make_map_grid(CUtensorMap* m, const void* base, int64_t pitch, int64_t L, int64_t T, int bs) {
   auto enc = get_encode_s();
   if (!enc) return false;
   cuuint64_t dims[3] = {(cuuint64_t)pitch, (cuuint64_t)T, (cuuint64_t)L};
   cuuint64_t strides[2] = {(cuuint64_t)(L * pitch * 2), (cuuint64_t)(pitch * 2)};
-  cuuint32_t box[3] = {(cuuint32_t)(kSpanS / 2), (cuuint32_t)kRowsBin, (cuuint32_t)kBinsStep};
+  cuuint32_t box[3] = {(cuuint32_t)(kSpanS / 2), (cuuint32_t)kRowsBin, (cuuint32_t)bs};
   cuuint32_t estr[3] = {1, 1, 1};
   return enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(base), dims, strides, box,
              estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
@@ -888,20 +924,32 @@ void tcs_schedule(int64_t nqt, int64_t steps, int64_t sms, int64_t* kq_out, int6
 }
 
 struct TcsShape {
-  int mode, nkb, nksteps, stages;
+  int mode, nkb, nksteps, stages, bs;
   uint32_t a_bytes, stage_bytes;
   size_t smem;
 };
 
+// Bins per step of the fused mode (rows up to 128 elements): 16 (N = 256,
+// 32 KB stages) or 8 (N = 128, double-buffered accumulators, 16 KB stages).
+// Measured on the 1M x 128 workloads: 16 bins 0.195 ms (L2) / 0.185 ms (IP),
+// 8 bins 0.320 / 0.302 ms -- the N = 128 MMAs read 1.5x the shared-memory
+// operand bytes per FLOP (A and B 4 KB each per 0.5 MFLOP) and are limited by
+// shared-memory bandwidth, which outweighs the deeper ring.
+constexpr int kFusedBins = 16;
+
+template <int BS>
+size_t tcs_fixed_smem(int ext) {
+  return 1024 + (ext ? kExtAS + StepT<BS>::kXS * StepT<BS>::kExtB : 0) + 512;
+}
+
 // The first mode whose shared memory fits: kFused (resident query tile, the
 // whole step's K blocks plus one of look-ahead), kKLoopA (resident query
 // tile, at least 2 stages of one K block), kKLoopQ (query K block streamed in
-// every stage).
+// every stage). The K-loop modes use 16-bin steps.
 bool tcs_shape(int D, int metric, TcsShape* sh) {
   const int pitch = (int)round_up(D, 16);
   const size_t budget = 227 * 1024;
   const int ext = metric == KNN_L2;
-  const size_t fixed0 = 1024 + (ext ? kExtAS + kExtSlotsS * kExtBS : 0) + 512;
   sh->nkb = (int)cdiv((int64_t)pitch * 2, kSpanS);
   const int nks = (int)cdiv((int64_t)pitch * 2, 32);
   const uint32_t a_res = (uint32_t)(sh->nkb * kQT * kSpanS);
@@ -909,56 +957,61 @@ bool tcs_shape(int D, int metric, TcsShape* sh) {
   // zero query columns: the query box reads zeros past the row)
   const int nks_even = (int)round_up(nks, 2);
   if (nks_even <= 8) {
-    const size_t fixed = fixed0 + a_res;
+    const size_t stage = (size_t)StepT<kFusedBins>::kStage;
+    const size_t fixed = tcs_fixed_smem<kFusedBins>(ext) + a_res;
     const int need = sh->nkb + 1 > 3 ? sh->nkb + 1 : 3;
-    if (fixed + (size_t)need * kStageS <= budget) {
+    if (fixed + (size_t)need * stage <= budget) {
       sh->mode = kFused;
+      sh->bs = kFusedBins;
       sh->nksteps = nks_even;
       sh->a_bytes = a_res;
-      sh->stage_bytes = kStageS;
-      sh->stages = (int)std::min<size_t>(8, (budget - fixed) / kStageS);
-      sh->smem = fixed + (size_t)sh->stages * kStageS;
+      sh->stage_bytes = (uint32_t)stage;
+      sh->stages = (int)std::min<size_t>(16, (budget - fixed) / stage);
+      sh->smem = fixed + (size_t)sh->stages * stage;
       return true;
     }
   }
+  const size_t fixed0 = tcs_fixed_smem<16>(ext);
+  const size_t stage16 = (size_t)StepT<16>::kStage;
+  sh->bs = 16;
   sh->nksteps = nks;
-  if (fixed0 + a_res + 2 * (size_t)kStageS <= budget) {
+  if (fixed0 + a_res + 2 * stage16 <= budget) {
     sh->mode = kKLoopA;
     sh->a_bytes = a_res;
-    sh->stage_bytes = kStageS;
-    sh->stages = (int)std::min<size_t>(8, (budget - fixed0 - a_res) / kStageS);
+    sh->stage_bytes = (uint32_t)stage16;
+    sh->stages = (int)std::min<size_t>(8, (budget - fixed0 - a_res) / stage16);
   } else {
     sh->mode = kKLoopQ;
     sh->a_bytes = 0;
-    sh->stage_bytes = 2 * kStageS;
-    sh->stages = (int)std::min<size_t>(4, (budget - fixed0) / (2 * kStageS));
+    sh->stage_bytes = (uint32_t)(kQT * kSpanS + stage16);
+    sh->stages = (int)std::min<size_t>(4, (budget - fixed0) / sh->stage_bytes);
     if (sh->stages < 2) return false;
   }
   sh->smem = fixed0 + sh->a_bytes + (size_t)sh->stages * sh->stage_bytes;
   return true;
 }
 
-template <int NKS, int MODE, int BM>
+template <int NKS, int MODE, int BM, int BS>
 cudaError_t launch_tcs(const CUtensorMap& mx, const CUtensorMap& mq, const TcsArgs& a, size_t smem,
                        int64_t blocks, cudaStream_t st) {
   // setmaxnreg.inc waits until the registers it asks for are free: refuse to
   // launch unless the launch-time allocation covers the split.
   cudaFuncAttributes fa;
-  cudaError_t e = cudaFuncGetAttributes(&fa, k1_tcs_kernel<NKS, MODE, BM>);
+  cudaError_t e = cudaFuncGetAttributes(&fa, k1_tcs_kernel<NKS, MODE, BM, BS>);
   if (e != cudaSuccess) return e;
   if ((int64_t)round_up(fa.numRegs, 8) * kThreadsS < 128 * kCtrlRegsS + 512 * kEpiRegsS)
     return cudaErrorNotSupported;
-  e = cudaFuncSetAttribute(k1_tcs_kernel<NKS, MODE, BM>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  e = cudaFuncSetAttribute(k1_tcs_kernel<NKS, MODE, BM, BS>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   if constexpr (BM == kBinsRun) {
     // Contiguous bins: a plain launch. Started early behind the query prep,
     // the CTAs land on SMs in the order those free up, and the sharers of a
     // part end up far apart (measured: 0.244 -> 0.284 ms per search).
-    k1_tcs_kernel<NKS, MODE, BM><<<(unsigned)blocks, kThreadsS, smem, st>>>(mx, mq, a);
+    k1_tcs_kernel<NKS, MODE, BM, BS><<<(unsigned)blocks, kThreadsS, smem, st>>>(mx, mq, a);
     return cudaGetLastError();
   } else {
-    return launch_pdl(k1_tcs_kernel<NKS, MODE, BM>, dim3((unsigned)blocks), dim3(kThreadsS),
+    return launch_pdl(k1_tcs_kernel<NKS, MODE, BM, BS>, dim3((unsigned)blocks), dim3(kThreadsS),
                       smem, st, mx, mq, a);
   }
 }
@@ -977,13 +1030,14 @@ bool k1_tcs_supported(int dtype, int D, int metric, int64_t N, int64_t L) {
 template <int BM>
 cudaError_t launch_tcs_mode(const TcsShape& sh, const CUtensorMap& mx, const CUtensorMap& mq,
                             const TcsArgs& a, int64_t blocks, cudaStream_t st) {
-  if (sh.mode == kKLoopA) return launch_tcs<4, kKLoopA, BM>(mx, mq, a, sh.smem, blocks, st);
-  if (sh.mode == kKLoopQ) return launch_tcs<4, kKLoopQ, BM>(mx, mq, a, sh.smem, blocks, st);
+  if (sh.mode == kKLoopA) return launch_tcs<4, kKLoopA, BM, 16>(mx, mq, a, sh.smem, blocks, st);
+  if (sh.mode == kKLoopQ) return launch_tcs<4, kKLoopQ, BM, 16>(mx, mq, a, sh.smem, blocks, st);
+  constexpr int FB = kFusedBins;
   switch (sh.nksteps) {
-    case 2: return launch_tcs<2, kFused, BM>(mx, mq, a, sh.smem, blocks, st);
-    case 4: return launch_tcs<4, kFused, BM>(mx, mq, a, sh.smem, blocks, st);
-    case 6: return launch_tcs<6, kFused, BM>(mx, mq, a, sh.smem, blocks, st);
-    case 8: return launch_tcs<8, kFused, BM>(mx, mq, a, sh.smem, blocks, st);
+    case 2: return launch_tcs<2, kFused, BM, FB>(mx, mq, a, sh.smem, blocks, st);
+    case 4: return launch_tcs<4, kFused, BM, FB>(mx, mq, a, sh.smem, blocks, st);
+    case 6: return launch_tcs<6, kFused, BM, FB>(mx, mq, a, sh.smem, blocks, st);
+    case 8: return launch_tcs<8, kFused, BM, FB>(mx, mq, a, sh.smem, blocks, st);
     default: return cudaErrorNotSupported;
   }
 }
@@ -1006,12 +1060,13 @@ cudaError_t launch_k1_tcs(int64_t N, int64_t M, int64_t L, int D, int metric, in
   a.L = L;
   a.T = N / L;
   a.ntg = cdiv(a.T, kRowsBin);
-  a.nbg = cdiv(L, kBinsStep);
+  const int cols = sh.bs * kRowsBin;  // MMA N: database rows per step
+  a.nbg = cdiv(L, sh.bs);
   a.bq = N / L;
   a.br = N % L;
   a.nqt = cdiv(M, kQT);
-  // a step: 16 bins x 16 grid rows (j mod L), or 256 consecutive rows
-  a.steps_per_q = runs ? cdiv(N, kCols) : a.ntg * a.nbg;
+  // a step: bs bins x 16 grid rows (j mod L), or 16 bs consecutive rows
+  a.steps_per_q = runs ? cdiv(N, cols) : a.ntg * a.nbg;
   const int64_t sms = device_sm_count();
   tcs_schedule(a.nqt, a.steps_per_q, sms, &a.kq, &a.parts, &a.steps_per_part, &a.groups);
   // step counters of a CTA are 32-bit
@@ -1023,14 +1078,14 @@ cudaError_t launch_k1_tcs(int64_t N, int64_t M, int64_t L, int D, int metric, in
   a.a_bytes = sh.a_bytes;
   a.stage_bytes = sh.stage_bytes;
   a.ext = metric == KNN_L2 ? 1 : 0;
-  // D = F32, A = B = BF16, both K-major, N = 256, M = 128
-  a.idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kCols >> 3) << 17) |
+  // D = F32, A = B = BF16, both K-major, N = cols, M = 128
+  a.idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(cols >> 3) << 17) |
             ((uint32_t)(kQH >> 4) << 24);
   a.hnorm = hnorm;
   a.G = G;
   CUtensorMap mx, mq;
-  const bool mapped = runs ? make_map_s(&mx, X, pitch, N, pitch, kCols)
-                           : make_map_grid(&mx, X, pitch, L, a.T);
+  const bool mapped = runs ? make_map_s(&mx, X, pitch, N, pitch, cols)
+                           : make_map_grid(&mx, X, pitch, L, a.T, sh.bs);
   if (!mapped) return cudaErrorInvalidValue;
   if (!make_map_s(&mq, Qp, pitch, M, pitch, kQT)) return cudaErrorInvalidValue;
   const int64_t blocks = a.groups * a.parts;
