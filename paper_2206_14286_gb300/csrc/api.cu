@@ -142,8 +142,21 @@ K1Plan make_plan(int64_t N, int64_t M, int64_t L, int D, int metric, int dtype,
     splits = force_splits;
   } else {
     const int64_t sms = device_sm_count();
-    const int64_t target = sms * (dtype == KNN_F32 ? 4 : 1);
-    splits = cdiv(target, units);
+    splits = cdiv(sms, units);
+    if (dtype == KNN_F32 && sms > 0) {
+      // SIMT CTAs run two per SM: the split count with the least
+      // (waves of 2 * sms CTAs) x (tiles per CTA), the smallest on ties,
+      // which also keeps the per-split partials no larger than needed
+      const int64_t wave = 2 * sms;
+      int64_t best = -1;
+      for (int64_t s = 1; s <= std::min<int64_t>(p.ntiles, 4 * wave); ++s) {
+        const int64_t cost = cdiv(units * s, wave) * cdiv(p.ntiles, s);
+        if (best < 0 || cost < best) {
+          best = cost;
+          splits = s;
+        }
+      }
+    }
     if (dtype != KNN_F32 && sms > 0) {
       // tensor-core CTAs run one per SM: among a few split counts, take the
       // one whose last wave is fullest (units * splits CTAs over `sms`)
