@@ -392,16 +392,16 @@ k1_tcs_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
               const uint64_t bd =
                   b_desc + (uint64_t)((sk[ks >> 2] * T::kStage + (ks & 3) * 32) >> 4);
               tc_mma<KNN_BF16>(d_tmem, ad, bd, a.idesc, ks > 0 ? 1u : 0u);
+              // half 1 is a K block's last reader: its stage is free once the
+              // MMAs so far complete (2-3% faster than freeing all stages of
+              // the step after the half's last MMA)
+              if (h == 1 && ((ks & 3) == 3 || ks == NKS - 1)) tc_commit(b_empty + 8 * sk[ks >> 2]);
             }
             if (a.ext)
               tc_mma<KNN_BF16>(d_tmem, ax_desc, bx_desc + (uint64_t)((e * T::kExtB) >> 4),
                                a.idesc, 1u);
             tc_commit(b_accf + 8 * c);
-            if (h == 1) {
-#pragma unroll
-              for (int kb = 0; kb < NKB; ++kb) tc_commit(b_empty + 8 * sk[kb]);
-              if (a.ext) tc_commit(b_xe + 8 * e);
-            }
+            if (h == 1 && a.ext) tc_commit(b_xe + 8 * e);
           }
           __syncwarp();
         }
