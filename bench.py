@@ -144,27 +144,41 @@ class Clocks:
 # CPU oracle (baseline and the reference arm)
 # ----------------------------------------------------------------------------
 class OracleRunner:
-    """The FP64 oracle running the same method (PartialReduce, top-2K, re-rank)
-    on a bounded sample of the workload's queries."""
+    """The FP64 oracle running the same method (PartialReduce, top-rerank*K,
+    FP32-data re-rank) on a bounded sample of the workload's queries. The rows
+    are stored as the library stores them (BF16 rounding or per-row E4M3, unit
+    rows for cosine) and converted to float64 once, outside the timed runs."""
 
-    def __init__(self, w, L, K, bins="mod"):
+    def __init__(self, w, L, K, bins="mod", rerank=2):
         import oracle
         self.o = oracle
-        self.bins = bins
-        self.X, self.Q, self.L, self.K, self.metric = w["X"], w["Q"], L, K, w["metric"]
-        self.lowp = w["dtype"] == "bf16"
-        self.Xs = oracle.bf16_round(self.X) if self.lowp else self.X.astype(np.float64)
+        self.bins, self.rerank = bins, rerank
+        self.Q, self.L, self.K = w["Q"], L, K
+        self.cos = w["metric"] == "cos"
+        self.metric = "ip" if self.cos else w["metric"]
+        self.dtype = w["dtype"]
+        self.Xf, self.Xs = self._stored(w["X"])
         self.cursor = 0
+
+    def _stored(self, A):
+        o = self.o
+        f = o.normalize_rows(A) if self.cos else np.asarray(A, np.float64)
+        f = np.ascontiguousarray(f, np.float64)
+        if self.dtype == "bf16":
+            return f, o.bf16_round(f.astype(np.float32))
+        if self.dtype == "e4m3":
+            return f, o.e4m3_rows(f.astype(np.float32))[0]
+        return f, f
 
     def run(self, n):
         o = self.o
         q = np.take(self.Q, np.arange(self.cursor, self.cursor + n) % self.Q.shape[0], axis=0)
         self.cursor = (self.cursor + n) % self.Q.shape[0]
-        Qs = o.bf16_round(q) if self.lowp else q.astype(np.float64)
+        qf, qs = self._stored(q)
         t0 = time.perf_counter()
-        V, A = o.partial_reduce(Qs, self.Xs, self.L, self.metric, bins=self.bins)
-        _, cand = o.topk_pairs(V, A, 2 * self.K)
-        o.rerank(q, self.X, cand, self.K, self.metric)
+        V, A = o.partial_reduce(qs, self.Xs, self.L, self.metric, bins=self.bins)
+        _, cand = o.topk_pairs(V, A, min(self.rerank * self.K, self.L))
+        o.rerank(qf, self.Xf, cand, self.K, self.metric)
         return time.perf_counter() - t0
 
     def size_for(self, seconds, cap):
@@ -172,12 +186,12 @@ class OracleRunner:
         return int(max(8, min(cap, seconds / max(t / 8, 1e-6))))
 
 
-def cpu_baseline(w, L, K, bins, seconds=4.0):
+def cpu_baseline(w, L, K, bins, seconds=4.0, rerank=2):
     """The oracle on all host cores and on one core: three runs each on a
     bounded sample of the queries (about `seconds` each), median."""
     import oracle
     oracle.build()
-    runner = OracleRunner(w, L, K, bins)
+    runner = OracleRunner(w, L, K, bins, rerank)
     M, N = w["Q"].shape[0], w["X"].shape[0]
     cores = oracle.set_threads(0)
     try:
@@ -747,6 +761,8 @@ def e4m3_leg(args, lib, pk, rates):
     S.sync_status()
     del d8, d16, Xd, Qd
     torch.cuda.empty_cache()
+    if not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(w, L, K, "mod", seconds=2.0, rerank=rr)
     return out
 
 
@@ -807,6 +823,8 @@ def grad_leg(args, lib, pk):
            "score_error": score_errors(d, Xd, Qd, v, i, "ip", n=64)}
     del d, Xd, Qd, dxb
     torch.cuda.empty_cache()
+    if not args.no_cpu_baseline:
+        out["forward"]["cpu_baseline"] = cpu_baseline(w, L, K, "mod", seconds=2.0)
     return out
 
 
