@@ -177,8 +177,11 @@ class OracleRunner:
         qf, qs = self._stored(q)
         t0 = time.perf_counter()
         V, A = o.partial_reduce(qs, self.Xs, self.L, self.metric, bins=self.bins)
-        _, cand = o.topk_pairs(V, A, min(self.rerank * self.K, self.L))
-        o.rerank(qf, self.Xf, cand, self.K, self.metric)
+        if self.rerank == 0:
+            o.topk_pairs(V, A, self.K)
+        else:
+            _, cand = o.topk_pairs(V, A, min(self.rerank * self.K, self.L))
+            o.rerank(qf, self.Xf, cand, self.K, self.metric)
         return time.perf_counter() - t0
 
     def size_for(self, seconds, cap):
@@ -544,7 +547,8 @@ def main():
     if not args.no_configs:
         del Xd, Qd
         torch.cuda.empty_cache()
-        configs = {"fp8_e4m3_cos_10m": e4m3_leg(args, lib, pk, rates),
+        configs = {"f32_ip_16k": small_leg(args, lib),
+                   "fp8_e4m3_cos_10m": e4m3_leg(args, lib, pk, rates),
                    "bf16_ip_grad_1m": grad_leg(args, lib, pk)}
 
     cpu = None
@@ -690,6 +694,50 @@ def reference_arm(args, rank):
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
+
+
+def small_leg(args, lib):
+    """The plain FP32 case: 16,384 x 128 i.i.d. N(0,1) rows, M = 64 queries,
+    inner product, K = 10, L = 1024 (no re-rank: the rows are FP32), and the
+    exact search beside it; a launch-latency case, timed over 200 calls, with
+    the oracle's full run (all 64 queries) as its CPU baseline."""
+    import torch
+    from paper_2206_14286_gb300 import search as S, synth
+    w = synth.workload("iid_ip_16k")
+    X, Q, K, L = w["X"], w["Q"], w["K"], w["L"]
+    M = Q.shape[0]
+    Xd = torch.from_numpy(X).cuda()
+    Qd = torch.from_numpy(Q).cuda()
+    d = S.Database(Xd, metric="ip", dtype="f32")
+    v = torch.empty((M, K), dtype=torch.float32, device="cuda")
+    i = torch.empty((M, K), dtype=torch.int32, device="cuda")
+    ms = timed(lambda: d.search(Qd, K, L=L, rerank=0, out=(v, i)), 200, 10)
+    ms_exact = timed(lambda: d.search_exact(Qd, K), 200, 10)
+    _, ei = d.search_exact(Qd, K)
+    S.sync_status()
+    out = {"workload": "iid N(0,1) inner product N=%d D=%d M=%d K=%d, FP32" % (X.shape + (M, K)),
+           "L": L, "value": M / (ms / 1e3), "unit": "queries/s", "ms_per_step": ms,
+           "recall_at_10": recall_of(i.cpu().numpy(), ei.cpu().numpy()),
+           "exact": {"value": M / (ms_exact / 1e3), "ms_per_step": ms_exact},
+           "bound": "launch latency (0.27 GFLOP per call)"}
+    if not args.no_cpu_baseline:
+        import oracle
+        oracle.build()
+        runner = OracleRunner(w, L, K, "mod", rerank=0)
+        cores = oracle.set_threads(0)
+        try:
+            t_all = statistics.median(runner.run(M) for _ in range(3))
+            oracle.set_threads(1)
+            t_one = statistics.median(runner.run(M) for _ in range(3))
+        finally:
+            oracle.set_threads(cores)
+        out["cpu_baseline"] = {"value": M / t_all, "unit": "queries/s", "cores": cores,
+                               "kind": "oracle", "sample": "all %d queries, median of 3" % M,
+                               "single_thread": {"value": M / t_one, "unit": "queries/s",
+                                                 "cores": 1}}
+    del d, Xd, Qd
+    torch.cuda.empty_cache()
+    return out
 
 
 def e4m3_leg(args, lib, pk, rates):

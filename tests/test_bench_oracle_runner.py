@@ -24,3 +24,11 @@ def test_oracle_runner_stores_rows_like_the_parity_tests(dtype, metric):
     assert r.metric == ("ip" if metric == "cos" else metric)
     assert r.run(4) > 0 and r.cursor == 4
     assert r.run(7) > 0 and r.cursor == 2          # wraps around the 9 queries
+
+
+def test_oracle_runner_without_rerank():
+    g = np.random.Generator(np.random.PCG64(6))
+    X = g.standard_normal((500, 16)).astype(np.float32)
+    Q = g.standard_normal((5, 16)).astype(np.float32)
+    r = bench.OracleRunner(dict(X=X, Q=Q, metric="ip", dtype="f32"), L=32, K=4, rerank=0)
+    assert r.run(5) > 0 and r.cursor == 0
