@@ -23,15 +23,30 @@ struct PairSource {
   const int32_t* a;
   int64_t M, Lk, L, nsplits, index_offset;
   int g;
+  // The splits' entries are read four at a time, value and index together
+  // (both arrays are written for every entry), so with few queries a warp
+  // still has many loads in flight.
   __device__ __forceinline__ uint64_t key(int64_t i, int64_t b) const {
     uint64_t best = 0;
-    for (int64_t s = 0; s < nsplits; ++s) {
-      const int64_t base = (s * M + i) * Lk + b;
-      for (int f = 0; f < g; ++f) {
-        const int32_t j = a[base + (int64_t)f * L];
-        if (j < 0) continue;
-        const uint64_t k = make_key(v[base + (int64_t)f * L], (int32_t)(j + index_offset));
-        best = k > best ? k : best;
+    for (int f = 0; f < g; ++f) {
+      const int64_t b0 = i * Lk + b + (int64_t)f * L;
+      for (int64_t s0 = 0; s0 < nsplits; s0 += 4) {
+        int32_t jj[4];
+        float vv[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const bool in = s0 + u < nsplits;
+          const int64_t e = b0 + (s0 + u) * M * Lk;
+          jj[u] = in ? a[e] : -1;
+          vv[u] = in ? v[e] : 0.0f;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          if (jj[u] >= 0) {
+            const uint64_t k = make_key(vv[u], (int32_t)(jj[u] + index_offset));
+            best = k > best ? k : best;
+          }
+        }
       }
     }
     return best;
@@ -48,6 +63,7 @@ struct PackedSource {
   __device__ __forceinline__ uint64_t key(int64_t i, int64_t b) const {
     const uint32_t mask = bits ? ((1u << bits) - 1u) : 0u;
     uint64_t best = 0;
+#pragma unroll 4
     for (int64_t s = 0; s < nsplits; ++s) {
       const int64_t base = (s * M + i) * Lk + b;
       for (int f = 0; f < g; ++f) {
@@ -122,6 +138,50 @@ __device__ __forceinline__ uint64_t shfl_xor_u64(uint64_t v, int o) {
   return ((uint64_t)hi << 32) | lo;
 }
 
+// Lane `lane`'s candidates b = lane + 32 r (r < KPL) of query i, 0 past L.
+template <class Src, int KPL>
+__device__ __forceinline__ void lane_keys(const Src& src, int64_t i, int lane, int64_t L,
+                                          uint64_t (&k)[KPL]) {
+#pragma unroll
+  for (int r = 0; r < KPL; ++r) {
+    const int64_t b = lane + 32 * r;
+    k[r] = b < L ? src.key(i, b) : 0;
+  }
+}
+// The same from per-split (value, index) partials: the splits are the outer
+// loop, so a lane has the loads of all its candidates of one split in flight
+// at once (with few queries the per-candidate loop over the splits left each
+// warp waiting on one load at a time).
+template <int KPL>
+__device__ __forceinline__ void lane_keys(const PairSource& src, int64_t i, int lane, int64_t L,
+                                          uint64_t (&k)[KPL]) {
+#pragma unroll
+  for (int r = 0; r < KPL; ++r) k[r] = 0;
+  for (int f = 0; f < src.g; ++f) {
+    for (int64_t s = 0; s < src.nsplits; ++s) {
+      const int64_t base = (s * src.M + i) * src.Lk + (int64_t)f * src.L + lane;
+#pragma unroll
+      for (int r0 = 0; r0 < KPL; r0 += 8) {
+        int32_t jj[8];
+        float vv[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const bool in = r0 + u < KPL && lane + 32 * (r0 + u) < L;
+          jj[u] = in ? src.a[base + 32 * (r0 + u)] : -1;
+          vv[u] = in ? src.v[base + 32 * (r0 + u)] : 0.0f;
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          if (r0 + u < KPL && jj[u] >= 0) {
+            const uint64_t key = make_key(vv[u], (int32_t)(jj[u] + src.index_offset));
+            k[r0 + u] = key > k[r0 + u] ? key : k[r0 + u];
+          }
+        }
+      }
+    }
+  }
+}
+
 // One warp per query: lane l holds candidates l, l+32, ... (KPL of them),
 // sorted; Kp rounds each take the warp-wide maximum of the lane heads and pop
 // it from its lane. Keys are unique (distinct indices), so one lane pops.
@@ -132,11 +192,7 @@ k2_warp_kernel(Src src, int64_t M, int64_t L, int Kp, uint64_t* __restrict__ out
   const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   if (i >= M) return;
   uint64_t k[KPL];
-#pragma unroll
-  for (int r = 0; r < KPL; ++r) {
-    const int64_t b = lane + 32 * r;
-    k[r] = b < L ? src.key(i, b) : 0;
-  }
+  lane_keys(src, i, lane, L, k);
   reg_sort_desc<KPL>(k);
   for (int r = 0; r < Kp; ++r) {
     uint64_t m = k[0];
