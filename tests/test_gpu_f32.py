@@ -322,3 +322,21 @@ def test_owned_database_handle_matches_prepared_buffers(metric, dtype, keep):
         assert torch.equal(a[1], b[1]) and torch.equal(a[0], b[0]), (K, L, rr)
     own.close()
     S.sync_status()
+
+
+@pytest.mark.parametrize("metric", ["ip", "l2"])
+def test_search_at_the_largest_K_and_D(metric):
+    """The largest K a search accepts (4096, so K' = 4096 candidates through
+    the streaming ExactRescoring kernel and the re-rank) and the largest row
+    length (4096 elements)."""
+    X, Q = inputs(20000, 12, 16, seed=95)
+    frac, gi = run_and_check(X, Q, metric, 4096, 8192, 1)
+    V, A = oracle.partial_reduce(Q, X, 8192, metric)
+    _, cand = oracle.topk_pairs(V, A, 4096)
+    _, oi = oracle.rerank(Q, X, cand, 4096, metric)
+    agree = np.mean([len(set(gi[r]) & set(oi[r])) / 4096 for r in range(len(Q))])
+    assert agree > 0.999, agree
+    X, Q = inputs(3000, 20, 4096, seed=96)
+    frac, _ = run_and_check(X, Q, metric, 10, 300, 2)
+    assert frac > 0.8, frac
+    S.sync_status()
