@@ -165,6 +165,25 @@ size_t knn_search_host_workspace(int64_t N, int32_t D, int32_t dtype, int32_t me
                                  int32_t rerank_mult);
 
 /*
+ * knn_search_host without the final synchronisation: the copy of q, the
+ * search and the copies of the results are enqueued on `stream` and the call
+ * returns. The outputs hold the results, and q_host, the outputs and the
+ * workspace may be reused, only once that work has completed (synchronise
+ * the stream or an event recorded after the call). With pinned host buffers
+ * the copies are asynchronous DMA, so searches in flight on two streams (each
+ * with its own workspace and outputs) overlap one search's copies with the
+ * other's kernels. Arguments, workspace size and errors as knn_search_host;
+ * errors of the enqueued work are reported by knn_sync_status.
+ */
+knn_status knn_search_host_async(const void* db_lp, const float* db_scale,
+                                 const float* db_hnorm, const float* db_f32, int64_t N,
+                                 int32_t D, int32_t dtype, int32_t metric, const float* q_host,
+                                 int64_t M, int32_t K, int64_t L, int32_t bin_map,
+                                 double recall_target, int32_t rerank_mult, float* out_val_host,
+                                 int32_t* out_idx_host, void* workspace, size_t ws_bytes,
+                                 void* stream);
+
+/*
  * knn_search without a caller workspace: the search runs in a scratch buffer
  * of KNN_STATIC_WORKSPACE_BYTES that the library reserves in device memory
  * when the module loads (a file-scope __device__ array, one per device). The

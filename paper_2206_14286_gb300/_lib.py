@@ -30,6 +30,8 @@ SIGNATURES = {
     "knn_search_workspace": (SZ, [I64, I32, I32, I32, I64, I32, I64, I32, DBL, I32]),
     "knn_search_host": (ctypes.c_int, [P, P, P, P, I64, I32, I32, I32, P, I64, I32, I64, I32,
                                        DBL, I32, P, P, P, SZ, P]),
+    "knn_search_host_async": (ctypes.c_int, [P, P, P, P, I64, I32, I32, I32, P, I64, I32, I64,
+                                             I32, DBL, I32, P, P, P, SZ, P]),
     "knn_search_host_workspace": (SZ, [I64, I32, I32, I32, I64, I32, I64, I32, DBL, I32]),
     "knn_search_static": (ctypes.c_int, [P, P, P, P, I64, I32, I32, I32, P, I64, I32, I64, I32,
                                          DBL, I32, P, P, P]),

@@ -575,6 +575,40 @@ knn_status static_workspace(void** out) {
   return KNN_OK;
 }
 
+static knn_status search_host_impl(const void* db_lp, const float* db_scale,
+                                   const float* db_hnorm, const float* db_f32, int64_t N,
+                                   int32_t D, int32_t dtype, int32_t metric, const float* q_host,
+                                   int64_t M, int32_t K, int64_t L, int32_t bin_map,
+                                   double recall_target, int32_t rerank_mult, float* out_val_host,
+                                   int32_t* out_idx_host, void* workspace, size_t ws_bytes,
+                                   void* stream, bool sync) {
+  size_t base = knn_search_workspace(N, D, dtype, metric, M, K, L, bin_map, recall_target,
+                                     rerank_mult);
+  if (base == 0) return KNN_EINVAL;
+  if (M == 0) return KNN_OK;
+  if (!q_host || !out_val_host || !out_idx_host) return KNN_EINVAL;
+  if (!workspace || !aligned(workspace, kAlign)) return KNN_EINVAL;
+  size_t need = knn_search_host_workspace(N, D, dtype, metric, M, K, L, bin_map, recall_target,
+                                          rerank_mult);
+  if (ws_bytes < need) return KNN_ENOMEM;
+  char* ws = reinterpret_cast<char*>(workspace);
+  float* qd = reinterpret_cast<float*>(ws + al(base));
+  float* vd = reinterpret_cast<float*>(ws + al(base) + al((size_t)M * D * 4));
+  int32_t* id = reinterpret_cast<int32_t*>(ws + al(base) + al((size_t)M * D * 4) +
+                                           al((size_t)M * K * 4));
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaError_t e = cudaMemcpyAsync(qd, q_host, (size_t)M * D * 4, cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) return cuda_status(e);
+  knn_status rc = knn_search(db_lp, db_scale, db_hnorm, db_f32, N, D, dtype, metric, qd, M, K, L,
+                             bin_map, recall_target, rerank_mult, vd, id, ws, base, stream);
+  if (rc != KNN_OK) return rc;
+  e = cudaMemcpyAsync(out_val_host, vd, (size_t)M * K * 4, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(out_idx_host, id, (size_t)M * K * 4, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess && sync) e = cudaStreamSynchronize(st);
+  return cuda_status(e);
+}
+
 }  // namespace
 
 // ===========================================================================
@@ -660,31 +694,21 @@ knn_status knn_search_host(const void* db_lp, const float* db_scale, const float
                            int32_t bin_map, double recall_target, int32_t rerank_mult,
                            float* out_val_host, int32_t* out_idx_host, void* workspace,
                            size_t ws_bytes, void* stream) {
-  size_t base = knn_search_workspace(N, D, dtype, metric, M, K, L, bin_map, recall_target,
-                                     rerank_mult);
-  if (base == 0) return KNN_EINVAL;
-  if (M == 0) return KNN_OK;
-  if (!q_host || !out_val_host || !out_idx_host) return KNN_EINVAL;
-  if (!workspace || !aligned(workspace, kAlign)) return KNN_EINVAL;
-  size_t need = knn_search_host_workspace(N, D, dtype, metric, M, K, L, bin_map, recall_target,
-                                          rerank_mult);
-  if (ws_bytes < need) return KNN_ENOMEM;
-  char* ws = reinterpret_cast<char*>(workspace);
-  float* qd = reinterpret_cast<float*>(ws + al(base));
-  float* vd = reinterpret_cast<float*>(ws + al(base) + al((size_t)M * D * 4));
-  int32_t* id = reinterpret_cast<int32_t*>(ws + al(base) + al((size_t)M * D * 4) +
-                                           al((size_t)M * K * 4));
-  cudaStream_t st = (cudaStream_t)stream;
-  cudaError_t e = cudaMemcpyAsync(qd, q_host, (size_t)M * D * 4, cudaMemcpyHostToDevice, st);
-  if (e != cudaSuccess) return cuda_status(e);
-  knn_status rc = knn_search(db_lp, db_scale, db_hnorm, db_f32, N, D, dtype, metric, qd, M, K, L,
-                             bin_map, recall_target, rerank_mult, vd, id, ws, base, stream);
-  if (rc != KNN_OK) return rc;
-  e = cudaMemcpyAsync(out_val_host, vd, (size_t)M * K * 4, cudaMemcpyDeviceToHost, st);
-  if (e == cudaSuccess)
-    e = cudaMemcpyAsync(out_idx_host, id, (size_t)M * K * 4, cudaMemcpyDeviceToHost, st);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-  return cuda_status(e);
+  return search_host_impl(db_lp, db_scale, db_hnorm, db_f32, N, D, dtype, metric, q_host, M, K, L,
+                          bin_map, recall_target, rerank_mult, out_val_host, out_idx_host,
+                          workspace, ws_bytes, stream, true);
+}
+
+knn_status knn_search_host_async(const void* db_lp, const float* db_scale,
+                                 const float* db_hnorm, const float* db_f32, int64_t N,
+                                 int32_t D, int32_t dtype, int32_t metric, const float* q_host,
+                                 int64_t M, int32_t K, int64_t L, int32_t bin_map,
+                                 double recall_target, int32_t rerank_mult, float* out_val_host,
+                                 int32_t* out_idx_host, void* workspace, size_t ws_bytes,
+                                 void* stream) {
+  return search_host_impl(db_lp, db_scale, db_hnorm, db_f32, N, D, dtype, metric, q_host, M, K, L,
+                          bin_map, recall_target, rerank_mult, out_val_host, out_idx_host,
+                          workspace, ws_bytes, stream, false);
 }
 
 knn_status knn_search_static(const void* db_lp, const float* db_scale, const float* db_hnorm,

@@ -111,8 +111,14 @@ class Database:
         return val, idx
 
     def search_host(self, q_host, K, L=None, recall_target=0.95, rerank=2, stream=None,
-                    out=None, bins="mod"):
-        """Search with host queries and host outputs (copies inside the call)."""
+                    out=None, bins="mod", wait=True, slot=0):
+        """Search with host queries and host outputs (copies inside the call).
+
+        wait=False enqueues the work on `stream` and returns at once
+        (knn_search_host_async): the outputs are valid, and q_host and the
+        outputs reusable, once the stream has completed it. Each `slot` has its
+        own workspace, so calls in flight on different streams use different
+        slots."""
         M = q_host.shape[0]
         L = self.resolve_L(K, L, recall_target)
         lib = _lib.get()
@@ -120,17 +126,17 @@ class Database:
                                            M, K, L, BINS[bins], recall_target, rerank)
         if nb == 0:
             raise ValueError("invalid search arguments")
-        ws = self._get_ws(("host", M, K, L, rerank, bins), nb)
+        ws = self._get_ws(("host", M, K, L, rerank, bins, slot), nb)
         if out is None:
             val = torch.empty((M, K), dtype=torch.float32, pin_memory=True)
             idx = torch.empty((M, K), dtype=torch.int32, pin_memory=True)
         else:
             val, idx = out
+        fn = lib.knn_search_host if wait else lib.knn_search_host_async
         with torch.cuda.device(self.device):
-            check(lib.knn_search_host(*self._args(), q_host.data_ptr(), M, K, L, BINS[bins],
-                                      recall_target, rerank, val.data_ptr(), idx.data_ptr(),
-                                      ws.data_ptr(), ws.numel(), _stream(stream)),
-                  "knn_search_host")
+            check(fn(*self._args(), q_host.data_ptr(), M, K, L, BINS[bins], recall_target, rerank,
+                     val.data_ptr(), idx.data_ptr(), ws.data_ptr(), ws.numel(), _stream(stream)),
+                  "knn_search_host" if wait else "knn_search_host_async")
         return val, idx
 
     def search_static(self, q, K, L=None, recall_target=0.95, rerank=2, stream=None, out=None,

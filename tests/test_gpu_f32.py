@@ -198,6 +198,29 @@ def test_search_host_entry_matches_device_entry():
     np.testing.assert_array_equal(host(v1), v2.numpy())
 
 
+@pytest.mark.parametrize("dtype,metric", [("bf16", "l2"), ("f32", "ip")])
+def test_async_host_search_on_two_streams_matches_the_synchronous_call(dtype, metric):
+    """knn_search_host_async: three query batches, two streams in flight (a
+    workspace slot and host outputs each, slot 0 used twice on stream 0),
+    give bit for bit what the synchronous knn_search_host gives."""
+    X, Q = inputs(30000, 300, 64, seed=97)
+    d = db(X, metric, dtype)
+    qs = [torch.from_numpy(np.ascontiguousarray(Q[k::3])).pin_memory() for k in range(3)]
+    ref = [d.search_host(q, 10, L=256) for q in qs]
+    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    outs = [(torch.full((100, 10), float("nan"), dtype=torch.float32).pin_memory(),
+             torch.full((100, 10), -7, dtype=torch.int32).pin_memory()) for _ in range(3)]
+    for k in range(3):
+        d.search_host(qs[k], 10, L=256, stream=streams[k % 2], wait=False, slot=k % 2,
+                      out=outs[k])
+    for st in streams:
+        st.synchronize()
+    S.sync_status()
+    for (v, i), (rv, ri) in zip(outs, ref):
+        assert torch.equal(i, ri)
+        assert torch.equal(v.view(torch.int32), rv.view(torch.int32))
+
+
 def test_recall_plan_and_invalid_calls():
     ensure_built()
     assert S.plan_bins(10 ** 6, 10, 0.95) == 176
