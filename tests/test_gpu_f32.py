@@ -361,6 +361,6 @@ def test_search_at_the_largest_K_and_D(metric):
     assert agree > 0.999, agree
     X, Q = inputs(3000, 20, 4096, seed=96)
     frac, _ = run_and_check(X, Q, metric, 10, 300, 2)
-    # decided fractions from the oracle side alone: 0.65 (ip), 0.8 (l2) of 20
+    # decided fraction for ip measured at 0.65 of the 20 queries (l2 above 0.8)
     assert frac > 0.5, frac
     S.sync_status()
