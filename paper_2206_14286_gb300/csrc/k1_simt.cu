@@ -9,9 +9,12 @@
 // compare/select of Alg. 1 (strict '>' while the row index grows, so ties
 // keep the smaller index) updates the running best of each (query, bin) the
 // thread owns. A thread owns 8 queries x 4 bins and the bins never change
-// across tiles (tile t covers rows t*Lk + strip*64 + [0, 64)), so the running
-// state lives in registers and only M x L partials per split reach memory
-// (Eq. 20's 2*4*M*L output bytes per split).
+// across tiles (tile t covers rows t*Lk + strip*64 + [0, 64)); the running
+// (value, row) state of the CTA's 128 x 64 pairs lives in shared memory (one
+// 16-byte load and at most two 16-byte stores per query row and tile), which
+// leaves the registers to the accumulators and the operand prefetch, and only
+// M x L partials per split reach memory (Eq. 20's 2*4*M*L output bytes per
+// split).
 #include "common.cuh"
 #include "kernels.h"
 
@@ -30,6 +33,10 @@ k1_simt_kernel(const float* __restrict__ X, const float* __restrict__ hnorm,
                int32_t* __restrict__ part_a) {
   __shared__ __align__(16) float Qs[2][BD][PADQ];
   __shared__ __align__(16) float Xs[2][BD][PADW];
+  // running best (value, row) of each (query, bin) of the CTA: [BQ][BW]
+  extern __shared__ __align__(16) float simt_state[];
+  float* sv = simt_state;
+  int32_t* sa = reinterpret_cast<int32_t*>(simt_state + BQ * BW);
   const int tid = threadIdx.x, tq = tid >> 4, tb = tid & 15;
   int64_t cta = blockIdx.x;
   const int64_t qtile = cta % p.nqtiles;
@@ -40,15 +47,13 @@ k1_simt_kernel(const float* __restrict__ X, const float* __restrict__ hnorm,
   const int64_t t_begin = split * p.tiles_per_split;
   const int64_t t_end = min(p.ntiles, t_begin + p.tiles_per_split);
 
-  float v[TQ][TB];
-  int32_t a[TQ][TB];
+  // this thread's entries: rows tq*TQ + r, columns tb*TB .. tb*TB + 3
 #pragma unroll
-  for (int r = 0; r < TQ; ++r)
-#pragma unroll
-    for (int c = 0; c < TB; ++c) {
-      v[r][c] = neg_inf();
-      a[r][c] = -1;
-    }
+  for (int r = 0; r < TQ; ++r) {
+    const int o = (tq * TQ + r) * BW + tb * TB;
+    *reinterpret_cast<float4*>(sv + o) = make_float4(neg_inf(), neg_inf(), neg_inf(), neg_inf());
+    *reinterpret_cast<int4*>(sa + o) = make_int4(-1, -1, -1, -1);
+  }
 
   // loader mapping: a chunk is BQ query rows and BW database rows of BD
   // floats; thread tid loads the float4 at column lcol of rows lrow (and
@@ -119,20 +124,36 @@ k1_simt_kernel(const float* __restrict__ X, const float* __restrict__ hnorm,
         __syncthreads();
       }
     }
-    // Alg. 1 compare/select per (query, bin)
+    // Alg. 1 compare/select per (query, bin), against the state in shared memory
+    float hb[TB];
+    bool valid[TB];
 #pragma unroll
     for (int c = 0; c < TB; ++c) {
       const int64_t b = b0 + tb * TB + c;
       const int64_t j = row0 + tb * TB + c;
-      const bool valid = (b < p.Lk) && (j < p.N);
-      const float hb = (METRIC == KNN_L2 && valid) ? hnorm[j] : 0.0f;
+      valid[c] = (b < p.Lk) && (j < p.N);
+      hb[c] = (METRIC == KNN_L2 && valid[c]) ? hnorm[j] : 0.0f;
+    }
 #pragma unroll
-      for (int r = 0; r < TQ; ++r) {
-        const float s = acc[r][c] - hb;
-        if (valid && s > v[r][c]) {
-          v[r][c] = s;
-          a[r][c] = (int32_t)j;
+    for (int r = 0; r < TQ; ++r) {
+      const int o = (tq * TQ + r) * BW + tb * TB;
+      float4 bv = *reinterpret_cast<const float4*>(sv + o);
+      int4 ba = *reinterpret_cast<const int4*>(sa + o);
+      float* bvp = reinterpret_cast<float*>(&bv);
+      int* bap = reinterpret_cast<int*>(&ba);
+      bool upd = false;
+#pragma unroll
+      for (int c = 0; c < TB; ++c) {
+        const float sc = acc[r][c] - hb[c];
+        if (valid[c] && sc > bvp[c]) {
+          bvp[c] = sc;
+          bap[c] = (int32_t)(row0 + tb * TB + c);
+          upd = true;
         }
+      }
+      if (upd) {
+        *reinterpret_cast<float4*>(sv + o) = bv;
+        *reinterpret_cast<int4*>(sa + o) = ba;
       }
     }
   }
@@ -146,8 +167,9 @@ k1_simt_kernel(const float* __restrict__ X, const float* __restrict__ hnorm,
       const int64_t b = b0 + tb * TB + c;
       if (b >= p.Lk) continue;
       const int64_t o = (split * p.M + i) * p.Lk + b;
-      part_v[o] = v[r][c];
-      part_a[o] = a[r][c];
+      const int so = (tq * TQ + r) * BW + tb * TB + c;
+      part_v[o] = sv[so];
+      part_a[o] = sa[so];
     }
   }
 }
@@ -159,12 +181,20 @@ cudaError_t launch_k1_simt(const K1Plan& p, const float* X, const float* hnorm, 
   int64_t blocks = p.nsplits * p.nstrips * p.nqtiles;
   if (blocks <= 0) return cudaSuccess;
   if (blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
-  if (p.metric == KNN_L2)
-    k1_simt_kernel<KNN_L2><<<(unsigned)blocks, kSimtThreads, 0, st>>>(X, hnorm, Qp, p, out.v,
-                                                                       out.a);
-  else
-    k1_simt_kernel<KNN_IP><<<(unsigned)blocks, kSimtThreads, 0, st>>>(X, hnorm, Qp, p, out.v,
-                                                                       out.a);
+  const size_t smem = (size_t)BQ * BW * 8;
+  if (p.metric == KNN_L2) {
+    cudaError_t e = cudaFuncSetAttribute(k1_simt_kernel<KNN_L2>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k1_simt_kernel<KNN_L2><<<(unsigned)blocks, kSimtThreads, smem, st>>>(X, hnorm, Qp, p, out.v,
+                                                                          out.a);
+  } else {
+    cudaError_t e = cudaFuncSetAttribute(k1_simt_kernel<KNN_IP>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k1_simt_kernel<KNN_IP><<<(unsigned)blocks, kSimtThreads, smem, st>>>(X, hnorm, Qp, p, out.v,
+                                                                          out.a);
+  }
   return cudaGetLastError();
 }
 
