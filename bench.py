@@ -65,6 +65,10 @@ def parse():
     ap.add_argument("--no-configs", action="store_true",
                     help="skip the E4M3 10M and the 1M x 256 backward workloads")
     ap.add_argument("--config-steps", type=int, default=10)
+    ap.add_argument("--config-list", default="small,e4m3,grad",
+                    help="which of the other workloads to run (comma list of small, e4m3, grad)")
+    ap.add_argument("--config-scale", type=float, default=1.0,
+                    help="shrink N and M of the e4m3 and grad workloads (small profiling runs)")
     ap.add_argument("--shard", action="store_true",
                     help="N-sharded search: the rows split over the ranks, two all-reduce MAX "
                          "exchanges per step (strong scaling); default: independent replicas")
@@ -574,9 +578,14 @@ def main():
     if not args.no_configs:
         del Xd, Qd
         torch.cuda.empty_cache()
-        configs = {"f32_ip_16k": small_leg(args, lib),
-                   "fp8_e4m3_cos_10m": e4m3_leg(args, lib, pk, rates),
-                   "bf16_ip_grad_1m": grad_leg(args, lib, pk)}
+        wanted = set(args.config_list.split(","))
+        configs = {}
+        if "small" in wanted:
+            configs["f32_ip_16k"] = small_leg(args, lib)
+        if "e4m3" in wanted:
+            configs["fp8_e4m3_cos_10m"] = e4m3_leg(args, lib, pk, rates)
+        if "grad" in wanted:
+            configs["bf16_ip_grad_1m"] = grad_leg(args, lib, pk)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -775,7 +784,7 @@ def e4m3_leg(args, lib, pk, rates):
     queries; the BF16 path on the same workload beside it."""
     import torch
     from paper_2206_14286_gb300 import search as S, synth
-    w = synth.workload("mix_cos_10m")
+    w = synth.workload("mix_cos_10m", scale=args.config_scale)
     X, Q, K = w["X"], w["Q"], w["K"]
     N, D = X.shape
     M = Q.shape[0]
@@ -792,7 +801,7 @@ def e4m3_leg(args, lib, pk, rates):
     ms = timed(step, args.config_steps, 3)
     prof = profiled(lib, step, 3)
     S.sync_status()
-    samp = np.random.Generator(np.random.PCG64(11)).choice(M, 2000, replace=False)
+    samp = np.random.Generator(np.random.PCG64(11)).choice(M, min(2000, M), replace=False)
     st = torch.from_numpy(samp).cuda()
     dx = S.Database(Xd, metric="cos", dtype="f32")
     _, ei = dx.search_exact(Qd[st].contiguous(), K)
@@ -808,7 +817,7 @@ def e4m3_leg(args, lib, pk, rates):
                        "scales" % (N, D, M, K),
            "L": L, "rerank": "FP32 top-%dK" % rr, "value": M / (ms / 1e3),
            "unit": "queries/s", "ms_per_step": ms, "recall_at_100": rec,
-           "recall_sample": "2000 queries vs exact FP32 search",
+           "recall_sample": "%d queries vs exact FP32 search" % len(samp),
            "kernels": {"prep": prof["prep"], "k1_partial_reduce": prof["k1"],
                        "k2_rescoring": prof["k2"], "k3_rerank": prof["k3"]},
            "roofline": {"bound": "tensor", "kernel": "k1_tc_kernel (E4M3 tcgen05 kind::f8f6f4, "
@@ -849,7 +858,7 @@ def grad_leg(args, lib, pk):
     zero-filled as torch's autograd needs it, and added into an existing dX)."""
     import torch
     from paper_2206_14286_gb300 import search as S, synth
-    w = synth.workload("iid_ip_grad_1m")
+    w = synth.workload("iid_ip_grad_1m", scale=args.config_scale)
     X, Q, K = w["X"], w["Q"], w["K"]
     N, D = X.shape
     M = Q.shape[0]
