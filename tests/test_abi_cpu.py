@@ -159,3 +159,28 @@ def test_shard_calls_reject_bad_layouts(lib):
     assert lib.knn_rescore_count(10, 2, 128) == 20
     assert lib.knn_rescore_count(10, 2, 15) == 15
     assert lib.knn_rescore_count(11, 1, 10) == -1
+
+
+def test_host_entries_reject_bad_arguments_without_a_device(lib):
+    """knn_search_host and knn_search_host_async check their arguments before
+    any copy: invalid sizes, null host buffers, a missing or small workspace."""
+    for f in (lib.knn_search_host, lib.knn_search_host_async):
+        base = [None, None, None, None, 100, 8, 0, 0, None, 4, 3, 10, 0, 0.9, 1, None, None,
+                None, 0, None]
+
+        def call(**kw):
+            a = list(base)
+            pos = {"N": 4, "K": 10, "L": 11, "q": 8, "ov": 15, "oi": 16, "ws": 17, "wsb": 18,
+                   "M": 9}
+            for k, v in kw.items():
+                a[pos[k]] = v
+            return f(*a)
+
+        assert call(N=0) == _lib.KNN_EINVAL
+        assert call(K=20) == _lib.KNN_EINVAL          # K > L
+        assert call(M=0) == _lib.KNN_OK               # empty query set
+        assert call() == _lib.KNN_EINVAL              # null host buffers
+        buf = ctypes.create_string_buffer(64)
+        p = ctypes.addressof(buf)
+        assert call(q=p, ov=p, oi=p) == _lib.KNN_EINVAL          # no workspace
+        assert call(q=p, ov=p, oi=p, ws=4096, wsb=16) == _lib.KNN_ENOMEM   # too small
