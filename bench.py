@@ -528,10 +528,13 @@ def main():
     e2e_run(e2e_steps, True)
     e2e_sync_s = time.perf_counter() - t0
     S.sync_status()
-    e2e = {"value": world * M * e2e_steps / e2e_s, "unit": "queries/s",
+    # whole-job rates: the slowest rank's wall clock
+    e2e_value, _ = job_rate(world, M * e2e_steps, e2e_s * 1e3, device="cuda")
+    e2e_sync_value, _ = job_rate(world, M * e2e_steps, e2e_sync_s * 1e3, device="cuda")
+    e2e = {"value": e2e_value, "unit": "queries/s",
            "h2d_bytes_per_step": int(M * D * 4), "d2h_bytes_per_step": int(M * K * 8),
            "mode": "knn_search_host_async, two steps in flight on two streams",
-           "synchronous": {"value": world * M * e2e_steps / e2e_sync_s,
+           "synchronous": {"value": e2e_sync_value,
                            "mode": "knn_search_host, one step at a time"}}
 
     # roofline of the dominant kernel (K1), and of the FP32 path's K1
@@ -579,6 +582,8 @@ def main():
         del Xd, Qd
         torch.cuda.empty_cache()
         wanted = set(args.config_list.split(","))
+        # the oracle baselines of the legs: rank 0 of a single-GPU run only
+        args.leg_cpu = rank == 0 and world == 1 and not args.no_cpu_baseline
         configs = {}
         if "small" in wanted:
             configs["f32_ip_16k"] = small_leg(args, lib)
@@ -757,7 +762,7 @@ def small_leg(args, lib):
            "recall_at_10": recall_of(i.cpu().numpy(), ei.cpu().numpy()),
            "exact": {"value": M / (ms_exact / 1e3), "ms_per_step": ms_exact},
            "bound": "launch latency (0.27 GFLOP per call)"}
-    if not args.no_cpu_baseline:
+    if args.leg_cpu:
         import oracle
         oracle.build()
         runner = OracleRunner(w, L, K, "mod", rerank=0)
@@ -846,7 +851,7 @@ def e4m3_leg(args, lib, pk, rates):
     S.sync_status()
     del d8, d16, Xd, Qd
     torch.cuda.empty_cache()
-    if not args.no_cpu_baseline:
+    if args.leg_cpu:
         out["cpu_baseline"] = cpu_baseline(w, L, K, "mod", seconds=2.0, rerank=rr)
     return out
 
@@ -908,7 +913,7 @@ def grad_leg(args, lib, pk):
            "score_error": score_errors(d, Xd, Qd, v, i, "ip", n=64)}
     del d, Xd, Qd, dxb
     torch.cuda.empty_cache()
-    if not args.no_cpu_baseline:
+    if args.leg_cpu:
         out["forward"]["cpu_baseline"] = cpu_baseline(w, L, K, "mod", seconds=2.0)
     return out
 
