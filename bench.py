@@ -426,17 +426,42 @@ def main():
         dist.barrier()
     torch.cuda.synchronize()
 
-    # the timed region: K searches back to back, one event pair around all
+    # The timed region: K searches, two in flight on two streams (a workspace
+    # slot and outputs each), as a serving loop runs them: one search's query
+    # prep and rescoring run beside the other's contraction. Events on the
+    # launching stream bracket all K; both streams join it before the end.
+    streams2 = [torch.cuda.Stream(), torch.cuda.Stream()]
+    outs2 = [(val, idx), (torch.empty_like(val), torch.empty_like(idx))]
+
+    def run2(n):
+        cur = torch.cuda.current_stream()
+        for st_ in streams2:
+            st_.wait_stream(cur)
+        for t in range(n):
+            db.search(Qd, K, L=L, rerank=rerank, out=outs2[t % 2], bins=bins,
+                      stream=streams2[t % 2], slot=t % 2)
+        for st_ in streams2:
+            cur.wait_stream(st_)
+
+    run2(4)
+    torch.cuda.synchronize()
     clocks = Clocks(local)
     t_a, t_b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     t_a.record()
-    for _ in range(args.steps):
-        step()
+    run2(args.steps)
     t_b.record()
     torch.cuda.synchronize()
     clk = clocks.stop()
     total_ms = t_a.elapsed_time(t_b)
     value, total_ms = job_rate(world, M * args.steps, total_ms, device="cuda")
+    # the same K searches one after another on one stream
+    t_a.record()
+    for _ in range(args.steps):
+        step()
+    t_b.record()
+    torch.cuda.synchronize()
+    single_value, single_ms = job_rate(world, M * args.steps, t_a.elapsed_time(t_b),
+                                       device="cuda")
     # step latency (p50 / p99): a separate pass of at least 100 searches with
     # an event pair around each
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
@@ -610,6 +635,9 @@ def main():
                                "recall_at_10": recall_other},
                 "p50_ms": sm[len(sm) // 2], "p99_ms": sm[min(len(sm) - 1, int(0.99 * len(sm)))],
                 "latency_samples": len(sm),
+                "streams": 2,
+                "single_stream": {"value": single_value, "unit": "queries/s",
+                                  "ms_per_step": single_ms / args.steps},
                 "fp32_path": {"value": world * M / (ms32 / 1e3), "unit": "queries/s",
                               "ms_per_step": ms32, "recall_at_10": recall32,
                               "roofline": fp32_roof},

@@ -85,10 +85,12 @@ class Database:
 
     # -- calls -----------------------------------------------------------------
     def search(self, q, K, L=None, recall_target=0.95, rerank=2, stream=None, out=None,
-               bins="mod"):
+               bins="mod", slot=0):
         """Approximate search; returns (values M x K float32, indices M x K int32).
 
-        bins: "mod" (row j in bin j mod L) or "contiguous" (runs of rows)."""
+        bins: "mod" (row j in bin j mod L) or "contiguous" (runs of rows).
+        slot: each slot has its own workspace; searches in flight on different
+        streams at the same time use different slots."""
         q = q.contiguous()
         M = q.shape[0]
         L = self.resolve_L(K, L, recall_target)
@@ -98,7 +100,7 @@ class Database:
         if nb == 0:
             raise ValueError("invalid search arguments (N=%d D=%d M=%d K=%d L=%d)"
                              % (self.N, self.D, M, K, L))
-        ws = self._get_ws(("search", M, K, L, rerank, bins), nb)
+        ws = self._get_ws(("search", M, K, L, rerank, bins, slot), nb)
         if out is None:
             val = torch.empty((M, K), dtype=torch.float32, device=self.device)
             idx = torch.empty((M, K), dtype=torch.int32, device=self.device)
