@@ -221,6 +221,36 @@ def test_async_host_search_on_two_streams_matches_the_synchronous_call(dtype, me
         assert torch.equal(v.view(torch.int32), rv.view(torch.int32))
 
 
+@pytest.mark.parametrize("dtype,metric", [("bf16", "l2"), ("e4m3", "cos")])
+def test_searches_in_flight_on_two_streams_match_sequential_ones(dtype, metric):
+    """Device-buffer searches with two in flight on two streams (a workspace
+    slot each, as the bench's timed loop runs them) give bit for bit the
+    results of the same searches one after another."""
+    X, Q = inputs(40000, 600, 96, seed=98)
+    d = db(X, metric, dtype)
+    qs = [dev(np.ascontiguousarray(Q[k::4])) for k in range(4)]
+    ref = [d.search(q, 16, L=512) for q in qs]
+    torch.cuda.synchronize()
+    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    cur = torch.cuda.current_stream()
+    for st in streams:
+        st.wait_stream(cur)
+    outs = []
+    for k, q in enumerate(qs):
+        st = streams[k % 2]
+        with torch.cuda.stream(st):
+            v = torch.full((150, 16), float("nan"), device="cuda")
+            i = torch.full((150, 16), -7, dtype=torch.int32, device="cuda")
+        outs.append(d.search(q, 16, L=512, out=(v, i), stream=st, slot=k % 2))
+    for st in streams:
+        cur.wait_stream(st)
+    torch.cuda.synchronize()
+    S.sync_status()
+    for (v, i), (rv, ri) in zip(outs, ref):
+        assert torch.equal(i, ri)
+        assert torch.equal(v.view(torch.int32), rv.view(torch.int32))
+
+
 def test_recall_plan_and_invalid_calls():
     ensure_built()
     assert S.plan_bins(10 ** 6, 10, 0.95) == 176
