@@ -63,3 +63,30 @@ def test_approx_max_k_many_rows_and_planned_bins():
     assert v.shape == (50, L2)
     ov, oi = oracle.approx_max_k(X[:50].astype(np.float64), K, L2, aggregate_to_topk=False)
     assert np.array_equal(i.cpu().numpy(), oi)
+
+
+@pytest.mark.parametrize("bins", ["mod", "contiguous"])
+@pytest.mark.parametrize("dtype", ["f32", "bf16"])
+@pytest.mark.parametrize("N", [4096, 5000, 70000])
+def test_approx_max_k_16_byte_loads_match_oracle(bins, dtype, N):
+    """L (j mod L bins) and N multiples of the columns one 16-byte load holds
+    (4 FP32, 8 BF16): the vectorised kernels, bit-exact against the oracle
+    including ties and zeros of both signs, rows, grid rows and column runs
+    split over many CTAs (70000 columns span several CTAs of a row)."""
+    ensure_built()
+    M, K = 37, 10
+    X = scores(M, N, 43)
+    t = torch.from_numpy(X).cuda()
+    if dtype == "bf16":
+        t = t.to(torch.bfloat16)
+    Xo = t.float().cpu().numpy().astype(np.float64)
+    for L in (8, 64, 1000, N):
+        for is_min in (False, True):
+            for agg in (False, True):
+                k = min(K, L)
+                v, i = S.approx_max_k(t, k, L=L, bins=bins, is_min=is_min, aggregate_to_topk=agg)
+                ov, oi = oracle.approx_max_k(Xo, k, L, bins=bins, is_min=is_min,
+                                             aggregate_to_topk=agg)
+                v, i = v.cpu().numpy(), i.cpu().numpy()
+                assert np.array_equal(i, oi), (L, is_min, agg)
+                assert np.array_equal(v.astype(np.float64), ov), (L, is_min, agg)
