@@ -911,11 +911,16 @@ def grad_leg(args, lib, pk):
     ms_b = timed(lambda: d.backward(Qd, i, g, dx=dxb, zero_dx=True), args.config_steps, 2)
     ms_b_acc = timed(lambda: d.backward(Qd, i, g, dx=dxb, zero_dx=False), args.config_steps, 2)
     ms_dq = timed(lambda: d.backward(Qd, i, g, want_dx=False), args.config_steps, 2)
+    ms_b_at = timed(lambda: d.backward(Qd, i, g, dx=dxb, zero_dx=True, atomic=True),
+                    args.config_steps, 2)
+    ms_b_acc_det = timed(lambda: d.backward(Qd, i, g, dx=dxb, zero_dx=False, deterministic=True),
+                         args.config_steps, 2)
     S.sync_status()
     touched = int(torch.unique(i).numel())
     flops = 2.0 * M * N * D
     k1 = prof["k1"]["ms_avg"]
-    sparse = M * K * D * 4 + 2 * M * D * 4 + M * K * 8 + 2 * touched * D * 4
+    gather = M * K * D * 4 + 2 * M * D * 4 + M * K * 8
+    sparse = gather + 2 * touched * D * 4
     dense = N * D * 4
     out = {"workload": "iid N(0,1/D) inner product N=%d D=%d M=%d K=%d, BF16" % (N, D, M, K),
            "L": L, "forward": {"value": M / (ms_f / 1e3), "unit": "queries/s",
@@ -926,18 +931,26 @@ def grad_leg(args, lib, pk):
                                             "frac": flops / (k1 / 1e3) / 1e12 /
                                             pk["bf16_tflops"]}},
            "backward": {"ms_dense_dx": ms_b, "ms_accumulate_dx": ms_b_acc, "ms_dq_only": ms_dq,
+                        "ms_dense_dx_atomic": ms_b_at,
+                        "ms_accumulate_dx_deterministic": ms_b_acc_det,
                         "touched_rows": touched,
-                        "algorithmic_bytes": {"dense_dx_fill": dense, "sparse": sparse},
+                        "algorithmic_bytes": {"dense": dense + gather, "accumulate": sparse},
                         "roofline": {"bound": "hbm", "unit": "GB/s", "peak": pk["hbm_gbs"],
-                                     "achieved_dense": (dense + sparse) / (ms_b / 1e3) / 1e9,
-                                     "frac_dense": (dense + sparse) / (ms_b / 1e3) / 1e9 /
+                                     "achieved_dense": (dense + gather) / (ms_b / 1e3) / 1e9,
+                                     "frac_dense": (dense + gather) / (ms_b / 1e3) / 1e9 /
                                      pk["hbm_gbs"],
                                      "achieved_accumulate": sparse / (ms_b_acc / 1e3) / 1e9,
                                      "frac_accumulate": sparse / (ms_b_acc / 1e3) / 1e9 /
                                      pk["hbm_gbs"]},
-                        "bytes_model": "dense: N*D*4 zero fill; sparse: gathered rows M*K*D*4, "
-                                       "q read + dq write 2*M*D*4, idx + g M*K*8, RMW of the "
-                                       "touched dX rows 2*rows*D*4"},
+                        "bytes_model": "dense: every dX row written once N*D*4, gathered rows "
+                                       "M*K*D*4, q read + dq write 2*M*D*4, idx + g M*K*8; "
+                                       "accumulate: the same without the N*D*4, plus read and "
+                                       "write of the touched dX rows 2*rows*D*4",
+                        "dx_modes": "ms_dense_dx: the row path (each dX row written once, "
+                                    "entries in order; deterministic); ms_dense_dx_atomic: zero "
+                                    "fill + FP32 atomics; ms_accumulate_dx: FP32 atomics into "
+                                    "the existing dX; ms_accumulate_dx_deterministic: the row "
+                                    "path adding into it"},
            "score_error": score_errors(d, Xd, Qd, v, i, "ip", n=64)}
     del d, Xd, Qd, dxb
     torch.cuda.empty_cache()

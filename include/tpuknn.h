@@ -394,11 +394,19 @@ size_t knn_search_exact_workspace(int64_t N, int32_t D, int32_t dtype, int32_t m
  * NULL, else from the prepared db_lp/db_scale (dequantised); queries q are
  * FP32 (M x D).
  *   dq : M x D FP32, overwritten (NULL = not needed).
- *   dx : N x D FP32 (NULL = not needed). If zero_dx != 0 the kernel first
- *        writes zeros over all of dx, else it adds into dx.
- *   deterministic: 0 = FP32 atomic adds (order-dependent rounding);
- *        1 = rows gathered in (i, k) order per touched row, bit-reproducible
- *        (needs knn_backward_workspace bytes; otherwise ws may be NULL).
+ *   dx : N x D FP32 (NULL = not needed). If zero_dx != 0 every row of dx
+ *        is overwritten (zeros where no entry selected it), else the
+ *        entries are added into dx.
+ *   workspace: NULL, or knn_backward_workspace bytes (256-byte aligned; a
+ *        smaller one is KNN_ENOMEM). Row path: each row of dx is written
+ *        once by one warp, its entries summed in (i, k) order, bit-
+ *        reproducible; taken with a workspace when zero_dx != 0 (the faster
+ *        way: no separate zero fill) or deterministic != 0. Otherwise: zero
+ *        fill (if zero_dx), then FP32 atomic adds (order-dependent rounding;
+ *        the faster way to add into an existing dx).
+ *   deterministic: 1 = the row path always; the workspace is required
+ *        (KNN_EINVAL if NULL); 0 = the workspace is optional. Not read when
+ *        dx is NULL or M = 0.
  */
 knn_status knn_backward(const void* db_lp, const float* db_scale, const float* x_f32, int64_t N,
                         int32_t D, int32_t dtype, int32_t metric, const float* q, int64_t M,
@@ -406,6 +414,8 @@ knn_status knn_backward(const void* db_lp, const float* db_scale, const float* x
                         float* dx, int32_t zero_dx, int32_t deterministic, void* workspace,
                         size_t ws_bytes, void* stream);
 
+/* Bytes of the workspace of knn_backward: 4 N + 4 M K rounded up (the same
+ * for both values of `deterministic`). */
 size_t knn_backward_workspace(int64_t N, int32_t D, int64_t M, int32_t K, int32_t deterministic);
 
 /*

@@ -864,7 +864,8 @@ knn_status knn_search_exact(const void* db_lp, const float* db_scale, const floa
 
 size_t knn_backward_workspace(int64_t N, int32_t D, int64_t M, int32_t K, int32_t deterministic) {
   (void)D;
-  return backward_ws_bytes(N, M, K, deterministic);
+  (void)deterministic;  // one size serves both modes
+  return backward_ws_bytes(N, M, K);
 }
 
 knn_status knn_backward(const void* db_lp, const float* db_scale, const float* x_f32, int64_t N,
@@ -879,15 +880,15 @@ knn_status knn_backward(const void* db_lp, const float* db_scale, const float* x
   if (!x_f32 && dtype == KNN_E4M3 && !db_scale) return KNN_EINVAL;
   if (M > 0 && (!q || !idx || !grad_val)) return KNN_EINVAL;
   if (M * (int64_t)K >= ((int64_t)1 << 31)) return KNN_EUNSUPPORTED;
-  const size_t need = backward_ws_bytes(N, M, K, deterministic);
-  if (dx && deterministic && M > 0) {
+  const size_t need = backward_ws_bytes(N, M, K);
+  if (dx && M > 0 && (deterministic || workspace)) {
     if (!workspace || !aligned(workspace, kAlign)) return KNN_EINVAL;
     if (ws_bytes < need) return KNN_ENOMEM;
   }
   if (!dq && !dx) return KNN_OK;
   return cuda_status(launch_backward(M, D, K, metric, q, x_f32, db_lp, dtype, knn_row_pitch(D),
                                      db_scale, N, idx, grad_val, dq, dx, zero_dx, deterministic,
-                                     workspace, (cudaStream_t)stream));
+                                     dx && M > 0 ? workspace : nullptr, (cudaStream_t)stream));
 }
 
 // ---------------------------------------------------------------------------

@@ -112,7 +112,7 @@ cudaError_t launch_backward(int64_t M, int D, int K, int metric, const float* q,
                             const float* xscale, int64_t N, const int32_t* idx,
                             const float* g, float* dq, float* dx, int zero_dx, int deterministic,
                             void* ws, cudaStream_t st);
-size_t backward_ws_bytes(int64_t N, int64_t M, int K, int deterministic);
+size_t backward_ws_bytes(int64_t N, int64_t M, int K);
 
 // Largest resident query tile of the tensor-core K1 for this row length
 // (256 or 128), or 0 if the rows are too long.

@@ -199,12 +199,16 @@ class Database:
         return V, A
 
     def backward(self, q, idx, grad_val, want_dq=True, want_dx=True, deterministic=False,
-                 x_f32=None, stream=None, dx=None, zero_dx=True):
+                 x_f32=None, stream=None, dx=None, zero_dx=True, atomic=False):
         """Gradient of sum(grad_val * value(q_i, x_idx)) w.r.t. q and the rows.
 
         dx: an N x D float32 CUDA tensor to write into (default: a new one);
         zero_dx=False adds into it instead of writing zeros over it first
-        (for a caller whose dx is already zero, or who accumulates)."""
+        (for a caller whose dx is already zero, or who accumulates).
+        A workspace is passed, so a zero-filled dx is written row by row in
+        entry order (bit-reproducible), as is every dx with deterministic=True;
+        atomic=True (with deterministic=False) passes none, so the library
+        zero-fills and adds with FP32 atomics instead."""
         q = q.contiguous()
         idx = idx.contiguous()
         grad_val = grad_val.contiguous().float()
@@ -220,8 +224,10 @@ class Database:
         elif not (dx.is_cuda and dx.dtype == torch.float32 and dx.is_contiguous()
                   and tuple(dx.shape) == (self.N, self.D)):
             raise ValueError("dx must be a contiguous N x D float32 CUDA tensor")
+        if atomic and deterministic:
+            raise ValueError("atomic=True is the non-deterministic mode")
         nb = lib.knn_backward_workspace(self.N, self.D, M, K, int(deterministic))
-        ws = self._get_ws(("bwd", M, K), nb) if nb else None
+        ws = self._get_ws(("bwd", M, K), nb) if (nb and want_dx and not atomic) else None
         with torch.cuda.device(self.device):
             check(lib.knn_backward(self.lp.data_ptr(), _ptr(self.scale), _ptr(xf), self.N, self.D,
                                    DTYPE[self.dtype], METRIC[self.metric], q.data_ptr(), M, K,

@@ -223,23 +223,72 @@ def test_autograd_grad_workload_1m_sampled():
     np.testing.assert_allclose(hq[same], oq[same], rtol=0, atol=1e-4 * sq)
 
 
-def test_backward_into_caller_dx_accumulates():
+@pytest.mark.parametrize("atomic", [False, True])
+def test_backward_into_caller_dx_accumulates(atomic):
     """zero_dx=False adds into the caller's dx: two backward passes into one
     buffer give twice one pass (atomic adds of the same values in FP32 may
-    round differently, hence the tolerance); zero_dx=True overwrites."""
+    round differently, hence the tolerance); zero_dx=True overwrites. Both
+    the row kernel and the atomic adds."""
     g = rng(17)
     X = g.standard_normal((5000, 64)).astype(np.float32)
     Q = g.standard_normal((40, 64)).astype(np.float32)
     d = db(X, "ip", "bf16")
     val, idx = d.search(dev(Q), 8, L=128)
     gv = torch.from_numpy(g.standard_normal((40, 8)).astype(np.float32)).cuda()
-    _, dx1 = d.backward(dev(Q), idx, gv, want_dq=False)
+    _, dx1 = d.backward(dev(Q), idx, gv, want_dq=False, atomic=atomic)
     acc = torch.zeros_like(dx1)
     for _ in range(2):
-        d.backward(dev(Q), idx, gv, want_dq=False, dx=acc, zero_dx=False)
+        d.backward(dev(Q), idx, gv, want_dq=False, dx=acc, zero_dx=False, atomic=atomic)
     torch.cuda.synchronize()
     scale = dx1.abs().max().item()
     assert torch.allclose(acc, 2 * dx1, rtol=0, atol=1e-5 * scale)
-    d.backward(dev(Q), idx, gv, want_dq=False, dx=acc, zero_dx=True)
+    d.backward(dev(Q), idx, gv, want_dq=False, dx=acc, zero_dx=True, atomic=atomic)
     torch.cuda.synchronize()
     assert torch.allclose(acc, dx1, rtol=0, atol=1e-6 * scale)
+
+
+@pytest.mark.parametrize("metric", ["ip", "l2", "cos"])
+def test_deterministic_dense_dx_written_once(metric):
+    """deterministic=True with zero_dx: each row of dx is written by one warp,
+    zeros or the row's sum in entry order, over whatever dx held (NaN here).
+    One row is taken by 600 entries (more than a warp sorts in shared memory),
+    some entries are -1 (skipped), K = 37 (two passes of 32 in the dq gather)
+    and D = 99 (ragged; the scalar atomic scatter). Checked against the oracle,
+    against the zero-then-add ordered path and the atomic path, and
+    bit-identical from run to run. Most rows hold more than the 8 entries a
+    lane keeps, so both ways of the row kernel run, writing and adding."""
+    g = rng(23)
+    N, M, D, K = 3000, 600, 99, 37
+    X = g.standard_normal((N, D)).astype(np.float32)
+    Q = g.standard_normal((M, D)).astype(np.float32)
+    idx = g.integers(0, N, size=(M, K)).astype(np.int32)
+    idx[:, 0] = 7
+    idx[::50, 3] = -1
+    gv = g.standard_normal((M, K)).astype(np.float32)
+    d = db(X, metric, "bf16")
+    xf, Qd, Gd = dev(X), dev(Q), dev(gv)
+    Id = torch.from_numpy(idx).cuda()
+    outs = []
+    for _ in range(2):
+        dx = torch.full((N, D), float("nan"), device="cuda")
+        dq, _ = d.backward(Qd, Id, Gd, deterministic=True, x_f32=xf, dx=dx, zero_dx=True)
+        outs.append((host(dq), host(dx)))
+    assert np.array_equal(outs[0][0], outs[1][0])
+    assert np.array_equal(outs[0][1], outs[1][1])
+    gdq, gdx = outs[0]
+    odq, odx = oracle.grad(Q, X, idx, gv, metric)
+    sq, sx = np.abs(odq).max(), np.abs(odx).max()
+    np.testing.assert_allclose(gdq, odq, rtol=0, atol=1e-4 * sq)
+    np.testing.assert_allclose(gdx, odx, rtol=0, atol=1e-4 * sx)
+    touched = np.zeros(N, bool)
+    touched[idx[idx >= 0]] = True
+    assert not gdx[~touched].any()
+    acc = torch.zeros((N, D), device="cuda")
+    d.backward(Qd, Id, Gd, want_dq=False, deterministic=True, x_f32=xf, dx=acc, zero_dx=False)
+    np.testing.assert_allclose(gdx, host(acc), rtol=0, atol=1e-6 * sx)
+    dq_a, dx_a = d.backward(Qd, Id, Gd, x_f32=xf, atomic=True)
+    np.testing.assert_array_equal(host(dq_a), gdq)
+    np.testing.assert_allclose(host(dx_a), odx, rtol=0, atol=1e-4 * sx)
+    # the default (non-deterministic) call takes the same row kernel
+    _, dx_d = d.backward(Qd, Id, Gd, x_f32=xf)
+    np.testing.assert_array_equal(host(dx_d), gdx)

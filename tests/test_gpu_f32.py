@@ -276,9 +276,10 @@ def test_backward_f32_matches_oracle(metric):
     w = g.standard_normal((M, K)).astype(np.float32)
     d = db(X, metric, "f32")
     xf = dev(X)
-    for det in (False, True):
+    # atomic adds, the row kernel, the row kernel as the required deterministic mode
+    for det, atomic in ((False, True), (False, False), (True, False)):
         dq, dx = d.backward(dev(Q), torch.from_numpy(idx).cuda(), dev(w), deterministic=det,
-                            x_f32=xf)
+                            x_f32=xf, atomic=atomic)
         oi = idx.astype(np.int64)
         odq, odx = oracle.grad(Q, X, oi, w.astype(np.float64), metric)
         sq = np.abs(odq).max() + 1.0
