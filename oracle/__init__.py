@@ -10,7 +10,8 @@ Contents
     PartialReduce (Alg. 1) with bins ``j mod L`` or contiguous runs,
     ExactRescoring (Sec. 5), the approx_max_k operator on a given score matrix
     (App. A.1), re-rank, the gradient of selected scores, and the input
-    preparation (bfloat16 / E4M3 rounding, cosine normalisation).
+    preparation (bfloat16 / E4M3 rounding with per-row or one database-wide
+    scale, cosine normalisation).
   * ``recall.py``: the expected-recall law (Eq. 12-13 and its exact form) and
     the bin count from a recall target (Eq. 14, App. A.4).
   * ``loss.py``: the softmax-over-top-K loss and its gradient in FP64.
@@ -24,6 +25,7 @@ from .core import (  # noqa: F401
     build, lib_path,
     exact_topk, partial_reduce, topk_pairs, binwise_topk, rerank, grad, score,
     bin_max, approx_max_k,
-    bf16_round, e4m3_rows, e4m3_round, normalize_rows, set_threads,
+    bf16_round, e4m3_rows, e4m3_round, e4m3_scaled, e4m3_tensor, e4m3_tensor_scale,
+    normalize_rows, set_threads,
 )
 from . import recall, loss  # noqa: F401

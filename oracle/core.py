@@ -59,6 +59,7 @@ def _load():
             lib.orc_score.restype = ctypes.c_double
             lib.orc_bf16_round_array.argtypes = [P, i64, P]
             lib.orc_e4m3_rows.argtypes = [P, i64, i32, P, P]
+            lib.orc_e4m3_scaled.argtypes = [P, i64, ctypes.c_float, P]
             lib.orc_normalize_rows.argtypes = [P, i64, i32, P]
             lib.orc_e4m3_round.argtypes = [ctypes.c_double]
             lib.orc_e4m3_round.restype = ctypes.c_double
@@ -219,6 +220,28 @@ def e4m3_rows(x):
     sc = np.empty((rows,), np.float32)
     _load().orc_e4m3_rows(_p(x), rows, D, _p(out), _p(sc))
     return out, sc
+
+
+def e4m3_tensor_scale(x):
+    """The database-wide E4M3 scale: max |x| over all values / 448 in binary32
+    (1 for an all-zero database)."""
+    mx = np.float32(np.abs(_f32(x)).max()) if np.size(x) else np.float32(0.0)
+    return np.float32(mx / np.float32(448.0)) if mx > 0 else np.float32(1.0)
+
+
+def e4m3_scaled(x, s):
+    """E4M3 quantisation of every value with the one scale s: dequantised
+    values (float64), code = E4M3(x / s) with the division in binary32."""
+    x = _f32(x)
+    out = np.empty(x.shape, np.float64)
+    _load().orc_e4m3_scaled(_p(x), x.size, ctypes.c_float(float(s)), _p(out))
+    return out
+
+
+def e4m3_tensor(x):
+    """E4M3 with one database-wide scale: (dequantised values, the scale)."""
+    s = e4m3_tensor_scale(x)
+    return e4m3_scaled(x, s), s
 
 
 def e4m3_round(v):

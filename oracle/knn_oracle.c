@@ -386,6 +386,17 @@ void orc_e4m3_rows(const float *x, int64_t rows, int D, double *out, float *scal
   }
 }
 
+/* E4M3 quantisation with one given scale s for every value (the database-
+ * wide scale: s = max |x| / 448 over the whole database, binary32 division,
+ * computed by the caller): code = E4M3(x / s) with the division in binary32,
+ * dequantised value = code * s (exact in binary64). */
+void orc_e4m3_scaled(const float *x, int64_t n, float s, double *out) {
+  for (int64_t t = 0; t < n; ++t) {
+    float q = x[t] / s;
+    out[t] = orc_e4m3_round((double)q) * (double)s;
+  }
+}
+
 /* Cosine preparation (Sec. 2: cosine search = MIPS on l2-normalised rows):
  * n2 = sum_d x_d^2 accumulated in binary64 in index order, inv = 1/sqrt(n2),
  * y_d = binary32(x_d * inv). A zero row stays zero. */

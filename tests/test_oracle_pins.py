@@ -513,3 +513,44 @@ def test_approx_max_k_bins_only_and_min_orientation():
             cols = np.arange(l, 50, 8)
             assert amin[i, l] == cols[np.argmin(S[i, cols])]
             assert vmin[i, l] == S[i, cols].min()
+
+
+def test_e4m3_tensor_equals_rows_when_every_row_has_the_same_maximum():
+    """With one maximum |x| shared by every row, the database-wide scale is
+    each row's own scale: e4m3_tensor reduces to the pinned e4m3_rows."""
+    g = rng(22)
+    x = g.uniform(-1.0, 1.0, (40, 33)).astype(np.float32)
+    x[:, 5] = np.where(g.random(40) < 0.5, 1.5, -1.5).astype(np.float32)
+    deq_t, s = oracle.e4m3_tensor(x)
+    deq_r, sc = oracle.e4m3_rows(x)
+    assert (sc == s).all()
+    np.testing.assert_array_equal(deq_t, deq_r)
+
+
+def test_e4m3_tensor_matches_torch_cast():
+    """Codes are torch's float8_e4m3fn cast of x / s (binary32 division)."""
+    torch = pytest.importorskip("torch")
+    g = rng(23)
+    x = (g.standard_normal((64, 96)) * np.exp(g.uniform(-6, 2, (64, 1)))).astype(np.float32)
+    x[7] = 0.0
+    deq, s = oracle.e4m3_tensor(x)
+    assert s == np.float32(np.abs(x).max()) / np.float32(448.0)
+    q = torch.from_numpy(x) / torch.tensor(float(s), dtype=torch.float32)
+    ref = q.to(torch.float8_e4m3fn).to(torch.float64).numpy() * np.float64(s)
+    np.testing.assert_array_equal(deq, ref)
+    # the largest |x| maps to the largest code, a zero row stays zero
+    i = np.unravel_index(np.abs(x).argmax(), x.shape)
+    assert abs(deq[i]) == 448.0 * np.float64(s)
+    assert (deq[7] == 0.0).all()
+    # a row much smaller than the largest keeps its relative precision
+    # (E4M3 is floating point): its codes are still normal numbers
+    rmax = np.abs(x).max(axis=1)
+    small = np.where(rmax > 0, rmax, np.inf).argmin()
+    assert rmax[small] < 1e-3 * rmax.max()
+    nz = x[small] != 0
+    rel = np.abs(deq[small][nz] - x[small][nz]) / np.abs(x[small][nz])
+    assert rel[np.abs(x[small][nz]) / s >= 2.0 ** -6].max() <= 2.0 ** -4
+
+
+def test_e4m3_tensor_scale_of_zero_database():
+    assert oracle.e4m3_tensor_scale(np.zeros((3, 4), np.float32)) == 1.0
