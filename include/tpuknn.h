@@ -57,8 +57,14 @@ typedef enum { KNN_IP = 0, KNN_L2 = 1, KNN_COS = 2 } knn_metric;
 
 /* Element type the contraction runs in. The database and the queries are
  * stored in it; products accumulate in FP32. E4M3 uses one FP32 scale per
- * row: value = code * scale. */
-typedef enum { KNN_F32 = 0, KNN_BF16 = 1, KNN_E4M3 = 2 } knn_dtype;
+ * row: value = code * scale. KNN_E4M3_T stores the database the same way
+ * (codes and a per-row scale array) with ONE scale for every row, the
+ * database-wide max|x| / 448; queries of a KNN_E4M3_T search keep their own
+ * per-row scales. E4M3 being a floating-point code, the shared scale costs
+ * precision only where a value falls below 2^-6 of the scale (subnormal
+ * codes); it lets the contraction compare raw dot products of different rows
+ * directly (the KNN_BF16 kernel's one compare per 16 rows, with IP and COS). */
+typedef enum { KNN_F32 = 0, KNN_BF16 = 1, KNN_E4M3 = 2, KNN_E4M3_T = 3 } knn_dtype;
 
 /* Map from database row j to its bin l (Alg. 1, Sec. 5):
  *   KNN_BINS_MOD        l = j mod L;
@@ -98,7 +104,9 @@ int64_t knn_plan_bins(int64_t N, int32_t K, double recall_target, int32_t round_
  *              copied (and normalised for KNN_COS).
  *   out_scale: rows FP32 scales, required for KNN_E4M3 (scale = max|x|/448,
  *              code = E4M3(x/scale), round-to-nearest-even, saturating; a
- *              zero row gets scale 1), else ignored (may be NULL).
+ *              zero row gets scale 1) and KNN_E4M3_T (every row gets the
+ *              scale of all `rows` together: max over them of |x| / 448, 1
+ *              if all are zero), else ignored (may be NULL).
  *   out_hnorm: rows FP32 values ||x^||^2/2 of the stored (rounded) rows,
  *              required for KNN_L2 (the half-norm of App. A.2, Eq. 19), else
  *              ignored (may be NULL).
@@ -327,8 +335,10 @@ size_t knn_db_search_workspace(const knn_db* db, int64_t M, int32_t K, int64_t L
  * (error below 2^-24 of the norm). With KNN_E4M3 the kernel keeps only the
  * top 32 - c bits of each FP32 score, c <= 13, while it reduces (the low bits
  * hold the row's position in its bin), and the per-query scale is left out of
- * the value (it does not change the order within a query). With KNN_F32 the
- * values are the FP32 scores.
+ * the value (it does not change the order within a query). With KNN_E4M3_T
+ * and IP or COS the values are the FP32 accumulator of the codes' products
+ * times the database scale (per-query scale left out, as for KNN_E4M3); with
+ * L2 it runs as KNN_E4M3. With KNN_F32 the values are the FP32 scores.
  */
 knn_status knn_partial_reduce(const void* db_lp, const float* db_scale, const float* db_hnorm,
                               int64_t N, int32_t D, int32_t dtype, int32_t metric, const float* q,

@@ -11,7 +11,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "libtpuknn.so")
 
 KNN_OK, KNN_EINVAL, KNN_ENOMEM, KNN_ECUDA, KNN_ETIMEOUT, KNN_EUNSUPPORTED = range(6)
 METRIC = {"ip": 0, "l2": 1, "cos": 2}
-DTYPE = {"f32": 0, "bf16": 1, "e4m3": 2}
+DTYPE = {"f32": 0, "bf16": 1, "e4m3": 2, "e4m3t": 3}
 BINS = {"mod": 0, "contiguous": 1}
 RATE = {"minmax": 0, "ffma": 1}
 STATIC_WORKSPACE_BYTES = 16 << 20  # KNN_STATIC_WORKSPACE_BYTES

@@ -68,7 +68,9 @@ constexpr size_t kAlign = 256;
 inline size_t al(size_t x) { return (x + kAlign - 1) & ~(kAlign - 1); }
 inline bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
 inline bool valid_metric(int m) { return m == KNN_IP || m == KNN_L2 || m == KNN_COS; }
-inline bool valid_dtype(int d) { return d == KNN_F32 || d == KNN_BF16 || d == KNN_E4M3; }
+inline bool valid_dtype(int d) {
+  return d == KNN_F32 || d == KNN_BF16 || d == KNN_E4M3 || d == KNN_E4M3_T;
+}
 
 knn_status cuda_status(cudaError_t e) {
   if (e == cudaSuccess) return KNN_OK;
@@ -101,6 +103,7 @@ int64_t plan_bins(int64_t N, int K, double r, int round_to) {
 
 // Tile shape of each K1 variant (BQ = 0: the row length is not supported).
 void k1_tile(int dtype, int D, int64_t M, int* BW, int* BQ) {
+  dtype = stored_dtype(dtype);
   if (dtype == KNN_F32) {
     *BW = 64;
     *BQ = 128;
@@ -128,7 +131,7 @@ K1Plan make_plan(int64_t N, int64_t M, int64_t L, int D, int metric, int dtype,
   p.D = D;
   p.pitch = (int)round_up(D, 16);
   p.metric = metric;
-  p.dtype = dtype;
+  p.dtype = stored_dtype(dtype);  // KNN_E4M3_T runs here as KNN_E4M3 (all scales equal)
   k1_tile(dtype, D, M, &p.BW, &p.BQ);
   if (p.BQ == 0) return p;
   p.g = L < p.BW ? (int)(p.BW / L) : 1;
@@ -197,7 +200,7 @@ QueryBufs query_bytes(int64_t M, int D, int dtype, int metric) {
   const int pitch = (int)round_up(D, 16);
   const int esz = dtype == KNN_F32 ? 4 : (dtype == KNN_BF16 ? 2 : 1);
   b.lp = al((size_t)M * pitch * esz);
-  b.scale = dtype == KNN_E4M3 ? al((size_t)M * 4) : 0;
+  b.scale = stored_dtype(dtype) == KNN_E4M3 ? al((size_t)M * 4) : 0;
   b.f32 = (metric == KNN_COS && dtype != KNN_F32) ? al((size_t)M * D * 4) : 0;
   return b;
 }
@@ -272,7 +275,7 @@ knn_status layout_search(const SearchArgs& a, SearchLayout* s) {
     p.D = a.D;
     p.pitch = (int)round_up(a.D, 16);
     p.metric = a.metric;
-    p.dtype = a.dtype;
+    p.dtype = stored_dtype(a.dtype);
     p.nsplits = 1;
     s->plan = p;
     s->Kp = kprime(a.K, a.rerank, L);
@@ -317,7 +320,7 @@ knn_status layout_search(const SearchArgs& a, SearchLayout* s) {
 knn_status check_pointers(const SearchArgs& a, const float* out_val, const int32_t* out_idx) {
   if (!a.db_lp || !a.q || !out_val || !out_idx) return KNN_EINVAL;
   if (a.metric == KNN_L2 && !a.db_hnorm) return KNN_EINVAL;
-  if (a.dtype == KNN_E4M3 && !a.db_scale) return KNN_EINVAL;
+  if (stored_dtype(a.dtype) == KNN_E4M3 && !a.db_scale) return KNN_EINVAL;
   if (!aligned(a.db_lp, 16) || !aligned(a.q, 4) || !aligned(out_val, 4) || !aligned(out_idx, 4))
     return KNN_EINVAL;
   if (a.db_f32 && !aligned(a.db_f32, 4)) return KNN_EINVAL;
@@ -337,8 +340,9 @@ cudaError_t prep_queries(const SearchArgs& a, const SearchLayout& s, char* ws, c
                                                    : nullptr;
   const int64_t zn = keys64 ? 2 * s.plan.M * s.plan.L
                             : (s.plan.atomic_merge ? s.plan.M * s.plan.Lk : 0);
-  cudaError_t e = launch_prep(a.q, a.M, a.D, s.plan.pitch, a.metric, a.dtype, qlp, qscale, nullptr,
-                              qf, st, zbuf, zn);
+  // queries keep per-row scales with either E4M3 database
+  cudaError_t e = launch_prep(a.q, a.M, a.D, s.plan.pitch, a.metric, stored_dtype(a.dtype), qlp,
+                              qscale, nullptr, qf, st, zbuf, zn);
   if (a.dtype == KNN_F32) {
     *qf32 = reinterpret_cast<const float*>(qlp);
     *q_stride = s.plan.pitch;
@@ -356,8 +360,8 @@ cudaError_t run_k1(const K1Plan& p, const SearchArgs& a, const void* xlp, const 
                    const float* hnorm, const void* qlp, const float* qscale, Partials parts,
                    cudaStream_t st) {
   if (parts.keys64)
-    return launch_k1_tcs(p.N, p.M, p.L, p.D, p.metric, a.bin_map, xlp, hnorm, qlp,
-                         reinterpret_cast<unsigned long long*>(parts.v), st);
+    return launch_k1_tcs(p.N, p.M, p.L, p.D, p.metric, a.dtype, a.bin_map, xlp, xscale, hnorm,
+                         qlp, reinterpret_cast<unsigned long long*>(parts.v), st);
   if (a.dtype == KNN_F32)
     return launch_k1_simt(p, reinterpret_cast<const float*>(xlp), hnorm,
                           reinterpret_cast<const float*>(qlp), parts, st);
@@ -410,7 +414,7 @@ knn_status search_impl(const SearchArgs& a, float* out_val, int32_t* out_idx, vo
   {
     ProfScope ps(3, st);
     e = launch_k3(a.M, a.D, a.metric, cand, s.Kp, a.K, qf32, q_stride, a.db_f32, a.db_lp,
-                  a.dtype, s.plan.pitch, a.db_scale, a.N, out_val, out_idx, st);
+                  stored_dtype(a.dtype), s.plan.pitch, a.db_scale, a.N, out_val, out_idx, st);
   }
   return cuda_status(e);
 }
@@ -498,8 +502,8 @@ knn_status exact_impl(const SearchArgs& a, float* out_val, int32_t* out_idx, voi
     e = launch_k2(p, parts, a.K, n0 == 0 ? nullptr : run, run, st);
     if (e != cudaSuccess) return cuda_status(e);
   }
-  e = launch_k3(a.M, a.D, a.metric, run, a.K, a.K, qf32, q_stride, a.db_f32, a.db_lp, a.dtype,
-                s.plan.pitch, a.db_scale, a.N, out_val, out_idx, st);
+  e = launch_k3(a.M, a.D, a.metric, run, a.K, a.K, qf32, q_stride, a.db_f32, a.db_lp,
+                stored_dtype(a.dtype), s.plan.pitch, a.db_scale, a.N, out_val, out_idx, st);
   return cuda_status(e);
 }
 
@@ -634,7 +638,8 @@ int32_t knn_dtype_bytes(int32_t dtype) {
   switch (dtype) {
     case KNN_F32: return 4;
     case KNN_BF16: return 2;
-    case KNN_E4M3: return 1;
+    case KNN_E4M3:
+    case KNN_E4M3_T: return 1;
     default: return 0;
   }
 }
@@ -652,7 +657,7 @@ knn_status knn_prepare(const float* x, int64_t rows, int32_t D, int32_t metric, 
   if (D > kMaxD) return KNN_EUNSUPPORTED;
   if (rows == 0) return KNN_OK;
   if (!x || !out_lp || !aligned(out_lp, 16) || !aligned(x, 4)) return KNN_EINVAL;
-  if (dtype == KNN_E4M3 && !out_scale) return KNN_EINVAL;
+  if (stored_dtype(dtype) == KNN_E4M3 && !out_scale) return KNN_EINVAL;
   if (metric == KNN_L2 && !out_hnorm) return KNN_EINVAL;
   if (metric == KNN_COS && !out_f32) return KNN_EINVAL;
   return cuda_status(launch_prep(x, rows, D, knn_row_pitch(D), metric, dtype, out_lp, out_scale,
@@ -877,7 +882,7 @@ knn_status knn_backward(const void* db_lp, const float* db_scale, const float* x
     return KNN_EINVAL;
   if (D > kMaxD) return KNN_EUNSUPPORTED;
   if (!x_f32 && !db_lp) return KNN_EINVAL;
-  if (!x_f32 && dtype == KNN_E4M3 && !db_scale) return KNN_EINVAL;
+  if (!x_f32 && stored_dtype(dtype) == KNN_E4M3 && !db_scale) return KNN_EINVAL;
   if (M > 0 && (!q || !idx || !grad_val)) return KNN_EINVAL;
   if (M * (int64_t)K >= ((int64_t)1 << 31)) return KNN_EUNSUPPORTED;
   const size_t need = backward_ws_bytes(N, M, K);
@@ -886,7 +891,8 @@ knn_status knn_backward(const void* db_lp, const float* db_scale, const float* x
     if (ws_bytes < need) return KNN_ENOMEM;
   }
   if (!dq && !dx) return KNN_OK;
-  return cuda_status(launch_backward(M, D, K, metric, q, x_f32, db_lp, dtype, knn_row_pitch(D),
+  return cuda_status(launch_backward(M, D, K, metric, q, x_f32, db_lp, stored_dtype(dtype),
+                                     knn_row_pitch(D),
                                      db_scale, N, idx, grad_val, dq, dx, zero_dx, deterministic,
                                      dx && M > 0 ? workspace : nullptr, (cudaStream_t)stream));
 }
@@ -1097,7 +1103,7 @@ knn_status knn_db_create(const float* x, int64_t N, int32_t D, int32_t metric, i
   const size_t lp_bytes = (size_t)N * knn_row_pitch(D) * knn_dtype_bytes(dtype);
   const bool want_f32 = metric == KNN_COS || keep_f32;
   if (e == cudaSuccess) e = cudaMalloc(&h->lp, lp_bytes);
-  if (e == cudaSuccess && dtype == KNN_E4M3)
+  if (e == cudaSuccess && stored_dtype(dtype) == KNN_E4M3)
     e = cudaMalloc(reinterpret_cast<void**>(&h->scale), (size_t)N * 4);
   if (e == cudaSuccess && metric == KNN_L2)
     e = cudaMalloc(reinterpret_cast<void**>(&h->hnorm), (size_t)N * 4);

@@ -51,6 +51,12 @@ constexpr uint32_t kNegInfBits = 0xff800000u;
 // smaller index gives the larger key. Key 0 is below every real pair and
 // marks an empty slot.
 // ---------------------------------------------------------------------------
+// How rows of `dtype` are stored and decoded: KNN_E4M3_T rows are KNN_E4M3
+// rows whose scales are all equal.
+__host__ __device__ __forceinline__ int stored_dtype(int dtype) {
+  return dtype == KNN_E4M3_T ? KNN_E4M3 : dtype;
+}
+
 __host__ __device__ __forceinline__ uint32_t f2u(float f) {
   uint32_t u;
   memcpy(&u, &f, 4);

@@ -47,6 +47,7 @@
 #include <cuda_bf16.h>
 
 #include "common.cuh"
+#include "dtypes.cuh"
 #include "kernels.h"
 #include "tc_ptx.cuh"
 
@@ -97,6 +98,7 @@ struct TcsArgs {
   int ext;
   uint32_t idesc;
   const float* hnorm;
+  const float* xscale;             // E4M3: the database-wide scale (xscale[0])
   unsigned long long* G;
 };
 
@@ -157,12 +159,14 @@ __device__ __forceinline__ int64_t run_bin_end(int64_t b, int64_t q, int64_t r) 
   return (b + 1) * q + min(b + 1, r);
 }
 
-template <int NKS, int MODE, int BM, int BS>
+template <int NKS, int MODE, int BM, int BS, int DT>
 __global__ void __launch_bounds__(kThreadsS, 1)
 k1_tcs_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmQ,
               const TcsArgs a) {
   using T = StepT<BS>;
   constexpr int kCols = T::kCols, NB = T::kNB, XS = T::kXS, BPW = T::kBPW;
+  // elements of one 128-byte K block (the x coordinate of a K block's box)
+  constexpr int kElS = DT == KNN_E4M3 ? kSpanS : kSpanS / 2;
   static_assert(MODE == kFused || BS == 16, "the K-loop modes use 16-bin steps");
   // 128-byte K blocks per step
   const int NKB = MODE == kFused ? (NKS + 3) / 4 : a.nkb;
@@ -266,7 +270,7 @@ k1_tcs_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
       } else {
         mbar_expect_tx(b_q, a.a_bytes);
         for (int kb = 0; kb < NKB; ++kb)
-          tma_load_2d(smem_u32(sA + (size_t)kb * kQT * kSpanS), &tmQ, b_q, kb * (kSpanS / 2),
+          tma_load_2d(smem_u32(sA + (size_t)kb * kQT * kSpanS), &tmQ, b_q, kb * kElS,
                       (int)(qtile * kQT));
       }
     }
@@ -284,18 +288,18 @@ k1_tcs_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
         uint32_t dst = smem_u32(sB + (size_t)s * a.stage_bytes);
         if (MODE == kKLoopQ) {
           // the queries' K block first: [256 queries][128 B]
-          tma_load_2d(dst, &tmQ, b_full + 8 * s, kb * (kSpanS / 2), (int)(qtile * kQT));
+          tma_load_2d(dst, &tmQ, b_full + 8 * s, kb * kElS, (int)(qtile * kQT));
           dst += kQT * kSpanS;
         }
         if constexpr (BM == kBinsRun) {
           // kCols consecutive rows; rows past N read the fill value (zero)
-          tma_load_2d(dst, &tmX, b_full + 8 * s, kb * (kSpanS / 2),
+          tma_load_2d(dst, &tmX, b_full + 8 * s, kb * kElS,
                       (int)((s_begin + g / NKB) * kCols));
         } else {
-          // one box: K block kb (64 elements), grid rows tg*16 .. +15, bins
+          // one box: K block kb (128 bytes), grid rows tg*16 .. +15, bins
           // bg*BS .. +BS-1, landing as [bin][grid row][128 B]; bins past L,
           // rows past T and elements past the row read the fill value (zero)
-          tma_load_3d(dst, &tmX, b_full + 8 * s, kb * (kSpanS / 2), (int)(tg * kRowsBin),
+          tma_load_3d(dst, &tmX, b_full + 8 * s, kb * kElS, (int)(tg * kRowsBin),
                       (int)(bg * BS));
         }
       }
@@ -391,7 +395,7 @@ k1_tcs_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
               const uint64_t ad = ah + (uint64_t)(((ks >> 2) * kQT * kSpanS + (ks & 3) * 32) >> 4);
               const uint64_t bd =
                   b_desc + (uint64_t)((sk[ks >> 2] * T::kStage + (ks & 3) * 32) >> 4);
-              tc_mma<KNN_BF16>(d_tmem, ad, bd, a.idesc, ks > 0 ? 1u : 0u);
+              tc_mma<DT>(d_tmem, ad, bd, a.idesc, ks > 0 ? 1u : 0u);
               // half 1 is a K block's last reader: its stage is free once the
               // MMAs so far complete (2-3% faster than freeing all stages of
               // the step after the half's last MMA)
@@ -452,8 +456,8 @@ k1_tcs_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
 #pragma unroll
               for (int kk = 0; kk < 4; ++kk)
                 if (kk < steps)
-                  tc_mma<KNN_BF16>(d_tmem, ad + (uint64_t)(kk * 2), bd + (uint64_t)(kk * 2),
-                                   a.idesc, (kb | kk) ? 1u : 0u);
+                  tc_mma<DT>(d_tmem, ad + (uint64_t)(kk * 2), bd + (uint64_t)(kk * 2), a.idesc,
+                             (kb | kk) ? 1u : 0u);
             }
             tc_commit(b_empty + 8 * s);
           }
@@ -597,6 +601,10 @@ k1_tcs_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
   // this thread's query in the current segment
   bool q_ok = false;
   unsigned long long* gq = a.G;
+  // E4M3: keys hold the raw dot of the codes times the database scale (the
+  // per-query scale is left out: it does not change the order in a query)
+  const float xs0 = DT == KNN_E4M3 ? a.xscale[0] : 1.0f;
+  auto scaled = [&](float v) { return DT == KNN_E4M3 ? __fmul_rn(v, xs0) : v; };
   auto set_query = [&](int sg) {
     const int64_t qi = (q0 + sg) * kQT + h * kQH + quad * 32 + lane;
     q_ok = qi < a.M;
@@ -615,7 +623,7 @@ k1_tcs_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
     float bv = __uint_as_float(kNegInfBits);
     auto flush_run = [&]() {
       if (q_ok && brow >= 0)
-        atomicMax(&gq[cur], (unsigned long long)make_key(bv, (int32_t)brow));
+        atomicMax(&gq[cur], (unsigned long long)make_key(scaled(bv), (int32_t)brow));
     };
     bool erun = true;
     for (int sg = 0; sg < nseg && erun; ++sg) {
@@ -701,7 +709,8 @@ k1_tcs_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
     for (int g = 0; g < BPW; ++g) {
       const int64_t b = bgx * BS + cq * BPW + g;
       if (q_ok && bt[g] >= 0 && b < a.L)
-        atomicMax(&gq[b], (unsigned long long)make_key(best[g], (int32_t)(bt[g] * a.L + b)));
+        atomicMax(&gq[b],
+                  (unsigned long long)make_key(scaled(best[g]), (int32_t)(bt[g] * a.L + b)));
       best[g] = __uint_as_float(kNegInfBits);
       bt[g] = -1;
     }
@@ -787,15 +796,33 @@ k1_tcs_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
 
 // Rows of the ragged last grid row: j = T*L + b for b < r = N - T*L. A CTA
 // stages 4 of these rows in shared memory and each of its 128 threads scores
-// one query against all 4 (FP32 sum of the BF16 products, minus the half
-// norm for L2), merging into G by the same 64-bit atomicMax.
+// one query against all 4 (FP32 sum of the BF16 or E4M3 products, minus the
+// half norm for L2; E4M3 times the database scale as in the main kernel),
+// merging into G by the same 64-bit atomicMax.
 constexpr int kTailRows = 4, kTailQ = 128;
+
+// the 16-byte piece v of a row as 16 / esz floats (8 BF16 or 16 E4M3 codes)
+template <int DT>
+__device__ __forceinline__ void tail_unpack(const uint4& v, float (&f)[DT == KNN_E4M3 ? 16 : 8]) {
+  if constexpr (DT == KNN_E4M3) {
+    const uint8_t* c = reinterpret_cast<const uint8_t*>(&v);
+#pragma unroll
+    for (int e = 0; e < 16; ++e) f[e] = e4m3_code_to_float(c[e]);
+  } else {
+    const __nv_bfloat16* b = reinterpret_cast<const __nv_bfloat16*>(&v);
+#pragma unroll
+    for (int e = 0; e < 8; ++e) f[e] = __bfloat162float(b[e]);
+  }
+}
+
+template <int DT>
 __global__ void __launch_bounds__(kTailQ)
-k1_tcs_tail(const __nv_bfloat16* __restrict__ X, const __nv_bfloat16* __restrict__ Q,
-            const float* __restrict__ hnorm, int64_t N, int64_t M, int64_t L, int64_t T,
-            int pitch, int metric, unsigned long long* G) {
-  extern __shared__ uint4 tail_smem[];  // kTailRows rows of `pitch` elements
-  __nv_bfloat16* rows = reinterpret_cast<__nv_bfloat16*>(tail_smem);
+k1_tcs_tail(const uint8_t* __restrict__ X, const uint8_t* __restrict__ Q,
+            const float* __restrict__ hnorm, const float* __restrict__ xscale, int64_t N,
+            int64_t M, int64_t L, int64_t T, int row_bytes, int metric, unsigned long long* G) {
+  constexpr int EPP = DT == KNN_E4M3 ? 16 : 8;  // elements per 16-byte piece
+  extern __shared__ uint4 tail_smem[];  // kTailRows rows of `row_bytes` bytes
+  uint8_t* rows = reinterpret_cast<uint8_t*>(tail_smem);
   // Launched behind the contraction, which has already waited for the
   // queries and the zeroed keys: this kernel's atomics merge with the
   // contraction's in any order. It finishes only after the contraction has
@@ -804,12 +831,12 @@ k1_tcs_tail(const __nv_bfloat16* __restrict__ X, const __nv_bfloat16* __restrict
   const int64_t r = N - T * L;
   const int64_t b0 = (int64_t)blockIdx.x * kTailRows;
   const int nr = (int)min((int64_t)kTailRows, r - b0);
-  const int chunks = pitch / 8;  // 16-byte pieces of a row
+  const int chunks = row_bytes / 16;  // 16-byte pieces of a row
   for (int c = threadIdx.x; c < kTailRows * chunks; c += kTailQ) {
     const int k = c / chunks, part = c % chunks;
     uint4 v = make_uint4(0, 0, 0, 0);
-    if (k < nr) v = reinterpret_cast<const uint4*>(X + (T * L + b0 + k) * pitch)[part];
-    reinterpret_cast<uint4*>(rows + k * pitch)[part] = v;
+    if (k < nr) v = reinterpret_cast<const uint4*>(X + (T * L + b0 + k) * row_bytes)[part];
+    reinterpret_cast<uint4*>(rows + k * row_bytes)[part] = v;
   }
   __syncthreads();
   const int64_t i = (int64_t)blockIdx.y * kTailQ + threadIdx.x;
@@ -817,7 +844,7 @@ k1_tcs_tail(const __nv_bfloat16* __restrict__ X, const __nv_bfloat16* __restrict
   float acc[kTailRows];
 #pragma unroll
   for (int k = 0; k < kTailRows; ++k) acc[k] = 0.0f;
-  const uint4* qrow = reinterpret_cast<const uint4*>(Q + i * pitch);
+  const uint4* qrow = reinterpret_cast<const uint4*>(Q + i * row_bytes);
   // eight 16-byte pieces of the query row in flight at a time
   for (int p0 = 0; p0 < chunks; p0 += 8) {
     uint4 qv[8];
@@ -826,24 +853,24 @@ k1_tcs_tail(const __nv_bfloat16* __restrict__ X, const __nv_bfloat16* __restrict
 #pragma unroll
     for (int u = 0; u < 8; ++u) {
       if (p0 + u >= chunks) break;
-      const __nv_bfloat16* qe = reinterpret_cast<const __nv_bfloat16*>(&qv[u]);
-      float qf[8];
-#pragma unroll
-      for (int e = 0; e < 8; ++e) qf[e] = __bfloat162float(qe[e]);
+      float qf[EPP];
+      tail_unpack<DT>(qv[u], qf);
 #pragma unroll
       for (int k = 0; k < kTailRows; ++k) {
-        const uint4 xv = reinterpret_cast<const uint4*>(rows + k * pitch)[p0 + u];
-        const __nv_bfloat16* xe = reinterpret_cast<const __nv_bfloat16*>(&xv);
+        float xf[EPP];
+        tail_unpack<DT>(reinterpret_cast<const uint4*>(rows + k * row_bytes)[p0 + u], xf);
 #pragma unroll
-        for (int e = 0; e < 8; ++e) acc[k] = fmaf(qf[e], __bfloat162float(xe[e]), acc[k]);
+        for (int e = 0; e < EPP; ++e) acc[k] = fmaf(qf[e], xf[e], acc[k]);
       }
     }
   }
+  const float xs0 = DT == KNN_E4M3 ? xscale[0] : 1.0f;
 #pragma unroll
   for (int k = 0; k < kTailRows; ++k) {
     if (k < nr) {
       const int64_t j = T * L + b0 + k;
-      const float sc = metric == KNN_L2 ? acc[k] - hnorm[j] : acc[k];
+      const float sc = metric == KNN_L2 ? acc[k] - hnorm[j]
+                                        : (DT == KNN_E4M3 ? __fmul_rn(acc[k], xs0) : acc[k]);
       atomicMax(&G[i * L + b0 + k], (unsigned long long)make_key(sc, (int32_t)j));
     }
   }
@@ -865,33 +892,39 @@ PFN_cuTensorMapEncodeTiled_v12000 get_encode_s() {
   return fn;
 }
 
-// 2-D BF16 map: inner extent `inner` elements, `rows` rows `stride_el`
-// elements apart, box 64 x box_rows, 128-byte swizzle.
+CUtensorMapDataType map_type(int esz) {
+  return esz == 1 ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+}
+
+// 2-D map of BF16 (esz 2) or E4M3 codes (esz 1): inner extent `inner`
+// elements, `rows` rows `stride_el` elements apart, box of 128 bytes x
+// box_rows, 128-byte swizzle.
 bool make_map_s(CUtensorMap* m, const void* base, int64_t inner, int64_t rows, int64_t stride_el,
-                int box_rows) {
+                int box_rows, int esz) {
   auto enc = get_encode_s();
   if (!enc) return false;
   cuuint64_t dims[2] = {(cuuint64_t)inner, (cuuint64_t)rows};
-  cuuint64_t strides[1] = {(cuuint64_t)stride_el * 2};
-  cuuint32_t box[2] = {(cuuint32_t)(kSpanS / 2), (cuuint32_t)box_rows};
+  cuuint64_t strides[1] = {(cuuint64_t)stride_el * esz};
+  cuuint32_t box[2] = {(cuuint32_t)(kSpanS / esz), (cuuint32_t)box_rows};
   cuuint32_t estr[2] = {1, 1};
-  return enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box,
+  return enc(m, map_type(esz), 2, const_cast<void*>(base), dims, strides, box,
              estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-// 3-D BF16 view of the database for the step boxes: element d of grid row t,
+// 3-D view of the database for the step boxes: element d of grid row t,
 // bin b is row t*L + b. Dimensions (d, t, b) with the bin outermost, so a
-// box of (64, 16, bs) lands as [bin][grid row][128 B]: each bin's 16 rows are
-// consecutive accumulator columns.
-bool make_map_grid(CUtensorMap* m, const void* base, int64_t pitch, int64_t L, int64_t T, int bs) {
+// box of (128 bytes, 16, bs) lands as [bin][grid row][128 B]: each bin's 16
+// rows are consecutive accumulator columns.
+bool make_map_grid(CUtensorMap* m, const void* base, int64_t pitch, int64_t L, int64_t T, int bs,
+                   int esz) {
   auto enc = get_encode_s();
   if (!enc) return false;
   cuuint64_t dims[3] = {(cuuint64_t)pitch, (cuuint64_t)T, (cuuint64_t)L};
-  cuuint64_t strides[2] = {(cuuint64_t)(L * pitch * 2), (cuuint64_t)(pitch * 2)};
-  cuuint32_t box[3] = {(cuuint32_t)(kSpanS / 2), (cuuint32_t)kRowsBin, (cuuint32_t)bs};
+  cuuint64_t strides[2] = {(cuuint64_t)(L * pitch * esz), (cuuint64_t)(pitch * esz)};
+  cuuint32_t box[3] = {(cuuint32_t)(kSpanS / esz), (cuuint32_t)kRowsBin, (cuuint32_t)bs};
   cuuint32_t estr[3] = {1, 1, 1};
-  return enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(base), dims, strides, box,
+  return enc(m, map_type(esz), 3, const_cast<void*>(base), dims, strides, box,
              estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
@@ -946,12 +979,13 @@ size_t tcs_fixed_smem(int ext) {
 // whole step's K blocks plus one of look-ahead), kKLoopA (resident query
 // tile, at least 2 stages of one K block), kKLoopQ (query K block streamed in
 // every stage). The K-loop modes use 16-bin steps.
-bool tcs_shape(int D, int metric, TcsShape* sh) {
+bool tcs_shape(int D, int metric, int esz, TcsShape* sh) {
   const int pitch = (int)round_up(D, 16);
   const size_t budget = 227 * 1024;
   const int ext = metric == KNN_L2;
-  sh->nkb = (int)cdiv((int64_t)pitch * 2, kSpanS);
-  const int nks = (int)cdiv((int64_t)pitch * 2, 32);
+  // 128-byte K blocks and 32-byte MMA K-steps (16 BF16 or 32 E4M3 elements)
+  sh->nkb = (int)cdiv((int64_t)pitch * esz, kSpanS);
+  const int nks = (int)cdiv((int64_t)pitch * esz, 32);
   const uint32_t a_res = (uint32_t)(sh->nkb * kQT * kSpanS);
   // kFused: K-steps rounded up to an even count (the extra step multiplies
   // zero query columns: the query box reads zeros past the row)
@@ -991,64 +1025,72 @@ bool tcs_shape(int D, int metric, TcsShape* sh) {
   return true;
 }
 
-template <int NKS, int MODE, int BM, int BS>
+template <int NKS, int MODE, int BM, int BS, int DT>
 cudaError_t launch_tcs(const CUtensorMap& mx, const CUtensorMap& mq, const TcsArgs& a, size_t smem,
                        int64_t blocks, cudaStream_t st) {
   // setmaxnreg.inc waits until the registers it asks for are free: refuse to
   // launch unless the launch-time allocation covers the split.
   cudaFuncAttributes fa;
-  cudaError_t e = cudaFuncGetAttributes(&fa, k1_tcs_kernel<NKS, MODE, BM, BS>);
+  cudaError_t e = cudaFuncGetAttributes(&fa, k1_tcs_kernel<NKS, MODE, BM, BS, DT>);
   if (e != cudaSuccess) return e;
   if ((int64_t)round_up(fa.numRegs, 8) * kThreadsS < 128 * kCtrlRegsS + 512 * kEpiRegsS)
     return cudaErrorNotSupported;
-  e = cudaFuncSetAttribute(k1_tcs_kernel<NKS, MODE, BM, BS>,
+  e = cudaFuncSetAttribute(k1_tcs_kernel<NKS, MODE, BM, BS, DT>,
                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   if constexpr (BM == kBinsRun) {
     // Contiguous bins: a plain launch. Started early behind the query prep,
     // the CTAs land on SMs in the order those free up, and the sharers of a
     // part end up far apart (measured: 0.244 -> 0.284 ms per search).
-    k1_tcs_kernel<NKS, MODE, BM, BS><<<(unsigned)blocks, kThreadsS, smem, st>>>(mx, mq, a);
+    k1_tcs_kernel<NKS, MODE, BM, BS, DT><<<(unsigned)blocks, kThreadsS, smem, st>>>(mx, mq, a);
     return cudaGetLastError();
   } else {
-    return launch_pdl(k1_tcs_kernel<NKS, MODE, BM, BS>, dim3((unsigned)blocks), dim3(kThreadsS),
+    return launch_pdl(k1_tcs_kernel<NKS, MODE, BM, BS, DT>, dim3((unsigned)blocks), dim3(kThreadsS),
                       smem, st, mx, mq, a);
   }
 }
 
 }  // namespace
 
+// KNN_BF16 with any metric; KNN_E4M3_T (one database-wide scale) with IP
+// and COS (the L2 half norm enters the BF16 contraction as an extra K block,
+// which the E4M3 MMAs do not take).
 bool k1_tcs_supported(int dtype, int D, int metric, int64_t N, int64_t L) {
   TcsShape sh;
-  if (dtype != KNN_BF16 || metric < KNN_IP || metric > KNN_COS) return false;
-  if (!tcs_shape(D, metric, &sh)) return false;
+  if (metric < KNN_IP || metric > KNN_COS) return false;
+  if (dtype != KNN_BF16 && !(dtype == KNN_E4M3_T && metric != KNN_L2)) return false;
+  const int esz = dtype == KNN_BF16 ? 2 : 1;
+  if (!tcs_shape(D, metric, esz, &sh)) return false;
   if (L < 1 || L > N || N >= ((int64_t)1 << 31)) return false;
   // the grid view's row stride (L rows) must stay below 2^40 bytes
-  return L * round_up(D, 16) * 2 < ((int64_t)1 << 40);
+  return L * round_up(D, 16) * esz < ((int64_t)1 << 40);
 }
 
-template <int BM>
+template <int BM, int DT>
 cudaError_t launch_tcs_mode(const TcsShape& sh, const CUtensorMap& mx, const CUtensorMap& mq,
                             const TcsArgs& a, int64_t blocks, cudaStream_t st) {
-  if (sh.mode == kKLoopA) return launch_tcs<4, kKLoopA, BM, 16>(mx, mq, a, sh.smem, blocks, st);
-  if (sh.mode == kKLoopQ) return launch_tcs<4, kKLoopQ, BM, 16>(mx, mq, a, sh.smem, blocks, st);
+  if (sh.mode == kKLoopA) return launch_tcs<4, kKLoopA, BM, 16, DT>(mx, mq, a, sh.smem, blocks, st);
+  if (sh.mode == kKLoopQ) return launch_tcs<4, kKLoopQ, BM, 16, DT>(mx, mq, a, sh.smem, blocks, st);
   constexpr int FB = kFusedBins;
   switch (sh.nksteps) {
-    case 2: return launch_tcs<2, kFused, BM, FB>(mx, mq, a, sh.smem, blocks, st);
-    case 4: return launch_tcs<4, kFused, BM, FB>(mx, mq, a, sh.smem, blocks, st);
-    case 6: return launch_tcs<6, kFused, BM, FB>(mx, mq, a, sh.smem, blocks, st);
-    case 8: return launch_tcs<8, kFused, BM, FB>(mx, mq, a, sh.smem, blocks, st);
+    case 2: return launch_tcs<2, kFused, BM, FB, DT>(mx, mq, a, sh.smem, blocks, st);
+    case 4: return launch_tcs<4, kFused, BM, FB, DT>(mx, mq, a, sh.smem, blocks, st);
+    case 6: return launch_tcs<6, kFused, BM, FB, DT>(mx, mq, a, sh.smem, blocks, st);
+    case 8: return launch_tcs<8, kFused, BM, FB, DT>(mx, mq, a, sh.smem, blocks, st);
     default: return cudaErrorNotSupported;
   }
 }
 
-cudaError_t launch_k1_tcs(int64_t N, int64_t M, int64_t L, int D, int metric, int bin_map,
-                          const void* X, const float* hnorm, const void* Qp,
-                          unsigned long long* G, cudaStream_t st) {
+cudaError_t launch_k1_tcs(int64_t N, int64_t M, int64_t L, int D, int metric, int dtype,
+                          int bin_map, const void* X, const float* xscale, const float* hnorm,
+                          const void* Qp, unsigned long long* G, cudaStream_t st) {
   TcsShape sh;
-  if (!k1_tcs_supported(KNN_BF16, D, metric, N, L) || !tcs_shape(D, metric, &sh))
+  const bool e4 = dtype == KNN_E4M3_T;
+  const int esz = e4 ? 1 : 2;
+  if (!k1_tcs_supported(dtype, D, metric, N, L) || !tcs_shape(D, metric, esz, &sh))
     return cudaErrorNotSupported;
   if (metric == KNN_L2 && !hnorm) return cudaErrorInvalidValue;
+  if (e4 && !xscale) return cudaErrorInvalidValue;
   if ((reinterpret_cast<uintptr_t>(X) & 15) || (reinterpret_cast<uintptr_t>(Qp) & 15))
     return cudaErrorInvalidValue;
   if (M <= 0) return cudaSuccess;
@@ -1078,29 +1120,39 @@ cudaError_t launch_k1_tcs(int64_t N, int64_t M, int64_t L, int D, int metric, in
   a.a_bytes = sh.a_bytes;
   a.stage_bytes = sh.stage_bytes;
   a.ext = metric == KNN_L2 ? 1 : 0;
-  // D = F32, A = B = BF16, both K-major, N = cols, M = 128
-  a.idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(cols >> 3) << 17) |
+  // D = F32, A = B = BF16 (kind::f16) or E4M3 (kind::f8f6f4, format 0), both
+  // K-major, N = cols, M = 128
+  a.idesc = (1u << 4) | (e4 ? 0u : (1u << 7) | (1u << 10)) | ((uint32_t)(cols >> 3) << 17) |
             ((uint32_t)(kQH >> 4) << 24);
   a.hnorm = hnorm;
+  a.xscale = xscale;
   a.G = G;
   CUtensorMap mx, mq;
-  const bool mapped = runs ? make_map_s(&mx, X, pitch, N, pitch, cols)
-                           : make_map_grid(&mx, X, pitch, L, a.T, sh.bs);
+  const bool mapped = runs ? make_map_s(&mx, X, pitch, N, pitch, cols, esz)
+                           : make_map_grid(&mx, X, pitch, L, a.T, sh.bs, esz);
   if (!mapped) return cudaErrorInvalidValue;
-  if (!make_map_s(&mq, Qp, pitch, M, pitch, kQT)) return cudaErrorInvalidValue;
+  if (!make_map_s(&mq, Qp, pitch, M, pitch, kQT, esz)) return cudaErrorInvalidValue;
   const int64_t blocks = a.groups * a.parts;
   if (blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
-  cudaError_t e = runs ? launch_tcs_mode<kBinsRun>(sh, mx, mq, a, blocks, st)
-                       : launch_tcs_mode<kBinsMod>(sh, mx, mq, a, blocks, st);
+  cudaError_t e;
+  if (e4)
+    e = runs ? launch_tcs_mode<kBinsRun, KNN_E4M3>(sh, mx, mq, a, blocks, st)
+             : launch_tcs_mode<kBinsMod, KNN_E4M3>(sh, mx, mq, a, blocks, st);
+  else
+    e = runs ? launch_tcs_mode<kBinsRun, KNN_BF16>(sh, mx, mq, a, blocks, st)
+             : launch_tcs_mode<kBinsMod, KNN_BF16>(sh, mx, mq, a, blocks, st);
   if (e != cudaSuccess) return e;
   const int64_t r = N - a.T * L;
   if (!runs && r > 0) {
     dim3 grid((unsigned)cdiv(r, kTailRows), (unsigned)cdiv(M, kTailQ));
-    const size_t tsmem = (size_t)kTailRows * pitch * 2;  // <= 32 KB (pitch <= 4096)
-    e = launch_pdl(k1_tcs_tail, grid, dim3(kTailQ), tsmem, st,
-                   reinterpret_cast<const __nv_bfloat16*>(X),
-                   reinterpret_cast<const __nv_bfloat16*>(Qp), hnorm, N, M, L, a.T, pitch, metric,
-                   G);
+    const int row_bytes = pitch * esz;
+    const size_t tsmem = (size_t)kTailRows * row_bytes;  // <= 32 KB (pitch <= 4096)
+    const uint8_t* xb = reinterpret_cast<const uint8_t*>(X);
+    const uint8_t* qb = reinterpret_cast<const uint8_t*>(Qp);
+    e = e4 ? launch_pdl(k1_tcs_tail<KNN_E4M3>, grid, dim3(kTailQ), tsmem, st, xb, qb, hnorm,
+                        xscale, N, M, L, a.T, row_bytes, metric, G)
+           : launch_pdl(k1_tcs_tail<KNN_BF16>, grid, dim3(kTailQ), tsmem, st, xb, qb, hnorm,
+                        xscale, N, M, L, a.T, row_bytes, metric, G);
   }
   return e;
 }

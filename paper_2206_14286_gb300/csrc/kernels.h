@@ -58,15 +58,16 @@ cudaError_t launch_k1_simt(const K1Plan& p, const float* X, const float* hnorm, 
 cudaError_t launch_k1_tc(const K1Plan& p, const void* X, const float* xscale, const float* hnorm,
                          const void* Qp, const float* qscale, Partials out, cudaStream_t st);
 
-// Tensor-core K1 (BF16, rows up to 4096 elements), queries on TMEM lanes;
+// Tensor-core K1 (BF16, rows up to 4096 elements; or E4M3 codes with one
+// database-wide scale xscale[0], IP and COS), queries on TMEM lanes;
 // with bin_map KNN_BINS_MOD each bin's rows sit side by side in the
 // accumulator (the ragged last grid row is scored by a small extra kernel),
 // with KNN_BINS_CONTIGUOUS a step is 256 consecutive rows. G[M][L] receives
 // ordered 64-bit (score, ~index) keys by atomicMax and must be zero on entry.
 bool k1_tcs_supported(int dtype, int D, int metric, int64_t N, int64_t L);
-cudaError_t launch_k1_tcs(int64_t N, int64_t M, int64_t L, int D, int metric, int bin_map,
-                          const void* X, const float* hnorm, const void* Qp,
-                          unsigned long long* G, cudaStream_t st);
+cudaError_t launch_k1_tcs(int64_t N, int64_t M, int64_t L, int D, int metric, int dtype,
+                          int bin_map, const void* X, const float* xscale, const float* hnorm,
+                          const void* Qp, unsigned long long* G, cudaStream_t st);
 bool k1_tcs_take_timeout();
 bool k1_tcs_set_wait_limit(unsigned long long ns);
 

@@ -8,7 +8,7 @@ import torch
 from . import _lib
 from ._lib import METRIC, DTYPE, BINS, check
 
-_ESIZE = {"f32": 4, "bf16": 2, "e4m3": 1}
+_ESIZE = {"f32": 4, "bf16": 2, "e4m3": 1, "e4m3t": 1}
 
 
 def _stream(stream):
@@ -40,7 +40,8 @@ class Database:
     """A device-resident database prepared for search (knn_prepare).
 
     x: N x D float32 CUDA tensor. metric: 'ip' | 'l2' | 'cos'.
-    dtype: 'f32' | 'bf16' | 'e4m3' (the contraction's element type).
+    dtype: 'f32' | 'bf16' | 'e4m3' (per-row scales) | 'e4m3t' (one scale for
+    the whole database) -- the contraction's element type.
     keep_f32: keep FP32 rows for the final re-rank (for 'cos' the
     unit-length copy is always kept; otherwise this holds a reference to x).
     """
@@ -55,7 +56,8 @@ class Database:
         self.pitch = row_pitch(self.D)
         dev = x.device
         self.lp = torch.empty(self.N * self.pitch * _ESIZE[dtype], dtype=torch.uint8, device=dev)
-        self.scale = torch.empty(self.N, dtype=torch.float32, device=dev) if dtype == "e4m3" else None
+        self.scale = (torch.empty(self.N, dtype=torch.float32, device=dev)
+                      if dtype in ("e4m3", "e4m3t") else None)
         self.hnorm = torch.empty(self.N, dtype=torch.float32, device=dev) if metric == "l2" else None
         if metric == "cos":
             self.f32 = torch.empty((self.N, self.D), dtype=torch.float32, device=dev)

@@ -72,6 +72,26 @@ def test_prepare_e4m3_bits(metric):
         np.testing.assert_allclose(d.hnorm.cpu().numpy(), 0.5 * (ref * ref).sum(1), rtol=1e-6)
 
 
+@pytest.mark.parametrize("metric", ["ip", "l2", "cos"])
+@pytest.mark.parametrize("rows,D", [(1000, 96), (70001, 40), (1, 16)])
+def test_prepare_e4m3_tensor_bits(metric, rows, D):
+    """One database-wide scale: every row's scale is max |y| / 448 over all
+    rows (y the unit row for COS), codes E4M3(y / s), bit for bit."""
+    X, _ = inputs(rows, 0, D, seed=rows + D, scale=2.0)
+    X[:: max(1, rows // 3)] *= 1e-3      # rows far below the largest
+    if rows > 7:
+        X[7] = 0.0
+    d = db(X, metric, "e4m3t")
+    src = oracle.normalize_rows(X) if metric == "cos" else X
+    ref, s = oracle.e4m3_tensor(src)
+    assert (d.scale.cpu().numpy() == s).all()
+    codes = d.lp.view(torch.float8_e4m3fn).reshape(rows, d.pitch).float().cpu().numpy()
+    assert (codes[:, D:] == 0).all()
+    np.testing.assert_array_equal(codes[:, :D].astype(np.float64) * np.float64(s), ref)
+    if metric == "l2":
+        np.testing.assert_allclose(d.hnorm.cpu().numpy(), 0.5 * (ref * ref).sum(1), rtol=1e-6)
+
+
 # ----------------------------------------------------------------------------
 # PartialReduce (Alg. 1) alone
 # ----------------------------------------------------------------------------

@@ -30,13 +30,23 @@ def inputs(N, M, D, seed=0):
     return g.standard_normal((N, D)).astype(np.float32), g.standard_normal((M, D)).astype(np.float32)
 
 
-def stored(A, metric, dtype):
-    """(dequantised stored rows, FP32 rows used by the re-rank) per the oracle."""
+def stored(A, metric, dtype, query=False):
+    """(dequantised stored rows, FP32 rows used by the re-rank) per the oracle.
+    'e4m3t' stores the database with one scale and the queries per row."""
     src = oracle.normalize_rows(A) if metric == "cos" else A.astype(np.float32)
     if dtype == "bf16":
         return oracle.bf16_round(src), src.astype(np.float64)
+    if dtype == "e4m3t" and not query:
+        deq, _ = oracle.e4m3_tensor(src)
+        return deq, src.astype(np.float64)
     deq, _ = oracle.e4m3_rows(src)
     return deq, src.astype(np.float64)
+
+
+def tcs_e4m3(dtype, metric):
+    """E4M3 with one database scale runs the BF16 kernel's design (FP32
+    accumulator in the keys) for IP and COS; with L2 it runs as 'e4m3'."""
+    return dtype == "e4m3t" and metric != "l2"
 
 
 def om(metric):
@@ -46,14 +56,14 @@ def om(metric):
 # ----------------------------------------------------------------------------
 # PartialReduce alone
 # ----------------------------------------------------------------------------
-@pytest.mark.parametrize("dtype", ["bf16", "e4m3"])
+@pytest.mark.parametrize("dtype", ["bf16", "e4m3", "e4m3t"])
 @pytest.mark.parametrize("metric", METRICS)
 @pytest.mark.parametrize("shape", [(3001, 70, 72), (5000, 300, 128), (2500, 40, 256), (700, 9, 16)])
 def test_partial_reduce_lowp(dtype, metric, shape):
     N, M, D = shape
     X, Q = inputs(N, M, D, seed=N + M)
     Xs, _ = stored(X, metric, dtype)
-    Qs, _ = stored(Q, metric, dtype)
+    Qs, _ = stored(Q, metric, dtype, query=True)
     d = db(X, metric, dtype)
     Sm = PT.score_matrix(Qs, Xs, om(metric))
     for L in (1, 5, 100, 128, 300, N):
@@ -62,12 +72,17 @@ def test_partial_reduce_lowp(dtype, metric, shape):
         Vo, Ao = oracle.partial_reduce(Qs, Xs, L, om(metric))
         if metric == "l2":
             Vo = (Vo + (Qs ** 2).sum(1)[:, None]) / 2.0
-        if dtype == "e4m3" and metric != "l2":
+        if dtype != "bf16" and metric != "l2":
             # the kernel leaves the per-query scale out of the value
             _, qsc = oracle.e4m3_rows(oracle.normalize_rows(Q) if metric == "cos" else Q)
             Vo = Vo / qsc[:, None].astype(np.float64)
         scale = PT.query_scale(Qs, Xs, metric)
-        if dtype == "bf16":
+        if tcs_e4m3(dtype, metric):
+            # FP32 accumulator of the codes' exact products, times the
+            # database scale (in the scale without the query's)
+            tol_bin = PT.fp32_acc_tol(Qs, Xs, metric)
+            tight = (tol_bin / qsc)[:, None] + 2.0 ** -20 * np.abs(Vo)
+        elif dtype == "bf16":
             # the BF16 kernel keeps the FP32 accumulator in its 64-bit keys;
             # its values are in the relaxed scale (half of -|q-x|^2 for L2)
             tol_bin = PT.fp32_acc_tol(Qs, Xs, metric)
@@ -89,11 +104,11 @@ def test_partial_reduce_lowp(dtype, metric, shape):
         own = Sm[np.arange(M)[:, None], A]
         if metric == "l2":
             own = (own + (Qs ** 2).sum(1)[:, None]) / 2.0
-        if dtype == "e4m3" and metric != "l2":
+        if dtype != "bf16" and metric != "l2":
             own = own / qsc[:, None]
         assert np.all(err[decided] <= tight[decided]), (L, err[decided].max())
         assert np.all(np.abs(V - own) <= tight), (L,)
-        if dtype == "bf16":
+        if dtype == "bf16" or tcs_e4m3(dtype, metric):
             assert decided.mean() > 0.9, (L, decided.mean())
 
 
@@ -152,7 +167,7 @@ def test_search_bf16_long_rows(metric):
 def lowp_oracle_side(X, Q, metric, dtype, K, L, rerank, bins="mod"):
     """The oracle's answer and the decided masks of run_lowp (no GPU)."""
     Xs, Xf = stored(X, metric, dtype)
-    Qs, Qf = stored(Q, metric, dtype)
+    Qs, Qf = stored(Q, metric, dtype, query=True)
     Kp = min(max(1, rerank) * K, L)
     V, A = oracle.partial_reduce(Qs, Xs, L, om(metric), bins=bins)
     _, cand = oracle.topk_pairs(V, A, Kp)
@@ -167,7 +182,7 @@ def lowp_oracle_side(X, Q, metric, dtype, K, L, rerank, bins="mod"):
     # a stricter rule derived from the kernels' arithmetic: the BF16 kernel
     # keeps the FP32 accumulator in its keys; the E4M3 kernel's packed key
     # keeps scores to 2^-10 of their magnitude, plus FP32 accumulation
-    if dtype == "bf16":
+    if dtype == "bf16" or tcs_e4m3(dtype, metric):
         tol_d = PT.fp32_acc_tol(Qs, Xs, metric)
     else:
         tol_d = 2.0 ** -9 * (scale_lp if metric == "l2" else np.abs(S_lp).max(1)) + \
@@ -193,7 +208,7 @@ def run_lowp(X, Q, metric, dtype, K, L, rerank, bins="mod"):
     return frac, gi
 
 
-@pytest.mark.parametrize("dtype", ["bf16", "e4m3"])
+@pytest.mark.parametrize("dtype", ["bf16", "e4m3", "e4m3t"])
 @pytest.mark.parametrize("metric", METRICS)
 def test_search_lowp_small(dtype, metric):
     X, Q = inputs(6007, 131, 64, seed=21)
@@ -203,7 +218,8 @@ def test_search_lowp_small(dtype, metric):
         # oracle side alone (BF16: 0.83-1.0; E4M3 IP/COS: 0.37-0.97; E4M3 L2,
         # whose packed-key truncation scales with the norm-dominated relaxed
         # score: 0.08-0.78)
-        floor = 0.75 if dtype == "bf16" else (0.05 if metric == "l2" else 0.3)
+        floor = 0.75 if dtype == "bf16" or tcs_e4m3(dtype, metric) else \
+            (0.05 if metric == "l2" else 0.3)
         assert frac > floor, (K, L, rr, frac)
 
 
@@ -253,7 +269,7 @@ def test_search_contiguous_bf16_small(metric):
         assert frac > 0.75, (K, L, rr, frac)      # decided: 0.82-1.0
 
 
-@pytest.mark.parametrize("dtype", ["bf16", "e4m3"])
+@pytest.mark.parametrize("dtype", ["bf16", "e4m3", "e4m3t"])
 @pytest.mark.parametrize("metric", ["ip", "l2"])
 def test_exact_search_lowp(dtype, metric):
     X, Q = inputs(9000, 150, 96, seed=22)
@@ -261,7 +277,7 @@ def test_exact_search_lowp(dtype, metric):
     val, idx = d.search_exact(dev(Q), 7)
     gv, gi = host(val), host(idx)
     Xs, Xf = stored(X, metric, dtype)
-    Qs, Qf = stored(Q, metric, dtype)
+    Qs, Qf = stored(Q, metric, dtype, query=True)
     _, cand = oracle.exact_topk(Qs, Xs, 7, metric)
     ov, oi = oracle.rerank(Qf, Xf, cand, 7, metric)
     S_lp = PT.score_matrix(Qs, Xs, metric)
@@ -316,14 +332,55 @@ def test_search_fused_rescoring_bounds(metric):
             assert len(set(r[r >= 0].tolist())) == int((r >= 0).sum())
 
 
+@pytest.mark.parametrize("dtype", ["bf16", "e4m3t"])
 @pytest.mark.parametrize("metric", METRICS)
-def test_search_ragged_last_grid_row(metric):
+def test_search_ragged_last_grid_row(dtype, metric):
     """With j mod L bins the N mod L rows of the ragged last grid row are
     scored by their own kernel and merge with the tensor-core bins: one such
     row, and a few hundred of them, with L up to the fused rescoring's 1024."""
+    if dtype == "e4m3t" and metric == "l2":
+        pytest.skip("E4M3 with L2 runs the per-row-scale kernel, which has no ragged path")
     for N, L in [(257, 64), (1456, 300), (2657, 600), (2303, 1024)]:
         X, Q = inputs(N, 77, 64, seed=N)
-        frac, gi = run_lowp(X, Q, metric, "bf16", 10, L, 2)
+        frac, gi = run_lowp(X, Q, metric, dtype, 10, L, 2)
         assert frac > 0.75, (N, L, frac)          # decided: 0.80-0.95
         ragged = N - (N // L) * L
         assert ragged in (1, 256, 257, 255)
+
+
+@pytest.mark.parametrize("metric", ["ip", "cos"])
+def test_search_contiguous_e4m3t_small(metric):
+    """Contiguous bins with E4M3 codes and one database scale (the BF16
+    kernel's run walk with E4M3 MMAs)."""
+    X, Q = inputs(6007, 131, 64, seed=32)
+    for K, L, rr in [(10, 176, 2), (4, 4, 1), (8, 6007, 1)]:
+        frac, _ = run_lowp(X, Q, metric, "e4m3t", K, L, rr, bins="contiguous")
+        assert frac > 0.75, (K, L, rr, frac)
+
+
+@pytest.mark.parametrize("metric", ["ip", "cos"])
+@pytest.mark.parametrize("shape", [(1500, 33, 768), (600, 3, 4096), (2049, 17, 200)])
+def test_partial_reduce_e4m3t_long_rows(metric, shape):
+    """E4M3 rows longer than 128 bytes walk one 128-byte K block per stage
+    (up to 4096 elements), as BF16 rows longer than 64 elements do."""
+    N, M, D = shape
+    X, Q = inputs(N, M, D, seed=N + D + 1)
+    Xs, _ = stored(X, metric, "e4m3t")
+    Qs, _ = stored(Q, metric, "e4m3t", query=True)
+    _, qsc = oracle.e4m3_rows(oracle.normalize_rows(Q) if metric == "cos" else Q)
+    d = db(X, metric, "e4m3t")
+    Sm = PT.score_matrix(Qs, Xs, om(metric))
+    tol = PT.fp32_acc_tol(Qs, Xs, metric)
+    for L in (1, 16, 100, N):
+        V, A = d.partial_reduce(dev(Q), L)
+        V, A = host(V).astype(np.float64), host(A)
+        Vo, Ao = oracle.partial_reduce(Qs, Xs, L, om(metric))
+        Vo = Vo / qsc[:, None]
+        best, second = PT.bin_best_second(Sm, L)
+        decided = (best - second) > 2 * tol[:, None]
+        assert np.all(A % L == np.arange(L)[None, :])
+        np.testing.assert_array_equal(A[decided], Ao[decided])
+        tight = (tol / qsc)[:, None] + 2.0 ** -20 * np.abs(Vo)
+        own = Sm[np.arange(M)[:, None], A] / qsc[:, None]
+        assert np.all(np.abs(V - Vo)[decided] <= tight[decided]), (L,)
+        assert np.all(np.abs(V - own) <= tight), (L,)
