@@ -72,7 +72,8 @@ typedef enum { KNN_F32 = 0, KNN_BF16 = 1, KNN_E4M3 = 2, KNN_E4M3_T = 3 } knn_dty
  *                       balanced for any L: with q = N / L and r = N mod L, bin l
  *                       holds rows [l*q + min(l, r), (l+1)*q + min(l+1, r)).
  * Both give every bin N/L rows (up to one), so the recall law of Sec. 5.1 is the
- * same for exchangeable rows. KNN_BINS_CONTIGUOUS is implemented for KNN_BF16. */
+ * same for exchangeable rows. KNN_BINS_CONTIGUOUS is implemented for KNN_BF16, and
+ * for KNN_E4M3_T with KNN_IP and KNN_COS. */
 typedef enum { KNN_BINS_MOD = 0, KNN_BINS_CONTIGUOUS = 1 } knn_bin_map;
 
 const char* knn_status_string(int status);
