@@ -408,7 +408,7 @@ knn_status search_impl(const SearchArgs& a, float* out_val, int32_t* out_idx, vo
   uint64_t* cand = reinterpret_cast<uint64_t*>(ws + s.off_cand);
   {
     ProfScope ps(2, st);
-    e = launch_k2(s.plan, parts, s.Kp, nullptr, cand, st);
+    e = launch_k2(s.plan, parts, s.Kp, nullptr, cand, st, /*sorted=*/false);
   }
   if (e != cudaSuccess) return cuda_status(e);
   {
@@ -1009,7 +1009,7 @@ knn_status knn_shard_rescore(const int64_t* keys, int64_t M, int64_t L, int32_t 
   p.g = 1;
   p.nsplits = 1;
   Partials parts{reinterpret_cast<float*>(G), nullptr, 0, false, true};
-  if (e == cudaSuccess) e = launch_k2(p, parts, Kp, nullptr, cand, st);
+  if (e == cudaSuccess) e = launch_k2(p, parts, Kp, nullptr, cand, st, /*sorted=*/false);
   const float* qf = q;
   int64_t q_stride = D;
   if (e == cudaSuccess && metric == KNN_COS) {

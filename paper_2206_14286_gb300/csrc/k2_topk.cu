@@ -524,6 +524,126 @@ cudaError_t run_k2_wsort(const Src& src, int64_t M, int64_t L, int Kp, uint64_t*
   return cudaGetLastError();
 }
 
+// The best Kp of a query's L keys as a set, in no particular order (for the
+// re-rank, which orders its candidates itself): one CTA of 256 threads per
+// query holds the L keys in registers (KPT per thread, L <= 256 KPT) and
+// finds the Kp-th largest key T by a radix select over the 64 key bits, 8 per
+// pass from the most significant: per pass a 256-bin histogram in shared
+// memory of the keys that match the digits chosen so far, and warp 0 picks
+// the digit where the count from the top reaches Kp. It stops once every key
+// matching the chosen digits is needed. Output: the keys above the chosen
+// digits, then as many matching keys as still needed (all of them but for
+// repeated empty keys, 0). Keys are distinct otherwise, so this is the set
+// of the Kp largest, the same set a sort would keep.
+template <class Src, int KPT>
+__global__ void __launch_bounds__(256)
+k2_select_kernel(Src src, int64_t L, int Kp, uint64_t* __restrict__ out_keys) {
+  __shared__ uint32_t hist[256];
+  __shared__ int s_digit, s_above, s_stop, s_hi, s_eq;
+  const int64_t i = blockIdx.x;
+  const int tid = threadIdx.x, lane = tid & 31;
+  uint64_t k[KPT];
+#pragma unroll
+  for (int u = 0; u < KPT; ++u) {
+    const int64_t b = (int64_t)u * 256 + tid;
+    k[u] = b < L ? src.key(i, b) : 0;
+  }
+  uint64_t prefix = 0, mask = 0;
+  int need = Kp;  // keys still to take among those matching the prefix
+  for (int shift = 56; shift >= 0; shift -= 8) {
+    hist[tid] = 0;
+    __syncthreads();
+#pragma unroll
+    for (int u = 0; u < KPT; ++u)
+      if ((int64_t)u * 256 + tid < L && (k[u] & mask) == prefix)
+        atomicAdd(&hist[(uint32_t)(k[u] >> shift) & 255u], 1u);
+    __syncthreads();
+    if (tid < 32) {
+      // lane l sums bins 255-8l .. 248-8l; counts from the top by a warp scan
+      uint32_t c[8], sum = 0;
+#pragma unroll
+      for (int t = 0; t < 8; ++t) {
+        c[t] = hist[255 - 8 * lane - t];
+        sum += c[t];
+      }
+      uint32_t incl = sum;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+      }
+      const uint32_t excl = incl - sum;  // keys matching the prefix in higher bins
+      const bool mine = excl < (uint32_t)need && (uint32_t)need <= incl;
+      const unsigned who = __ballot_sync(0xffffffffu, mine);
+      if (who == 0) {
+        // fewer matching keys than needed cannot happen for need <= L
+        if (lane == 0) {
+          s_digit = 0;
+          s_above = 0;
+          s_stop = 1;
+        }
+      } else if (mine) {
+        uint32_t above = excl, ct = 0;
+        int tf = 7;
+        bool found = false;
+#pragma unroll
+        for (int t = 0; t < 8; ++t) {
+          if (!found) {
+            if (above + c[t] >= (uint32_t)need) {
+              tf = t;
+              ct = c[t];
+              found = true;
+            } else {
+              above += c[t];
+            }
+          }
+        }
+        s_digit = 255 - 8 * lane - tf;
+        s_above = (int)above;
+        s_stop = (above + ct == (uint32_t)need) ? 1 : 0;
+      }
+    }
+    __syncthreads();
+    prefix |= (uint64_t)s_digit << shift;
+    mask |= (uint64_t)0xFF << shift;
+    need -= s_above;
+    const bool stop = s_stop != 0;
+    __syncthreads();  // s_* are rewritten by the next pass
+    if (stop) break;
+  }
+  // the keys above the prefix (masked), then `need` of those matching it
+  if (tid == 0) {
+    s_hi = 0;
+    s_eq = 0;
+  }
+  __syncthreads();
+  uint64_t* out = out_keys + i * Kp;
+  const int n_hi = Kp - need;
+#pragma unroll
+  for (int u = 0; u < KPT; ++u) {
+    if ((int64_t)u * 256 + tid >= L) continue;
+    const uint64_t m = k[u] & mask;
+    if (m > prefix) {
+      out[atomicAdd(&s_hi, 1)] = k[u];
+    } else if (m == prefix) {
+      const int p = atomicAdd(&s_eq, 1);
+      if (p < need) out[n_hi + p] = k[u];
+    }
+  }
+}
+
+template <class Src>
+cudaError_t run_k2_select(const Src& src, int64_t M, int64_t L, int Kp, uint64_t* out,
+                          cudaStream_t st) {
+  if (L <= 2048)
+    k2_select_kernel<Src, 8><<<(unsigned)M, 256, 0, st>>>(src, L, Kp, out);
+  else if (L <= 4096)
+    k2_select_kernel<Src, 16><<<(unsigned)M, 256, 0, st>>>(src, L, Kp, out);
+  else
+    k2_select_kernel<Src, 32><<<(unsigned)M, 256, 0, st>>>(src, L, Kp, out);
+  return cudaGetLastError();
+}
+
 }  // namespace
 
 cudaError_t launch_merge_bins(const K1Plan& p, Partials parts, float* out_v, int32_t* out_a,
@@ -551,35 +671,39 @@ cudaError_t launch_merge_bins(const K1Plan& p, Partials parts, float* out_v, int
 
 // Per query: the warp kernel serves up to 1024 candidates and 64 selected,
 // the sorting CTA kernel up to 2048 candidates and 256 selected (both with
-// no running input); the streaming CTA kernel everything else.
+// no running input); beyond those, when an unordered set will do, the radix
+// select up to 8192 candidates; the streaming CTA kernel everything else.
 template <class Src>
 cudaError_t dispatch_k2(const Src& s, const K1Plan& p, int Kp, const uint64_t* run_in,
-                        uint64_t* out_keys, cudaStream_t st) {
+                        uint64_t* out_keys, bool sorted, cudaStream_t st) {
   if (run_in == nullptr && p.L <= 1024 && Kp <= 64) return run_k2_warp(s, p.M, p.L, Kp, out_keys, st);
   if (run_in == nullptr && p.L <= 2048 && Kp <= 256 && p.M <= 0x7fffffffLL)
     return run_k2_wsort(s, p.M, p.L, Kp, out_keys, st);
+  // a set is enough (the re-rank orders it): radix select instead of sorts
+  if (!sorted && run_in == nullptr && p.L <= 8192 && p.M <= 0x7fffffffLL)
+    return run_k2_select(s, p.M, p.L, Kp, out_keys, st);
   return run_k2(s, p.M, p.L, Kp, run_in, out_keys, st);
 }
 
 cudaError_t launch_k2(const K1Plan& p, Partials parts, int Kp, const uint64_t* run_in,
-                      uint64_t* out_keys, cudaStream_t st) {
+                      uint64_t* out_keys, cudaStream_t st, bool sorted) {
   if (p.M <= 0) return cudaSuccess;
   if (parts.keys64) {
     KeySource s{reinterpret_cast<const uint64_t*>(parts.v), p.L};
-    return dispatch_k2(s, p, Kp, run_in, out_keys, st);
+    return dispatch_k2(s, p, Kp, run_in, out_keys, sorted, st);
   }
   if (parts.a) {
     PairSource s{parts.v, parts.a, p.M, p.Lk, p.L, p.nsplits, parts.index_offset, p.g};
-    return dispatch_k2(s, p, Kp, run_in, out_keys, st);
+    return dispatch_k2(s, p, Kp, run_in, out_keys, sorted, st);
   }
   if (parts.merged) {
     MergedSource s{reinterpret_cast<const uint32_t*>(parts.v), p.M, p.Lk, p.L,
                    parts.index_offset, p.g, p.code_bits};
-    return dispatch_k2(s, p, Kp, run_in, out_keys, st);
+    return dispatch_k2(s, p, Kp, run_in, out_keys, sorted, st);
   }
   PackedSource s{reinterpret_cast<const uint32_t*>(parts.v), p.M, p.Lk, p.L, p.nsplits,
                  p.tiles_per_split, parts.index_offset, p.g, p.code_bits};
-  return dispatch_k2(s, p, Kp, run_in, out_keys, st);
+  return dispatch_k2(s, p, Kp, run_in, out_keys, sorted, st);
 }
 
 bool k23_supported(int64_t M, int64_t L, int Kp, int K, int D, const float* qf32,

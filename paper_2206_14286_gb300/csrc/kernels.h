@@ -81,9 +81,11 @@ cudaError_t launch_keys_to_pairs(const uint64_t* keys, int64_t n, int neg, float
 
 // K2: per query, merge the partials of every split and fold and select the
 // best Kp (score, index) keys, sorted. If run_in is given its Kp keys per
-// query join the selection (running top-K of a chunked search).
+// query join the selection (running top-K of a chunked search). With
+// sorted = false the keys may come in any order (for the re-rank, which
+// orders its candidates itself).
 cudaError_t launch_k2(const K1Plan& p, Partials parts, int Kp, const uint64_t* run_in,
-                      uint64_t* out_keys, cudaStream_t st);
+                      uint64_t* out_keys, cudaStream_t st, bool sorted = true);
 
 // PartialReduce output alone: per (query, bin) the merged best value and
 // index (index -1 and value -inf for a bin no row reached).

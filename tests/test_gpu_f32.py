@@ -323,12 +323,13 @@ def test_backward_deterministic_is_bitwise_repeatable():
 
 
 @pytest.mark.parametrize("dtype", ["f32", "bf16"])
-@pytest.mark.parametrize("K,L", [(100, 2048), (150, 3000), (10, 1025)])
+@pytest.mark.parametrize("K,L", [(100, 2048), (150, 3000), (10, 1025), (64, 4097), (40, 8192)])
 def test_search_many_queries_large_L_cta_rescoring(dtype, K, L):
     """L > 1024 or K' > 64 take a CTA ExactRescoring kernel: up to L = 2048
     and K' = 256 the one that sorts 256-key lists per warp and merges them,
-    beyond that the one whose candidate buffer fills and flushes many times
-    per query. 1500 queries against the oracle catch a lost candidate."""
+    beyond that (up to L = 8192, 8 / 16 / 32 keys per thread) the radix
+    select, whose set the re-rank orders. 1500 queries against the oracle
+    catch a lost candidate."""
     X, Q = inputs(20000, 1500, 32, seed=91)
     if dtype == "f32":
         # few queries are decided at all 100 ranks; the per-query rules (values

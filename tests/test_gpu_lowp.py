@@ -384,3 +384,16 @@ def test_partial_reduce_e4m3t_long_rows(metric, shape):
         own = Sm[np.arange(M)[:, None], A] / qsc[:, None]
         assert np.all(np.abs(V - Vo)[decided] <= tight[decided]), (L,)
         assert np.all(np.abs(V - own) <= tight), (L,)
+
+
+@pytest.mark.parametrize("K,L,rr", [(100, 2049, 3), (64, 4097, 8), (1, 2500, 2500), (10, 8192, 300)])
+def test_search_select_rescoring_edges(K, L, rr):
+    """ExactRescoring as a radix select (L > 2048 or K' > 256, up to 8192):
+    the key-per-thread boundaries (L = 2049, 4097, 8192) and K' = L (every
+    bin winner re-ranked: the select keeps them all). i.i.d. rows of length
+    32 leave few queries decided at every rank (0-0.13 here); run_lowp's
+    per-query rules (values by rank, own values, bin maxima) cover them all."""
+    X, Q = inputs(20000, 45, 32, seed=L + K)
+    _, gi = run_lowp(X, Q, "ip", "bf16", K, L, rr)
+    for r in gi:
+        assert len(set(r.tolist())) == K
