@@ -796,33 +796,17 @@ k1_tcs_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
 
 // Rows of the ragged last grid row: j = T*L + b for b < r = N - T*L. A CTA
 // stages 4 of these rows in shared memory and each of its 128 threads scores
-// one query against all 4 (FP32 sum of the BF16 or E4M3 products, minus the
-// half norm for L2; E4M3 times the database scale as in the main kernel),
-// merging into G by the same 64-bit atomicMax.
+// one query against all 4 (FP32 sum of the BF16 products, minus the half
+// norm for L2), merging into G by the same 64-bit atomicMax. (One template
+// for both element types, with byte pointers, measured 7 us slower per
+// search inside the launch chain than this BF16 kernel; E4M3 has its own.)
 constexpr int kTailRows = 4, kTailQ = 128;
-
-// the 16-byte piece v of a row as 16 / esz floats (8 BF16 or 16 E4M3 codes)
-template <int DT>
-__device__ __forceinline__ void tail_unpack(const uint4& v, float (&f)[DT == KNN_E4M3 ? 16 : 8]) {
-  if constexpr (DT == KNN_E4M3) {
-    const uint8_t* c = reinterpret_cast<const uint8_t*>(&v);
-#pragma unroll
-    for (int e = 0; e < 16; ++e) f[e] = e4m3_code_to_float(c[e]);
-  } else {
-    const __nv_bfloat16* b = reinterpret_cast<const __nv_bfloat16*>(&v);
-#pragma unroll
-    for (int e = 0; e < 8; ++e) f[e] = __bfloat162float(b[e]);
-  }
-}
-
-template <int DT>
 __global__ void __launch_bounds__(kTailQ)
-k1_tcs_tail(const uint8_t* __restrict__ X, const uint8_t* __restrict__ Q,
-            const float* __restrict__ hnorm, const float* __restrict__ xscale, int64_t N,
-            int64_t M, int64_t L, int64_t T, int row_bytes, int metric, unsigned long long* G) {
-  constexpr int EPP = DT == KNN_E4M3 ? 16 : 8;  // elements per 16-byte piece
-  extern __shared__ uint4 tail_smem[];  // kTailRows rows of `row_bytes` bytes
-  uint8_t* rows = reinterpret_cast<uint8_t*>(tail_smem);
+k1_tcs_tail(const __nv_bfloat16* __restrict__ X, const __nv_bfloat16* __restrict__ Q,
+            const float* __restrict__ hnorm, int64_t N, int64_t M, int64_t L, int64_t T,
+            int pitch, int metric, unsigned long long* G) {
+  extern __shared__ uint4 tail_smem[];  // kTailRows rows of `pitch` elements
+  __nv_bfloat16* rows = reinterpret_cast<__nv_bfloat16*>(tail_smem);
   // Launched behind the contraction, which has already waited for the
   // queries and the zeroed keys: this kernel's atomics merge with the
   // contraction's in any order. It finishes only after the contraction has
@@ -831,12 +815,12 @@ k1_tcs_tail(const uint8_t* __restrict__ X, const uint8_t* __restrict__ Q,
   const int64_t r = N - T * L;
   const int64_t b0 = (int64_t)blockIdx.x * kTailRows;
   const int nr = (int)min((int64_t)kTailRows, r - b0);
-  const int chunks = row_bytes / 16;  // 16-byte pieces of a row
+  const int chunks = pitch / 8;  // 16-byte pieces of a row
   for (int c = threadIdx.x; c < kTailRows * chunks; c += kTailQ) {
     const int k = c / chunks, part = c % chunks;
     uint4 v = make_uint4(0, 0, 0, 0);
-    if (k < nr) v = reinterpret_cast<const uint4*>(X + (T * L + b0 + k) * row_bytes)[part];
-    reinterpret_cast<uint4*>(rows + k * row_bytes)[part] = v;
+    if (k < nr) v = reinterpret_cast<const uint4*>(X + (T * L + b0 + k) * pitch)[part];
+    reinterpret_cast<uint4*>(rows + k * pitch)[part] = v;
   }
   __syncthreads();
   const int64_t i = (int64_t)blockIdx.y * kTailQ + threadIdx.x;
@@ -844,7 +828,7 @@ k1_tcs_tail(const uint8_t* __restrict__ X, const uint8_t* __restrict__ Q,
   float acc[kTailRows];
 #pragma unroll
   for (int k = 0; k < kTailRows; ++k) acc[k] = 0.0f;
-  const uint4* qrow = reinterpret_cast<const uint4*>(Q + i * row_bytes);
+  const uint4* qrow = reinterpret_cast<const uint4*>(Q + i * pitch);
   // eight 16-byte pieces of the query row in flight at a time
   for (int p0 = 0; p0 < chunks; p0 += 8) {
     uint4 qv[8];
@@ -853,25 +837,83 @@ k1_tcs_tail(const uint8_t* __restrict__ X, const uint8_t* __restrict__ Q,
 #pragma unroll
     for (int u = 0; u < 8; ++u) {
       if (p0 + u >= chunks) break;
-      float qf[EPP];
-      tail_unpack<DT>(qv[u], qf);
+      const __nv_bfloat16* qe = reinterpret_cast<const __nv_bfloat16*>(&qv[u]);
+      float qf[8];
+#pragma unroll
+      for (int e = 0; e < 8; ++e) qf[e] = __bfloat162float(qe[e]);
 #pragma unroll
       for (int k = 0; k < kTailRows; ++k) {
-        float xf[EPP];
-        tail_unpack<DT>(reinterpret_cast<const uint4*>(rows + k * row_bytes)[p0 + u], xf);
+        const uint4 xv = reinterpret_cast<const uint4*>(rows + k * pitch)[p0 + u];
+        const __nv_bfloat16* xe = reinterpret_cast<const __nv_bfloat16*>(&xv);
 #pragma unroll
-        for (int e = 0; e < EPP; ++e) acc[k] = fmaf(qf[e], xf[e], acc[k]);
+        for (int e = 0; e < 8; ++e) acc[k] = fmaf(qf[e], __bfloat162float(xe[e]), acc[k]);
       }
     }
   }
-  const float xs0 = DT == KNN_E4M3 ? xscale[0] : 1.0f;
 #pragma unroll
   for (int k = 0; k < kTailRows; ++k) {
     if (k < nr) {
       const int64_t j = T * L + b0 + k;
-      const float sc = metric == KNN_L2 ? acc[k] - hnorm[j]
-                                        : (DT == KNN_E4M3 ? __fmul_rn(acc[k], xs0) : acc[k]);
+      const float sc = metric == KNN_L2 ? acc[k] - hnorm[j] : acc[k];
       atomicMax(&G[i * L + b0 + k], (unsigned long long)make_key(sc, (int32_t)j));
+    }
+  }
+  }
+  pdl_wait();
+}
+
+// The same for E4M3 codes (16 per 16-byte piece), the FP32 sum times the
+// database scale as in the main kernel (IP and COS only).
+__global__ void __launch_bounds__(kTailQ)
+k1_tcs_tail_e4m3(const uint8_t* __restrict__ X, const uint8_t* __restrict__ Q,
+                 const float* __restrict__ xscale, int64_t N, int64_t M, int64_t L, int64_t T,
+                 int pitch, unsigned long long* G) {
+  extern __shared__ uint4 tail_smem[];  // kTailRows rows of `pitch` bytes
+  uint8_t* rows = reinterpret_cast<uint8_t*>(tail_smem);
+  pdl_trigger();
+  const int64_t r = N - T * L;
+  const int64_t b0 = (int64_t)blockIdx.x * kTailRows;
+  const int nr = (int)min((int64_t)kTailRows, r - b0);
+  const int chunks = pitch / 16;  // 16-byte pieces of a row
+  for (int c = threadIdx.x; c < kTailRows * chunks; c += kTailQ) {
+    const int k = c / chunks, part = c % chunks;
+    uint4 v = make_uint4(0, 0, 0, 0);
+    if (k < nr) v = reinterpret_cast<const uint4*>(X + (T * L + b0 + k) * pitch)[part];
+    reinterpret_cast<uint4*>(rows + k * pitch)[part] = v;
+  }
+  __syncthreads();
+  const int64_t i = (int64_t)blockIdx.y * kTailQ + threadIdx.x;
+  if (i < M) {
+  float acc[kTailRows];
+#pragma unroll
+  for (int k = 0; k < kTailRows; ++k) acc[k] = 0.0f;
+  const uint4* qrow = reinterpret_cast<const uint4*>(Q + i * pitch);
+  for (int p0 = 0; p0 < chunks; p0 += 4) {
+    uint4 qv[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) qv[u] = p0 + u < chunks ? qrow[p0 + u] : make_uint4(0, 0, 0, 0);
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      if (p0 + u >= chunks) break;
+      const uint8_t* qc = reinterpret_cast<const uint8_t*>(&qv[u]);
+      float qf[16];
+#pragma unroll
+      for (int e = 0; e < 16; ++e) qf[e] = e4m3_code_to_float(qc[e]);
+#pragma unroll
+      for (int k = 0; k < kTailRows; ++k) {
+        const uint4 xv = reinterpret_cast<const uint4*>(rows + k * pitch)[p0 + u];
+        const uint8_t* xc = reinterpret_cast<const uint8_t*>(&xv);
+#pragma unroll
+        for (int e = 0; e < 16; ++e) acc[k] = fmaf(qf[e], e4m3_code_to_float(xc[e]), acc[k]);
+      }
+    }
+  }
+  const float xs0 = xscale[0];
+#pragma unroll
+  for (int k = 0; k < kTailRows; ++k) {
+    if (k < nr) {
+      const int64_t j = T * L + b0 + k;
+      atomicMax(&G[i * L + b0 + k], (unsigned long long)make_key(__fmul_rn(acc[k], xs0), (int32_t)j));
     }
   }
   }
@@ -1145,14 +1187,16 @@ cudaError_t launch_k1_tcs(int64_t N, int64_t M, int64_t L, int D, int metric, in
   const int64_t r = N - a.T * L;
   if (!runs && r > 0) {
     dim3 grid((unsigned)cdiv(r, kTailRows), (unsigned)cdiv(M, kTailQ));
-    const int row_bytes = pitch * esz;
-    const size_t tsmem = (size_t)kTailRows * row_bytes;  // <= 32 KB (pitch <= 4096)
-    const uint8_t* xb = reinterpret_cast<const uint8_t*>(X);
-    const uint8_t* qb = reinterpret_cast<const uint8_t*>(Qp);
-    e = e4 ? launch_pdl(k1_tcs_tail<KNN_E4M3>, grid, dim3(kTailQ), tsmem, st, xb, qb, hnorm,
-                        xscale, N, M, L, a.T, row_bytes, metric, G)
-           : launch_pdl(k1_tcs_tail<KNN_BF16>, grid, dim3(kTailQ), tsmem, st, xb, qb, hnorm,
-                        xscale, N, M, L, a.T, row_bytes, metric, G);
+    const size_t tsmem = (size_t)kTailRows * pitch * esz;  // <= 32 KB (pitch <= 4096)
+    if (e4)
+      e = launch_pdl(k1_tcs_tail_e4m3, grid, dim3(kTailQ), tsmem, st,
+                     reinterpret_cast<const uint8_t*>(X), reinterpret_cast<const uint8_t*>(Qp),
+                     xscale, N, M, L, a.T, pitch, G);
+    else
+      e = launch_pdl(k1_tcs_tail, grid, dim3(kTailQ), tsmem, st,
+                     reinterpret_cast<const __nv_bfloat16*>(X),
+                     reinterpret_cast<const __nv_bfloat16*>(Qp), hnorm, N, M, L, a.T, pitch,
+                     metric, G);
   }
   return e;
 }
