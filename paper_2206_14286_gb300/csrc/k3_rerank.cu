@@ -4,7 +4,7 @@
 //
 // Kp <= 32: one warp per query (k3_warp4_kernel for 16-byte aligned FP32
 // rows, k3_warp_kernel otherwise), the keys sorted across the lanes. Larger
-// Kp: one CTA per query; each warp scores candidates one at a time with lanes
+// Kp: one CTA per query; each warp scores four candidates at a time with lanes
 // splitting D (coalesced row reads), then the Kp keys are sorted in shared
 // memory. Values: IP <q,x>; L2 sum (q-x)^2 evaluated directly; COS <q,x> of
 // the unit-length rows.
@@ -25,27 +25,49 @@ k3_rerank_kernel(const uint64_t* __restrict__ cand, int Kp, int K, int P2, int D
   const int64_t i = blockIdx.x;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
   const float* q = qf32 + i * q_stride;
-  for (int c = warp; c < Kp; c += nwarps) {
-    const uint64_t key = cand[i * Kp + c];
-    const int32_t j = key ? key_index(key) : -1;
-    if (j < 0 || j >= N) {
-      if (lane == 0) sk[c] = 0;
-      continue;
+  // a warp scores kCand candidates together, their row loads in flight at
+  // once; per candidate the same sums in the same order as one at a time
+  constexpr int kCand = 4;
+  for (int c0 = warp * kCand; c0 < Kp; c0 += nwarps * kCand) {
+    int32_t jj[kCand];
+#pragma unroll
+    for (int u = 0; u < kCand; ++u) {
+      const uint64_t key = c0 + u < Kp ? cand[i * Kp + c0 + u] : 0;
+      const int32_t j = key ? key_index(key) : -1;
+      jj[u] = (j >= 0 && j < N) ? j : -1;
     }
-    float acc = 0.0f;
+    float acc[kCand];
+#pragma unroll
+    for (int u = 0; u < kCand; ++u) acc[u] = 0.0f;
     for (int d = lane; d < D; d += 32) {
-      const float x = xf32 ? xf32[(int64_t)j * D + d] : load_stored(xlp, dtype, j, pitch, d, xscale);
       const float qq = q[d];
-      if (metric == KNN_L2) {
-        const float t = qq - x;
-        acc = fmaf(t, t, acc);
-      } else {
-        acc = fmaf(qq, x, acc);
+      float xv[kCand];
+#pragma unroll
+      for (int u = 0; u < kCand; ++u)
+        xv[u] = jj[u] < 0 ? 0.0f
+                          : (xf32 ? xf32[(int64_t)jj[u] * D + d]
+                                  : load_stored(xlp, dtype, jj[u], pitch, d, xscale));
+#pragma unroll
+      for (int u = 0; u < kCand; ++u) {
+        if (metric == KNN_L2) {
+          const float t = qq - xv[u];
+          acc[u] = fmaf(t, t, acc[u]);
+        } else {
+          acc[u] = fmaf(qq, xv[u], acc[u]);
+        }
       }
     }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    if (lane == 0) sk[c] = make_key(metric == KNN_L2 ? -acc : acc, j);
+    for (int u = 0; u < kCand; ++u) {
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) acc[u] += __shfl_xor_sync(0xffffffffu, acc[u], o);
+    }
+    if (lane == 0) {
+#pragma unroll
+      for (int u = 0; u < kCand; ++u)
+        if (c0 + u < Kp)
+          sk[c0 + u] = jj[u] < 0 ? 0 : make_key(metric == KNN_L2 ? -acc[u] : acc[u], jj[u]);
+    }
   }
   for (int t = Kp + threadIdx.x; t < P2; t += blockDim.x) sk[t] = 0;
   bitonic_sort_desc(sk, P2);
