@@ -142,7 +142,8 @@ knn_status knn_prepare(const float* x, int64_t rows, int32_t D, int32_t metric, 
  *   workspace : device scratch of at least knn_search_workspace(...) bytes,
  *               256-byte aligned. Its contents on entry do not matter.
  * M = 0 is a valid no-op. Errors: KNN_EINVAL (sizes, NULL, alignment),
- * KNN_ENOMEM (workspace too small), KNN_EUNSUPPORTED (D > 4096).
+ * KNN_ENOMEM (workspace too small), KNN_EUNSUPPORTED (D > 4096; with E4M3
+ * D > 256, except KNN_E4M3_T with KNN_IP or KNN_COS).
  */
 knn_status knn_search(const void* db_lp, const float* db_scale, const float* db_hnorm,
                       const float* db_f32, int64_t N, int32_t D, int32_t dtype, int32_t metric,
