@@ -426,8 +426,10 @@ knn_status knn_backward(const void* db_lp, const float* db_scale, const float* x
                         float* dx, int32_t zero_dx, int32_t deterministic, void* workspace,
                         size_t ws_bytes, void* stream);
 
-/* Bytes of the workspace of knn_backward: 4 N + 4 M K rounded up (the same
- * for both values of `deterministic`). */
+/* Bytes of the workspace of knn_backward: about 4 N + 4 M K + 4 min(N, M K)
+ * (each part rounded up to 256 bytes) + 256: a list head per row, a link per
+ * entry, the list of touched rows and its count. The same for both values of
+ * `deterministic`. */
 size_t knn_backward_workspace(int64_t N, int32_t D, int64_t M, int32_t K, int32_t deterministic);
 
 /*
