@@ -184,3 +184,21 @@ def test_host_entries_reject_bad_arguments_without_a_device(lib):
         p = ctypes.addressof(buf)
         assert call(q=p, ov=p, oi=p) == _lib.KNN_EINVAL          # no workspace
         assert call(q=p, ov=p, oi=p, ws=4096, wsb=16) == _lib.KNN_ENOMEM   # too small
+
+
+@pytest.mark.parametrize("N,M,K", [(1, 1, 1), (1000, 7, 3), (1_000_000, 4096, 32), (50, 100, 10)])
+def test_backward_workspace_size(lib, N, M, K):
+    """A list head per row, a link per entry, the touched-row list (at most
+    min(N, M K) rows) and its count, each rounded up to 256 bytes; the same
+    for both modes."""
+    def r(b):
+        return (b + 255) // 256 * 256
+    E = M * K
+    want = r(4 * N) + r(4 * E) + r(4 * min(N, E)) + 256
+    for det in (0, 1):
+        assert lib.knn_backward_workspace(N, 16, M, K, det) == want
+
+
+def test_e4m3_database_scale_dtype(lib):
+    """KNN_E4M3_T stores one byte per element like KNN_E4M3."""
+    assert lib.knn_dtype_bytes(_lib.DTYPE["e4m3t"]) == 1 == lib.knn_dtype_bytes(_lib.DTYPE["e4m3"])
